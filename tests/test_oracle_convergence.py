@@ -1,0 +1,65 @@
+"""Manufactured-solution convergence of the oracle discretisation (pins the whole pipeline:
+basis, quadrature, Jacobians of the affine and curved maps, assembly, Dirichlet, RHS and
+error integrals).  Model problem of Sec. 2 / Sec. 6.1: -Lap u = f on the unit cube with
+homogeneous Dirichlet data; u = sin(2 pi x) sin(2 pi y) sin(2 pi z)."""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from tests._fem_ref import assemble_csr
+
+
+def solve_direct(op, b):
+    A = assemble_csr(op, dirichlet=True)
+    free = ~op.boundary_mask()
+    u = np.zeros(op.n_unique)
+    Af = A[free][:, free].tocsc()
+    u[free] = spla.spsolve(Af, b[free])
+    return u
+
+
+@pytest.mark.parametrize("k,geom,Ns", [
+    (1, "cart", (4, 8, 16)),
+    (2, "cart", (2, 4, 8)),
+    (3, "cart", (2, 4, 8)),
+    (1, "curved", (4, 8, 16)),
+    (2, "curved", (2, 4, 8)),
+    (3, "curved", (2, 4, 6)),
+])
+def test_manufactured_convergence_rates(oracle, k, geom, Ns):
+    l2s, h1s = [], []
+    for N in Ns:
+        op = oracle.Op(N, N, N, k, oracle.CURVED if geom == "curved" else oracle.AFFINE, bc=1)
+        b = op.rhs_manufactured(2.0)
+        u = solve_direct(op, b)
+        l2, h1 = op.errors(u, 2.0)
+        l2s.append(l2)
+        h1s.append(h1)
+    r_l2 = math.log(l2s[-2] / l2s[-1]) / math.log(Ns[-1] / Ns[-2])
+    r_h1 = math.log(h1s[-2] / h1s[-1]) / math.log(Ns[-1] / Ns[-2])
+    assert abs(r_l2 - (k + 1)) < 0.35, (l2s, r_l2)
+    assert abs(r_h1 - k) < 0.35, (h1s, r_h1)
+
+
+def test_oracle_cg_matches_direct_solve(oracle):
+    op = oracle.Op(3, 3, 3, 2, oracle.CURVED, bc=1)
+    b = op.rhs_manufactured(1.0)
+    ud = solve_direct(op, b)
+    uc, hist = op.cg(b, maxit=500, rtol=1e-13)
+    assert hist[-1] <= 1e-13
+    assert np.abs(uc - ud).max() < 1e-11 * np.abs(ud).max()
+    # residual history is monotone in the A-norm sense only; the Euclidean one need not be,
+    # but it must start at 1 and end below the tolerance
+    assert hist[0] == 1.0
+
+
+def test_interpolant_error_rate(oracle):
+    """Nodal interpolation of the smooth u converges at k+1 in L2 on the curved mesh."""
+    errs = []
+    for N in (4, 8):
+        op = oracle.Op(N, N, N, 2, oracle.CURVED)
+        errs.append(op.errors(op.interpolate_manufactured(1.0), 1.0)[0])
+    assert abs(math.log2(errs[0] / errs[1]) - 3.0) < 0.3
