@@ -1,0 +1,430 @@
+"""Benchmark of the matrix-free Q_k hot path on GB300 (prints ONE JSON line on rank 0).
+
+Workload (N=1): Q4 Laplace on the curved 64^3 mesh of the unit cube (x + 0.1 sin(pi x)
+sin(pi y) sin(pi z) on every coordinate, per-Gauss-point Jacobians), FP64, homogeneous
+Dirichlet.  A step is one CG iteration: q = P A P p (sum-factorised apply + deterministic
+duplicate summation + mask) and the fused CG vector updates with their dot products.
+value = cell-wise DoFs per step / step time.  Extra fields: the apply alone for Q3/Q4 in
+FP64 and FP32, the Helmholtz degree sweep at ~50M cell-wise DoFs, the end-to-end apply from
+host memory, and the CPU oracle baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-sweep] [--solve]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "operator-apply GDoF/s and % HBM roofline per degree; solved DoF/s + p99 latency at 1e-10"
+SWEEP_N = {1: 184, 2: 123, 3: 92, 4: 74, 5: 61, 6: 53, 7: 46, 8: 41}
+
+
+def peaks():
+    p = {"hbm_gbs": 6800.0, "source": "fallback"}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            j = json.load(f)
+        p = {"hbm_gbs": float(j["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        pass
+    # FP64 FMA pipe of GB300: nominal 1.25 TFLOP/s dense at the 2070 MHz maximum clock,
+    # i.e. 2 FP64 FMA / clock / SM x 152 SMs x 2 FLOP.
+    p["fp64_tflops"] = 2 * 2 * 152 * 2.070e9 / 1e12
+    # FP32 FMA pipe: 128 lanes / SM
+    p["fp32_tflops"] = 128 * 2 * 152 * 2.070e9 / 1e12
+    return p
+
+
+def flops_per_dof(path: int, n: int, helm: bool) -> float:
+    """Algorithmic FLOPs per cell-wise DoF of one apply (FMA = 2)."""
+    if path == 0:
+        return 14.0 * n
+    return 24.0 * n + 15.0 + (2.0 if helm else 0.0)
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_op(mf, torch, N, k, geom, kind, prec, bc, stream):
+    mesh = mf.mf_mesh_create(N, N, N, geom, None, 0.1)
+    op = mf.mf_operator_create(mesh, k, kind, 1.0, prec, bc)
+    info = mf.mf_operator_info(op)
+    ws = torch.empty(max(info["workspace_bytes"], 256), dtype=torch.uint8, device="cuda")
+    mf.mf_operator_setup(op, ws.data_ptr(), ws.numel(), stream)
+    return mesh, op, info, ws
+
+
+def random_native(mf, torch, op, info, N, k, seed, dtype, stream):
+    from paper_2609_04534_gb300 import inputs
+
+    u = torch.as_tensor(inputs.random_unique(N, N, N, k, seed), device="cuda").to(dtype)
+    x = torch.empty(info["n_native"], dtype=dtype, device="cuda")
+    mf.mf_scatter_unique(op, u.data_ptr(), x.data_ptr(), stream)
+    return x
+
+
+def time_apply(mf, torch, op, x, y, stream_obj, reps, warm):
+    s = stream_obj.cuda_stream
+    for _ in range(warm):
+        mf.mf_apply(op, x.data_ptr(), y.data_ptr(), s)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    stream_obj.synchronize()
+    ev[0].record(stream_obj)
+    for _ in range(reps):
+        mf.mf_apply(op, x.data_ptr(), y.data_ptr(), s)
+    ev[1].record(stream_obj)
+    ev[1].synchronize()
+    return ev[0].elapsed_time(ev[1]) / 1e3 / reps
+
+
+def time_kernels(mf, torch, op, x, y, stream_obj, reps):
+    """Per-kernel device time of the apply's two kernels (split apply, duplicate summation)."""
+    s = stream_obj.cuda_stream
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ta = td = 0.0
+    for _ in range(reps):
+        e[0].record(stream_obj)
+        mf.mf_apply_split(op, x.data_ptr(), y.data_ptr(), s)
+        e[1].record(stream_obj)
+        mf.mf_dss(op, y.data_ptr(), s)
+        e[2].record(stream_obj)
+        e[2].synchronize()
+        ta += e[0].elapsed_time(e[1]) / 1e3
+        td += e[1].elapsed_time(e[2]) / 1e3
+    return ta / reps, td / reps
+
+
+def cpu_baseline(N, k, curved, kind_helm, target_s=12.0):
+    """The FP64 oracle (as it stands) on a bounded sample of cells of the same mesh, all
+    host threads; reports cell-wise DoF/s of its apply."""
+    import oracle
+
+    oracle.build()
+    o = oracle.Op(N, N, N, k, oracle.CURVED if curved else oracle.AFFINE, cm=1.0 if kind_helm else 0.0, bc=1)
+    n3 = (k + 1) ** 3
+    rng = np.random.default_rng(0)
+    ncal = 256
+    cells = np.sort(rng.choice(o.ncells, ncal, replace=False)).astype(np.int64)
+    xcw = np.zeros(o.ncells * n3) if o.ncells * n3 < 6e7 else None
+    if xcw is None:
+        return None
+    xcw[:] = rng.uniform(-1, 1, xcw.size)
+    t0 = time.perf_counter()
+    o.apply_cells(xcw, cells)
+    dt = time.perf_counter() - t0
+    m = int(min(o.ncells, max(ncal, ncal * target_s / max(dt, 1e-6))))
+    cells = np.sort(rng.choice(o.ncells, m, replace=False)).astype(np.int64)
+    t0 = time.perf_counter()
+    o.apply_cells(xcw, cells)
+    dt = time.perf_counter() - t0
+    return {"value": m * n3 / dt / 1e9, "unit": "GDoF/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{m} of {o.ncells} cells of the same mesh (local quadrature-loop apply, FP64), {dt:.1f} s"}
+
+
+def reference_arm(args):
+    """CPU oracle arm: each step applies the oracle to a bounded sample of cells."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    N, k = 64, 4
+    o = oracle.Op(N, N, N, k, oracle.CURVED, bc=1)
+    n3 = (k + 1) ** 3
+    rng = np.random.default_rng(0)
+    xcw = rng.uniform(-1, 1, o.ncells * n3)
+    m = 2048
+    cells = np.sort(rng.choice(o.ncells, m, replace=False)).astype(np.int64)
+    for _ in range(args.warmup):
+        o.apply_cells(xcw, cells)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.apply_cells(xcw, cells)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = m * n3 / dt / 1e9
+    sample = f"{m} of {o.ncells} cells per step (local quadrature-loop apply, FP64)"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GDoF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "Q4 Laplace curved 64^3 (x+0.1 sin sin sin), FP64, Dirichlet; CPU oracle sample",
+                       "global_batch": 1, "seq_len": 0, "parallelism": "replicas"},
+            "cpu_baseline": {"value": v, "unit": "GDoF/s", "kind": "oracle", "cores": oracle.max_threads(),
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def profile_apply(args):
+    """A few applies of one case, for ncu captures of the apply and DSS kernels."""
+    import torch
+
+    import paper_2609_04534_gb300 as mf
+
+    N, k, geom, prec, kind = args.profile_apply.split(",")
+    N, k = int(N), int(k)
+    g = mf.MF_CURVED_SIN if geom == "curved" else mf.MF_AFFINE
+    p = {"fp64": mf.MF_FP64, "fp32": mf.MF_FP32}[prec]
+    kd = mf.MF_HELMHOLTZ if kind == "helmholtz" else mf.MF_LAPLACE
+    dt = torch.float64 if p == mf.MF_FP64 else torch.float32
+    stream = torch.cuda.Stream()
+    s = stream.cuda_stream
+    mesh, op, info, ws = make_op(mf, torch, N, k, g, kd, p, 0, s)
+    with torch.cuda.stream(stream):
+        x = random_native(mf, torch, op, info, N, k, 1, dt, s)
+        y = torch.empty_like(x)
+    t = time_apply(mf, torch, op, x, y, stream, args.reps, 1)
+    print(json.dumps({"case": args.profile_apply, "n_cellwise": info["n_cellwise"], "ms": t * 1e3,
+                      "gdofs": info["n_cellwise"] / t / 1e9,
+                      "alg_bytes": info["algorithmic_bytes_per_apply"]}), flush=True)
+    mf.mf_operator_destroy(op)
+    mf.mf_mesh_destroy(mesh)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--solve", action="store_true")
+    ap.add_argument("--profile-apply", default=None, metavar="N,k,geom,prec,kind",
+                    help="only run a few applies of one case (for ncu), e.g. 32,4,curved,fp64,laplace")
+    ap.add_argument("--reps", type=int, default=3)
+    args = ap.parse_args()
+    if args.profile_apply:
+        profile_apply(args)
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import torch
+
+    import paper_2609_04534_gb300 as mf
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    pk = peaks()
+    stream = torch.cuda.Stream()
+    s = stream.cuda_stream
+
+    # ------------------------------------------------------------ primary: CG iteration
+    N, k = 64, 4
+    mesh, op, info, ws = make_op(mf, torch, N, k, mf.MF_CURVED_SIN, mf.MF_LAPLACE, mf.MF_FP64, mf.MF_BC_DIRICHLET0, s)
+    ncw = info["n_cellwise"]
+    with torch.cuda.stream(stream):
+        b = random_native(mf, torch, op, info, N, k, 1, torch.float64, s)
+        x = torch.zeros_like(b)
+        y = torch.empty_like(b)
+        cws = torch.empty(mf.mf_cg_workspace_bytes(op, 0), dtype=torch.uint8, device="cuda")
+    stream.synchronize()
+    # warm-up (also builds and caches the solve's graph path once)
+    mf.mf_cg_solve(op, b.data_ptr(), x.data_ptr(), 0.0, args.warmup, 0, cws.data_ptr(), cws.numel(), s,
+                   allow_not_converged=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with Clocks(local) as clk:
+        ev[0].record(stream)
+        st = mf.mf_cg_solve(op, b.data_ptr(), x.data_ptr(), 0.0, args.steps, 0, cws.data_ptr(), cws.numel(), s,
+                            allow_not_converged=True)
+        ev[1].record(stream)
+        ev[1].synchronize()
+    torch.cuda.synchronize()
+    t_steps = ev[0].elapsed_time(ev[1]) / 1e3
+    if dist:
+        tt = torch.tensor([t_steps], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_steps = float(tt.item())
+        dist.barrier()
+    its = st["iterations"]
+    t_it = t_steps / max(its, 1)
+    value = world * ncw / t_it / 1e9
+
+    # apply alone on the same operator, plus per-kernel times of the dominant kernel
+    t_apply = time_apply(mf, torch, op, b, y, stream, 20, 3)
+    t_split, t_dss = time_kernels(mf, torch, op, b, y, stream, 10)
+    fpd = flops_per_dof(info["path"], info["n"], False)
+    flops = fpd * ncw
+    roof = {"bound": "alu", "achieved": flops / t_split / 1e12, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
+            "frac": flops / t_split / 1e12 / pk["fp64_tflops"], "traffic": None,
+            "kernel": "apply_general<double,5,16,curved,laplace>",
+            "peak_source": "nominal FP64 pipe: 2 FMA/clk/SM x 152 SMs x 2070 MHz (derived)"}
+    alg_bytes = info["algorithmic_bytes_per_apply"]
+    hbm_frac_apply = alg_bytes / t_apply / 1e9 / pk["hbm_gbs"]
+
+    # e2e through the public API from host memory: pinned b in, x out, K CG iterations
+    e2e = None
+    try:
+        hb = torch.empty(info["n_native"], dtype=torch.float64, pin_memory=True)
+        hb.copy_(b.cpu())
+        hx = torch.empty_like(hb).pin_memory()
+        db = torch.empty_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            db.copy_(hb, non_blocking=True)
+        st2 = mf.mf_cg_solve(op, db.data_ptr(), x.data_ptr(), 0.0, args.steps, 0, cws.data_ptr(), cws.numel(), s,
+                             allow_not_converged=True)
+        with torch.cuda.stream(stream):
+            hx.copy_(x, non_blocking=True)
+        stream.synchronize()
+        te = time.perf_counter() - t0
+        e2e = {"value": world * ncw * st2["iterations"] / te / 1e9, "unit": "GDoF/s",
+               "h2d_bytes_per_step": info["n_native"] * 8 / max(st2["iterations"], 1),
+               "d2h_bytes_per_step": info["n_native"] * 8 / max(st2["iterations"], 1),
+               "note": "mf_cg_solve of K iterations from pinned host b to host x; copies amortised per step"}
+    except Exception as exc:  # keep the line even if pinned memory is unavailable
+        e2e = {"value": None, "unit": "GDoF/s", "error": str(exc)[:200]}
+    del cws
+    mf.mf_operator_destroy(op)
+    mf.mf_mesh_destroy(mesh)
+    del ws, b, x, y
+    torch.cuda.empty_cache()
+
+    # ------------------------------------------------------------ applies of the same config
+    applies = {}
+    for kk in (3, 4):
+        for prec, dt, nm in ((mf.MF_FP64, torch.float64, "fp64"), (mf.MF_FP32, torch.float32, "fp32")):
+            mesh, op, info, ws = make_op(mf, torch, 64, kk, mf.MF_CURVED_SIN, mf.MF_LAPLACE, prec, 0, s)
+            with torch.cuda.stream(stream):
+                xx = random_native(mf, torch, op, info, 64, kk, 1, dt, s)
+                yy = torch.empty_like(xx)
+            t = time_apply(mf, torch, op, xx, yy, stream, 20, 3)
+            ta, td = time_kernels(mf, torch, op, xx, yy, stream, 5)
+            gd = info["n_cellwise"] / t / 1e9
+            applies[f"Q{kk}_{nm}"] = {"gdofs": round(gd, 3),
+                                      "hbm_frac": round(info["algorithmic_bytes_per_apply"] / t / 1e9 / pk["hbm_gbs"], 4),
+                                      "apply_kernel_ms": round(ta * 1e3, 4), "dss_kernel_ms": round(td * 1e3, 4)}
+            mf.mf_operator_destroy(op)
+            mf.mf_mesh_destroy(mesh)
+            del ws, xx, yy
+            torch.cuda.empty_cache()
+
+    # ------------------------------------------------------------ degree sweep (Helmholtz, ~50M)
+    sweep = {}
+    if not args.no_sweep:
+        for kk, NN in SWEEP_N.items():
+            mesh, op, info, ws = make_op(mf, torch, NN, kk, mf.MF_AFFINE, mf.MF_HELMHOLTZ, mf.MF_FP64, 0, s)
+            with torch.cuda.stream(stream):
+                xx = random_native(mf, torch, op, info, NN, kk, 2, torch.float64, s)
+                yy = torch.empty_like(xx)
+            t = time_apply(mf, torch, op, xx, yy, stream, 10, 3)
+            gd = info["n_cellwise"] / t / 1e9
+            sweep[f"k{kk}"] = {"N": NN, "n_cellwise": info["n_cellwise"], "gdofs": round(gd, 3),
+                               "hbm_frac": round(info["algorithmic_bytes_per_apply"] / t / 1e9 / pk["hbm_gbs"], 4),
+                               "fp64_frac": round(flops_per_dof(0, kk + 1, True) * info["n_cellwise"] / t / 1e12
+                                                  / pk["fp64_tflops"], 4)}
+            mf.mf_operator_destroy(op)
+            mf.mf_mesh_destroy(mesh)
+            del ws, xx, yy
+            torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        try:
+            cpu = cpu_baseline(64, 4, True, False)
+        except Exception as exc:
+            cpu = {"value": None, "error": str(exc)[:200]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "GDoF/s", "n_gpus": world, "steps": its,
+            "warmup": args.warmup, "ms_per_step": round(t_it * 1e3, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "Q4 Laplace curved 64^3 (x+0.1 sin(pi x)sin(pi y)sin(pi z)), per-Gauss-point "
+                                   "Jacobians, FP64, Dirichlet; step = one CG iteration (apply + DSS + mask + "
+                                   "fused CG updates), x uniform[-1,1] seed 1",
+                       "n_cellwise": ncw, "global_batch": 1, "seq_len": 0,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (vectors 262 MB + geometry 1.57 GB per apply)"},
+            "apply_only": {"gdofs": round(ncw / t_apply / 1e9, 4), "hbm_frac_of_measured": round(hbm_frac_apply, 4),
+                           "apply_kernel_ms": round(t_split * 1e3, 4), "dss_kernel_ms": round(t_dss * 1e3, 4)},
+            "roofline": roof,
+            "applies_64cubed_curved": applies,
+            "helmholtz_sweep_50M": sweep,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 5 * its,
+            "clocks": clk.summary(),
+            "peaks": pk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

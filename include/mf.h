@@ -1,0 +1,166 @@
+/*
+ * mf.h -- C ABI of the GB300 matrix-free Q_k operator library (libmf.so).
+ *
+ * The library evaluates y = A x for the continuous tensor-product Q_k finite-element
+ * operator (Laplace, or Helmholtz = mass + Laplace) on a structured hexahedral mesh of the
+ * unit cube, affine or curved, with the vector held in cell-wise storage: every cell owns
+ * its (k+1)^3 nodal values and shared vertex/edge/face values are duplicated.  The apply
+ * is the volume term of the paper's bilinear form (Sec. 2, Eq. (sipg), first sum) evaluated
+ * by sum factorisation (Sec. 3.1, Eq. (eval_pipeline) for the Cartesian form), followed by
+ * a deterministic summation of the duplicated values (the assembly G G^T of Sec. 4,
+ * Eqs. (shadow_gather), (shadow_assembly)), organised as the dimension-split,
+ * atomic-free sweeps of Sec. 3.
+ *
+ * Conventions for every entry point:
+ *  - Return value: MF_OK (0) or a negative mf_status.  No entry point aborts.
+ *  - Pointers named *_dev are device pointers owned by the caller (allocated e.g. through
+ *    PyTorch).  The library never allocates, frees or retains device memory except inside
+ *    a workspace the caller hands over (mf_operator_setup, mf_cg_solve, mf_server_create).
+ *  - Pointers named *_host are host pointers owned by the caller.
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream).  Work is
+ *    enqueued on it; the call returns before the GPU finishes unless stated otherwise.
+ *  - Vectors in "native" layout have mf_info.n_native elements of the operator's element
+ *    type (double for MF_FP64 and MF_MIXED, float for MF_FP32).  Native layout: tiles of
+ *    32 cells (a 4x4x2 brick), element (tile, local dof l, lane) at (tile*n^3 + l)*32 + lane,
+ *    l = i + n*(j + n*k) with x fastest.  Lanes of cells outside the mesh are padding: they
+ *    are ignored on input and written as 0 on output.
+ *  - "Canonical" cell-wise layout: [cell (x fastest)][k][j][i], n_cellwise elements.
+ *  - "Unique" layout: global nodes (I,J,L), I = cx*k + i, lexicographic with x fastest,
+ *    n_unique elements.
+ *  - A cell-wise vector is consistent when all copies of each shared node are equal.
+ */
+#ifndef MF_H
+#define MF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int mf_status;
+#define MF_OK 0
+#define MF_ERR_ARG (-1)           /* invalid argument, size or state */
+#define MF_ERR_OOM (-2)           /* workspace or arena too small */
+#define MF_ERR_CUDA (-3)          /* a CUDA call failed */
+#define MF_ERR_NOT_CONVERGED (-4) /* solver reached maxit */
+#define MF_ERR_BREAKDOWN (-5)     /* CG: p^T A p <= 0 or non-finite scalar */
+#define MF_ERR_TIMEOUT (-6)       /* a bounded wait gave up */
+#define MF_ERR_BUSY (-7)          /* request still pending / queue full */
+#define MF_ERR_UNSUPPORTED (-8)   /* combination not built */
+
+enum { MF_AFFINE = 0, MF_CURVED_SIN = 1 };
+enum { MF_LAPLACE = 0, MF_HELMHOLTZ = 1 };
+enum { MF_FP64 = 0, MF_FP32 = 1, MF_MIXED = 2 };
+enum { MF_BC_NONE = 0, MF_BC_DIRICHLET0 = 1 };
+
+typedef struct mf_mesh mf_mesh;
+typedef struct mf_operator mf_operator;
+typedef struct mf_server mf_server;
+
+/* Last error message of the calling thread (static storage, never NULL). */
+const char* mf_last_error(void);
+
+/* ------------------------------------------------------------------ mesh
+ * nx*ny*nz cells of the unit cube.  geometry MF_AFFINE maps xh -> A xh + b with
+ * affine_3x4 = {A row-major (9), b (3)} (NULL = identity).  MF_CURVED_SIN maps
+ * xh -> xh + curve_amp * sin(pi xh1) sin(pi xh2) sin(pi xh3) on every coordinate; the
+ * Jacobian is evaluated analytically at every Gauss point (Sec. 2: six metric entries and
+ * det J per point).  Host-only object. */
+mf_status mf_mesh_create(int nx, int ny, int nz, int geometry, const double* affine_3x4, double curve_amp,
+                         mf_mesh** out);
+void mf_mesh_destroy(mf_mesh* mesh);
+
+/* ------------------------------------------------------------------ operator
+ * degree k in 1..8 (n = k+1 GLL nodes and Gauss points per direction).  kind MF_LAPLACE or
+ * MF_HELMHOLTZ (A = mass_coeff*M + K).  precision MF_FP64, MF_FP32 or MF_MIXED (FP64
+ * vectors and geometry plus an FP32 copy of the geometry for the inner solver of
+ * mf_cg_solve).  bc MF_BC_DIRICHLET0 applies P A P with P zeroing nodes on the cube
+ * boundary.  Host-only until mf_operator_setup. */
+mf_status mf_operator_create(const mf_mesh* mesh, int degree, int kind, double mass_coeff, int precision, int bc,
+                             mf_operator** out);
+void mf_operator_destroy(mf_operator* op);
+
+typedef struct {
+  int64_t n_cellwise;     /* cells * n^3 */
+  int64_t n_unique;       /* (nx k+1)(ny k+1)(nz k+1) */
+  int64_t n_native;       /* elements of a native vector (with padding lanes) */
+  int64_t n_cells;
+  int32_t degree, n, elem_bytes, path; /* path: 0 Cartesian, 1 affine general, 2 curved */
+  size_t geom_bytes;      /* device bytes of per-point geometry (0 for affine paths) */
+  size_t workspace_bytes; /* bytes mf_operator_setup needs (>= geom_bytes) */
+  double algorithmic_bytes_per_apply; /* read x + write y + geometry, per apply */
+} mf_info;
+mf_status mf_operator_info(const mf_operator* op, mf_info* info);
+
+/* Binds a caller-owned device workspace of >= info.workspace_bytes bytes (256-byte
+ * aligned) and precomputes the per-point geometry into it on `stream`.  The workspace
+ * must outlive the operator. */
+mf_status mf_operator_setup(mf_operator* op, void* workspace_dev, size_t bytes, void* stream);
+
+/* ------------------------------------------------------------------ layout helpers */
+/* canonical cell-wise -> native and back (device pointers, operator element type). */
+mf_status mf_to_native(const mf_operator* op, const void* canonical_dev, void* native_dev, void* stream);
+mf_status mf_from_native(const mf_operator* op, const void* native_dev, void* canonical_dev, void* stream);
+/* unique -> native cell-wise copies (the gather G of Sec. 4, Eq. (shadow_gather)). */
+mf_status mf_scatter_unique(const mf_operator* op, const void* unique_dev, void* native_dev, void* stream);
+/* native consistent -> unique (reads one copy per node). */
+mf_status mf_gather_unique(const mf_operator* op, const void* native_dev, void* unique_dev, void* stream);
+
+/* ------------------------------------------------------------------ apply
+ * y = G G^T A~ x: local sum-factorised apply of every cell followed by the deterministic
+ * duplicate summation, so y is consistent; with MF_BC_DIRICHLET0, x is read as P x and y
+ * is returned as P y.  x must be consistent.  x and y are native vectors and must not
+ * overlap.  Summation order of duplicates: pairwise x, then y, then z
+ * (((c000+c100)+(c010+c110))+((c001+c101)+(c011+c111)) for a vertex), independent of
+ * tiling, so results are bitwise reproducible. */
+mf_status mf_apply(const mf_operator* op, const void* x_dev, void* y_dev, void* stream);
+/* y~ = A~ x: the split (unassembled) local results, no duplicate summation (Sec. 4,
+ * Eq. (split_operator)). */
+mf_status mf_apply_split(const mf_operator* op, const void* x_dev, void* y_dev, void* stream);
+/* In-place duplicate summation y <- G G^T y (and P y for Dirichlet). */
+mf_status mf_dss(const mf_operator* op, void* y_dev, void* stream);
+/* End to end from host memory: copies canonical x_host to the device, applies, copies the
+ * canonical result to y_host and synchronises `stream`.  Uses the caller's device
+ * workspace of >= mf_apply_host_workspace_bytes() bytes. */
+size_t mf_apply_host_workspace_bytes(const mf_operator* op);
+mf_status mf_apply_host(const mf_operator* op, const void* x_host, void* y_host, void* workspace_dev, size_t bytes,
+                        void* stream);
+
+/* ------------------------------------------------------------------ reductions
+ * Assembled inner product of two consistent native vectors (each unique node counted once:
+ * copies weighted by 1/multiplicity, powers of two, so exact), accumulated in FP64 in a
+ * fixed order; result written to *result_dev (one double, device).  With split=1 the
+ * first vector is a split dual and the pairing is the flat sum over all copies (Lemma 1,
+ * Eq. (shadow_pairing)).  Needs mf_reduce_workspace_bytes() of scratch. */
+size_t mf_reduce_workspace_bytes(const mf_operator* op);
+mf_status mf_dot(const mf_operator* op, const void* a_dev, const void* b_dev, int split, double* result_dev,
+                 void* scratch_dev, size_t scratch_bytes, void* stream);
+
+/* ------------------------------------------------------------------ CG solver
+ * Unpreconditioned CG on (P A P) x = P b from x = 0 for consistent native b, to
+ * ||b - A x|| <= rtol ||b|| (assembled Euclidean norm = the pairing <r, r> of Sec. 4) or
+ * maxit iterations.  mixed = 0: FP64 (or FP32 for an MF_FP32 operator) CG.  mixed = 1
+ * (operator MF_MIXED): FP64 defect correction -- outer residual r = b - A x, the update and
+ * all dot products in FP64, inner CG with the FP32 apply.  Synchronous.  Workspace:
+ * mf_cg_workspace_bytes(op, mixed) device bytes. */
+typedef struct {
+  int32_t iterations;       /* total CG iterations (inner iterations for mixed) */
+  int32_t outer_iterations; /* defect-correction steps (mixed) */
+  double rel_residual;      /* final ||b - A x|| / ||b|| in FP64 */
+  double seconds;           /* wall time of the solve */
+  int32_t status;           /* MF_OK, MF_ERR_NOT_CONVERGED, MF_ERR_BREAKDOWN */
+  int32_t check_every;      /* iterations between host residual checks */
+} mf_solve_stats;
+size_t mf_cg_workspace_bytes(const mf_operator* op, int mixed);
+mf_status mf_cg_solve(const mf_operator* op, const void* b_dev, void* x_dev, double rtol, int maxit, int mixed,
+                      mf_solve_stats* stats, void* workspace_dev, size_t bytes, void* stream);
+/* Records up to `cap` relative residual norms (one per iteration, FP64) of the next
+ * mf_cg_solve on this thread into hist_host; pass NULL to stop recording. */
+mf_status mf_cg_record_history(double* hist_host, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MF_H */

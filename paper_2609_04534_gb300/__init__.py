@@ -1,0 +1,194 @@
+"""GB300-native matrix-free Q_k operator: thin Python binding of the C ABI in include/mf.h.
+
+Every function here only marshals arguments (ints for device pointers, ctypes structs) and
+calls ``libmf.so``; every step of the apply, the duplicate summation and the solvers runs
+in the library's CUDA kernels.  There is no CPU fallback: importing the binding without a
+built library raises.  PyTorch, where used by callers, supplies device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmf.so")
+
+MF_OK, MF_ERR_ARG, MF_ERR_OOM, MF_ERR_CUDA = 0, -1, -2, -3
+MF_ERR_NOT_CONVERGED, MF_ERR_BREAKDOWN, MF_ERR_TIMEOUT, MF_ERR_BUSY, MF_ERR_UNSUPPORTED = -4, -5, -6, -7, -8
+MF_AFFINE, MF_CURVED_SIN = 0, 1
+MF_LAPLACE, MF_HELMHOLTZ = 0, 1
+MF_FP64, MF_FP32, MF_MIXED = 0, 1, 2
+MF_BC_NONE, MF_BC_DIRICHLET0 = 0, 1
+
+_STATUS = {0: "MF_OK", -1: "MF_ERR_ARG", -2: "MF_ERR_OOM", -3: "MF_ERR_CUDA", -4: "MF_ERR_NOT_CONVERGED",
+           -5: "MF_ERR_BREAKDOWN", -6: "MF_ERR_TIMEOUT", -7: "MF_ERR_BUSY", -8: "MF_ERR_UNSUPPORTED"}
+
+
+class MfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class mf_info(C.Structure):
+    _fields_ = [("n_cellwise", C.c_int64), ("n_unique", C.c_int64), ("n_native", C.c_int64),
+                ("n_cells", C.c_int64), ("degree", C.c_int32), ("n", C.c_int32), ("elem_bytes", C.c_int32),
+                ("path", C.c_int32), ("geom_bytes", C.c_size_t), ("workspace_bytes", C.c_size_t),
+                ("algorithmic_bytes_per_apply", C.c_double)]
+
+
+class mf_solve_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("outer_iterations", C.c_int32), ("rel_residual", C.c_double),
+                ("seconds", C.c_double), ("status", C.c_int32), ("check_every", C.c_int32)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libmf.so (built by ``paper_2609_04534_gb300.build``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libmf.so not built at {LIB_PATH}: run `python -m paper_2609_04534_gb300.build`")
+    L = C.CDLL(LIB_PATH)
+    vp, sz, i32, d = C.c_void_p, C.c_size_t, C.c_int, C.c_double
+    L.mf_last_error.restype = C.c_char_p
+    L.mf_mesh_create.argtypes = [i32, i32, i32, i32, C.POINTER(C.c_double), d, C.POINTER(vp)]
+    L.mf_mesh_destroy.argtypes = [vp]
+    L.mf_mesh_destroy.restype = None
+    L.mf_operator_create.argtypes = [vp, i32, i32, d, i32, i32, C.POINTER(vp)]
+    L.mf_operator_destroy.argtypes = [vp]
+    L.mf_operator_destroy.restype = None
+    L.mf_operator_info.argtypes = [vp, C.POINTER(mf_info)]
+    L.mf_operator_setup.argtypes = [vp, vp, sz, vp]
+    for nm in ("mf_to_native", "mf_from_native", "mf_scatter_unique", "mf_gather_unique", "mf_apply",
+               "mf_apply_split"):
+        getattr(L, nm).argtypes = [vp, vp, vp, vp]
+    L.mf_dss.argtypes = [vp, vp, vp]
+    L.mf_apply_host_workspace_bytes.argtypes = [vp]
+    L.mf_apply_host_workspace_bytes.restype = sz
+    L.mf_apply_host.argtypes = [vp, vp, vp, vp, sz, vp]
+    L.mf_reduce_workspace_bytes.argtypes = [vp]
+    L.mf_reduce_workspace_bytes.restype = sz
+    L.mf_dot.argtypes = [vp, vp, vp, i32, vp, vp, sz, vp]
+    L.mf_cg_workspace_bytes.argtypes = [vp, i32]
+    L.mf_cg_workspace_bytes.restype = sz
+    L.mf_cg_solve.argtypes = [vp, vp, vp, d, i32, i32, C.POINTER(mf_solve_stats), vp, sz, vp]
+    L.mf_cg_record_history.argtypes = [vp, i32]
+    _lib = L
+    return L
+
+
+def _check(code: int) -> int:
+    if code != MF_OK:
+        raise MfError(code, lib().mf_last_error().decode())
+    return code
+
+
+def last_error() -> str:
+    return lib().mf_last_error().decode()
+
+
+# ---------------------------------------------------------------- handles
+def mf_mesh_create(nx: int, ny: int, nz: int, geometry: int = MF_AFFINE, affine_3x4=None, curve_amp: float = 0.1):
+    h = C.c_void_p()
+    arr = None
+    if affine_3x4 is not None:
+        vals = [float(v) for v in affine_3x4]
+        assert len(vals) == 12
+        arr = (C.c_double * 12)(*vals)
+    _check(lib().mf_mesh_create(nx, ny, nz, geometry, arr, curve_amp, C.byref(h)))
+    return h.value
+
+
+def mf_mesh_destroy(mesh) -> None:
+    lib().mf_mesh_destroy(mesh)
+
+
+def mf_operator_create(mesh, degree: int, kind: int = MF_LAPLACE, mass_coeff: float = 1.0,
+                       precision: int = MF_FP64, bc: int = MF_BC_NONE):
+    h = C.c_void_p()
+    _check(lib().mf_operator_create(mesh, degree, kind, mass_coeff, precision, bc, C.byref(h)))
+    return h.value
+
+
+def mf_operator_destroy(op) -> None:
+    lib().mf_operator_destroy(op)
+
+
+def mf_operator_info(op) -> dict:
+    info = mf_info()
+    _check(lib().mf_operator_info(op, C.byref(info)))
+    return {f: getattr(info, f) for f, _ in mf_info._fields_}
+
+
+def mf_operator_setup(op, workspace_ptr: int, nbytes: int, stream: int = 0) -> None:
+    _check(lib().mf_operator_setup(op, workspace_ptr or None, nbytes, stream or None))
+
+
+# ---------------------------------------------------------------- vectors
+def mf_to_native(op, canonical_ptr: int, native_ptr: int, stream: int = 0) -> None:
+    _check(lib().mf_to_native(op, canonical_ptr, native_ptr, stream or None))
+
+
+def mf_from_native(op, native_ptr: int, canonical_ptr: int, stream: int = 0) -> None:
+    _check(lib().mf_from_native(op, native_ptr, canonical_ptr, stream or None))
+
+
+def mf_scatter_unique(op, unique_ptr: int, native_ptr: int, stream: int = 0) -> None:
+    _check(lib().mf_scatter_unique(op, unique_ptr, native_ptr, stream or None))
+
+
+def mf_gather_unique(op, native_ptr: int, unique_ptr: int, stream: int = 0) -> None:
+    _check(lib().mf_gather_unique(op, native_ptr, unique_ptr, stream or None))
+
+
+def mf_apply(op, x_ptr: int, y_ptr: int, stream: int = 0) -> None:
+    _check(lib().mf_apply(op, x_ptr, y_ptr, stream or None))
+
+
+def mf_apply_split(op, x_ptr: int, y_ptr: int, stream: int = 0) -> None:
+    _check(lib().mf_apply_split(op, x_ptr, y_ptr, stream or None))
+
+
+def mf_dss(op, y_ptr: int, stream: int = 0) -> None:
+    _check(lib().mf_dss(op, y_ptr, stream or None))
+
+
+def mf_apply_host_workspace_bytes(op) -> int:
+    return int(lib().mf_apply_host_workspace_bytes(op))
+
+
+def mf_apply_host(op, x_host_ptr: int, y_host_ptr: int, workspace_ptr: int, nbytes: int, stream: int = 0) -> None:
+    _check(lib().mf_apply_host(op, x_host_ptr, y_host_ptr, workspace_ptr, nbytes, stream or None))
+
+
+def mf_reduce_workspace_bytes(op) -> int:
+    return int(lib().mf_reduce_workspace_bytes(op))
+
+
+def mf_dot(op, a_ptr: int, b_ptr: int, result_ptr: int, scratch_ptr: int, scratch_bytes: int, split: int = 0,
+           stream: int = 0) -> None:
+    _check(lib().mf_dot(op, a_ptr, b_ptr, split, result_ptr, scratch_ptr, scratch_bytes, stream or None))
+
+
+def mf_cg_workspace_bytes(op, mixed: int = 0) -> int:
+    return int(lib().mf_cg_workspace_bytes(op, mixed))
+
+
+def mf_cg_solve(op, b_ptr: int, x_ptr: int, rtol: float, maxit: int, mixed: int, workspace_ptr: int,
+                nbytes: int, stream: int = 0, allow_not_converged: bool = False) -> dict:
+    st = mf_solve_stats()
+    code = lib().mf_cg_solve(op, b_ptr, x_ptr, rtol, maxit, mixed, C.byref(st), workspace_ptr, nbytes,
+                             stream or None)
+    if not (code == MF_OK or (allow_not_converged and code == MF_ERR_NOT_CONVERGED)):
+        _check(code)
+    out = {f: getattr(st, f) for f, _ in mf_solve_stats._fields_}
+    out["code"] = code
+    return out
+
+
+def mf_cg_record_history(hist_ptr: int | None, cap: int) -> None:
+    _check(lib().mf_cg_record_history(hist_ptr, cap))

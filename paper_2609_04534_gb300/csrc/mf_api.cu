@@ -1,0 +1,292 @@
+// mf_api.cu -- C ABI: mesh and operator handles, workspace binding, layout helpers, apply.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "mf_internal.h"
+
+namespace mf {
+
+static thread_local char g_err[512] = "";
+
+mf_status set_error(mf_status code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+mf_status cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return MF_OK;
+  return set_error(MF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define MF_DISPATCH_N(n, fn, ...)                                                   \
+  switch (n) {                                                                      \
+    case 2: return fn<2>(__VA_ARGS__);                                              \
+    case 3: return fn<3>(__VA_ARGS__);                                              \
+    case 4: return fn<4>(__VA_ARGS__);                                              \
+    case 5: return fn<5>(__VA_ARGS__);                                              \
+    case 6: return fn<6>(__VA_ARGS__);                                              \
+    case 7: return fn<7>(__VA_ARGS__);                                              \
+    case 8: return fn<8>(__VA_ARGS__);                                              \
+    case 9: return fn<9>(__VA_ARGS__);                                              \
+    default: return set_error(MF_ERR_UNSUPPORTED, "degree %d not built", (n) - 1);  \
+  }
+
+mf_status launch_apply_split(const mf_operator* op, int elem, const void* x, void* y, cudaStream_t s) {
+  MF_DISPATCH_N(op->n, apply_split_n, op, elem, x, y, s);
+}
+mf_status launch_dss(const mf_operator* op, int elem, void* y, cudaStream_t s) {
+  MF_DISPATCH_N(op->n, dss_n, op, elem, y, s);
+}
+mf_status launch_geometry(const mf_operator* op, int elem, void* geom, cudaStream_t s) {
+  MF_DISPATCH_N(op->n, geometry_n, op, elem, geom, s);
+}
+mf_status launch_layout(const mf_operator* op, int elem, int mode, const void* in, void* out, cudaStream_t s) {
+  MF_DISPATCH_N(op->n, layout_n, op, elem, mode, in, out, s);
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+} // namespace mf
+
+using namespace mf;
+
+extern "C" {
+
+const char* mf_last_error(void) { return g_err; }
+
+mf_status mf_mesh_create(int nx, int ny, int nz, int geometry, const double* affine_3x4, double curve_amp,
+                         mf_mesh** out) {
+  if (!out) return set_error(MF_ERR_ARG, "mf_mesh_create: out is NULL");
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1) return set_error(MF_ERR_ARG, "mf_mesh_create: cell counts must be >= 1");
+  if ((long long)nx * ny * nz > (1LL << 31)) return set_error(MF_ERR_ARG, "mf_mesh_create: too many cells");
+  if (geometry != MF_AFFINE && geometry != MF_CURVED_SIN)
+    return set_error(MF_ERR_ARG, "mf_mesh_create: unknown geometry %d", geometry);
+  mf_mesh* m = new (std::nothrow) mf_mesh;
+  if (!m) return set_error(MF_ERR_OOM, "mf_mesh_create: host allocation failed");
+  m->nx = nx; m->ny = ny; m->nz = nz; m->geom = geometry; m->amp = curve_amp;
+  for (int i = 0; i < 9; ++i) m->A[i] = (i % 4 == 0) ? 1.0 : 0.0;
+  for (int i = 0; i < 3; ++i) m->b[i] = 0.0;
+  if (geometry == MF_AFFINE && affine_3x4) {
+    for (int i = 0; i < 9; ++i) m->A[i] = affine_3x4[i];
+    for (int i = 0; i < 3; ++i) m->b[i] = affine_3x4[9 + i];
+  }
+  if (geometry == MF_CURVED_SIN) {
+    // det of the map is 1 + amp*pi*(c s s + s c s + s s c) >= 1 - amp*pi*sqrt(3)*... ; require
+    // a strictly positive Jacobian everywhere: |amp| * pi * 3 < 1 is sufficient.
+    if (!(std::fabs(curve_amp) * M_PI * 3.0 < 1.0)) {
+      delete m;
+      return set_error(MF_ERR_ARG, "mf_mesh_create: curve_amp %g may fold the mesh", curve_amp);
+    }
+  }
+  *out = m;
+  return MF_OK;
+}
+
+void mf_mesh_destroy(mf_mesh* mesh) { delete mesh; }
+
+mf_status mf_operator_create(const mf_mesh* mesh, int degree, int kind, double mass_coeff, int precision, int bc,
+                             mf_operator** out) {
+  if (!out || !mesh) return set_error(MF_ERR_ARG, "mf_operator_create: NULL argument");
+  *out = nullptr;
+  if (degree < 1 || degree > 8) return set_error(MF_ERR_ARG, "mf_operator_create: degree %d not in 1..8", degree);
+  if (kind != MF_LAPLACE && kind != MF_HELMHOLTZ) return set_error(MF_ERR_ARG, "mf_operator_create: kind %d", kind);
+  if (precision != MF_FP64 && precision != MF_FP32 && precision != MF_MIXED)
+    return set_error(MF_ERR_ARG, "mf_operator_create: precision %d", precision);
+  if (bc != MF_BC_NONE && bc != MF_BC_DIRICHLET0) return set_error(MF_ERR_ARG, "mf_operator_create: bc %d", bc);
+  mf_operator* op = new (std::nothrow) mf_operator;
+  if (!op) return set_error(MF_ERR_OOM, "mf_operator_create: host allocation failed");
+  op->mesh = *mesh;
+  op->degree = degree;
+  op->n = degree + 1;
+  op->kind = kind;
+  op->mass = (kind == MF_HELMHOLTZ) ? mass_coeff : 0.0;
+  op->precision = precision;
+  op->bc = bc;
+  if (make_host_tables(degree, &op->tab)) {
+    delete op;
+    return set_error(MF_ERR_ARG, "mf_operator_create: table construction failed");
+  }
+  GridInfo& g = op->g;
+  g.nx = mesh->nx; g.ny = mesh->ny; g.nz = mesh->nz;
+  g.ntx = (g.nx + TX - 1) / TX; g.nty = (g.ny + TY - 1) / TY; g.ntz = (g.nz + TZ - 1) / TZ;
+  g.ntiles = (long long)g.ntx * g.nty * g.ntz;
+  g.bc = bc;
+  const long long n3 = (long long)op->n * op->n * op->n;
+  op->n_cellwise = (long long)g.nx * g.ny * g.nz * n3;
+  op->n_unique = (long long)(g.nx * degree + 1) * (g.ny * degree + 1) * (g.nz * degree + 1);
+  op->n_native = g.ntiles * n3 * BL;
+  // affine constants: J = A diag(1/nx, 1/ny, 1/nz) is the same on every cell
+  for (int m = 0; m < 6; ++m) op->G[m] = 0.0;
+  op->mdet = op->gx = op->gy = op->gz = op->cmass = 0.0;
+  if (mesh->geom == MF_AFFINE) {
+    double J[9];
+    const double h[3] = {1.0 / g.nx, 1.0 / g.ny, 1.0 / g.nz};
+    for (int r = 0; r < 3; ++r)
+      for (int d = 0; d < 3; ++d) J[3 * r + d] = mesh->A[3 * r + d] * h[d];
+    const double det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+                       J[2] * (J[3] * J[7] - J[4] * J[6]);
+    if (!(std::fabs(det) > 0.0)) {
+      delete op;
+      return set_error(MF_ERR_ARG, "mf_operator_create: singular affine map");
+    }
+    double Ji[9];
+    Ji[0] = (J[4] * J[8] - J[5] * J[7]) / det; Ji[1] = (J[2] * J[7] - J[1] * J[8]) / det;
+    Ji[2] = (J[1] * J[5] - J[2] * J[4]) / det; Ji[3] = (J[5] * J[6] - J[3] * J[8]) / det;
+    Ji[4] = (J[0] * J[8] - J[2] * J[6]) / det; Ji[5] = (J[2] * J[3] - J[0] * J[5]) / det;
+    Ji[6] = (J[3] * J[7] - J[4] * J[6]) / det; Ji[7] = (J[1] * J[6] - J[0] * J[7]) / det;
+    Ji[8] = (J[0] * J[4] - J[1] * J[3]) / det;
+    const int pr[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    const double ad = std::fabs(det);
+    for (int m = 0; m < 6; ++m) {
+      const int r = pr[m][0], s = pr[m][1];
+      op->G[m] = ad * (Ji[3 * r] * Ji[3 * s] + Ji[3 * r + 1] * Ji[3 * s + 1] + Ji[3 * r + 2] * Ji[3 * s + 2]);
+    }
+    op->mdet = op->mass * ad;
+    const bool diag = J[1] == 0.0 && J[2] == 0.0 && J[3] == 0.0 && J[5] == 0.0 && J[6] == 0.0 && J[7] == 0.0;
+    if (diag) {
+      op->path = PATH_CARTESIAN;
+      op->gx = op->G[0]; op->gy = op->G[3]; op->gz = op->G[5];
+      op->cmass = op->mdet;
+    } else {
+      op->path = PATH_AFFINE;
+    }
+  } else {
+    op->path = PATH_CURVED;
+  }
+  const size_t npts = (size_t)op->n_native; // points per tile equal dofs per tile
+  op->v64.elem_bytes = 8;
+  op->v32.elem_bytes = 4;
+  if (op->path == PATH_CURVED) {
+    const size_t comps = (size_t)geom_comps(op);
+    op->v64.geom_bytes = (precision == MF_FP32) ? 0 : comps * npts * 8;
+    op->v32.geom_bytes = (precision == MF_FP64) ? 0 : comps * npts * 4;
+  }
+  *out = op;
+  return MF_OK;
+}
+
+void mf_operator_destroy(mf_operator* op) { delete op; }
+
+mf_status mf_operator_info(const mf_operator* op, mf_info* info) {
+  if (!op || !info) return set_error(MF_ERR_ARG, "mf_operator_info: NULL argument");
+  std::memset(info, 0, sizeof(*info));
+  info->n_cellwise = op->n_cellwise;
+  info->n_unique = op->n_unique;
+  info->n_native = op->n_native;
+  info->n_cells = (long long)op->g.nx * op->g.ny * op->g.nz;
+  info->degree = op->degree;
+  info->n = op->n;
+  info->elem_bytes = (op->precision == MF_FP32) ? 4 : 8;
+  info->path = op->path;
+  info->geom_bytes = op->v64.geom_bytes + op->v32.geom_bytes;
+  info->workspace_bytes = align256(op->v64.geom_bytes) + align256(op->v32.geom_bytes) + 256;
+  const double e = info->elem_bytes;
+  double per_dof = 2.0 * e;
+  if (op->path == PATH_CURVED) per_dof += geom_comps(op) * e;
+  info->algorithmic_bytes_per_apply = per_dof * (double)op->n_cellwise;
+  return MF_OK;
+}
+
+mf_status mf_operator_setup(mf_operator* op, void* workspace_dev, size_t bytes, void* stream) {
+  if (!op) return set_error(MF_ERR_ARG, "mf_operator_setup: NULL operator");
+  mf_info info;
+  mf_operator_info(op, &info);
+  if (info.workspace_bytes > 256 && (!workspace_dev || bytes < info.workspace_bytes))
+    return set_error(MF_ERR_OOM, "mf_operator_setup: workspace of %zu bytes < %zu", bytes, info.workspace_bytes);
+  if (workspace_dev && (reinterpret_cast<uintptr_t>(workspace_dev) & 255))
+    return set_error(MF_ERR_ARG, "mf_operator_setup: workspace not 256-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(workspace_dev);
+  op->v64.geom = nullptr;
+  op->v32.geom = nullptr;
+  if (op->v64.geom_bytes) { op->v64.geom = w; w += align256(op->v64.geom_bytes); }
+  if (op->v32.geom_bytes) { op->v32.geom = w; w += align256(op->v32.geom_bytes); }
+  op->workspace = workspace_dev;
+  op->workspace_bytes = bytes;
+  if (op->path == PATH_CURVED) {
+    if (op->v64.geom) { mf_status st = launch_geometry(op, 8, op->v64.geom, s); if (st) return st; }
+    if (op->v32.geom) { mf_status st = launch_geometry(op, 4, op->v32.geom, s); if (st) return st; }
+  }
+  op->ready = true;
+  return MF_OK;
+}
+
+static mf_status check_ready(const mf_operator* op, const char* who) {
+  if (!op) return set_error(MF_ERR_ARG, "%s: NULL operator", who);
+  if (!op->ready) return set_error(MF_ERR_ARG, "%s: operator not set up (mf_operator_setup)", who);
+  return MF_OK;
+}
+
+static int elem_of(const mf_operator* op) { return op->precision == MF_FP32 ? 4 : 8; }
+
+mf_status mf_to_native(const mf_operator* op, const void* canonical_dev, void* native_dev, void* stream) {
+  if (!op || !canonical_dev || !native_dev) return set_error(MF_ERR_ARG, "mf_to_native: NULL argument");
+  return launch_layout(op, elem_of(op), LAYOUT_TO_NATIVE, canonical_dev, native_dev, static_cast<cudaStream_t>(stream));
+}
+mf_status mf_from_native(const mf_operator* op, const void* native_dev, void* canonical_dev, void* stream) {
+  if (!op || !canonical_dev || !native_dev) return set_error(MF_ERR_ARG, "mf_from_native: NULL argument");
+  return launch_layout(op, elem_of(op), LAYOUT_FROM_NATIVE, native_dev, canonical_dev, static_cast<cudaStream_t>(stream));
+}
+mf_status mf_scatter_unique(const mf_operator* op, const void* unique_dev, void* native_dev, void* stream) {
+  if (!op || !unique_dev || !native_dev) return set_error(MF_ERR_ARG, "mf_scatter_unique: NULL argument");
+  return launch_layout(op, elem_of(op), LAYOUT_SCATTER_UNIQUE, unique_dev, native_dev, static_cast<cudaStream_t>(stream));
+}
+mf_status mf_gather_unique(const mf_operator* op, const void* native_dev, void* unique_dev, void* stream) {
+  if (!op || !unique_dev || !native_dev) return set_error(MF_ERR_ARG, "mf_gather_unique: NULL argument");
+  return launch_layout(op, elem_of(op), LAYOUT_GATHER_UNIQUE, native_dev, unique_dev, static_cast<cudaStream_t>(stream));
+}
+
+mf_status mf_apply_split(const mf_operator* op, const void* x_dev, void* y_dev, void* stream) {
+  mf_status st = check_ready(op, "mf_apply_split");
+  if (st) return st;
+  if (!x_dev || !y_dev || x_dev == y_dev) return set_error(MF_ERR_ARG, "mf_apply_split: bad vectors");
+  return launch_apply_split(op, elem_of(op), x_dev, y_dev, static_cast<cudaStream_t>(stream));
+}
+
+mf_status mf_dss(const mf_operator* op, void* y_dev, void* stream) {
+  if (!op || !y_dev) return set_error(MF_ERR_ARG, "mf_dss: NULL argument");
+  return launch_dss(op, elem_of(op), y_dev, static_cast<cudaStream_t>(stream));
+}
+
+mf_status mf_apply(const mf_operator* op, const void* x_dev, void* y_dev, void* stream) {
+  mf_status st = mf_apply_split(op, x_dev, y_dev, stream);
+  if (st) return st;
+  return launch_dss(op, elem_of(op), y_dev, static_cast<cudaStream_t>(stream));
+}
+
+size_t mf_apply_host_workspace_bytes(const mf_operator* op) {
+  if (!op) return 0;
+  const size_t e = (size_t)elem_of(op);
+  return 2 * align256((size_t)op->n_native * e) + align256((size_t)op->n_cellwise * e);
+}
+
+mf_status mf_apply_host(const mf_operator* op, const void* x_host, void* y_host, void* workspace_dev, size_t bytes,
+                        void* stream) {
+  mf_status st = check_ready(op, "mf_apply_host");
+  if (st) return st;
+  if (!x_host || !y_host) return set_error(MF_ERR_ARG, "mf_apply_host: NULL host buffer");
+  const size_t need = mf_apply_host_workspace_bytes(op);
+  if (!workspace_dev || bytes < need) return set_error(MF_ERR_OOM, "mf_apply_host: workspace %zu < %zu", bytes, need);
+  const size_t e = (size_t)elem_of(op);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(workspace_dev);
+  void* xn = w;
+  void* yn = w + align256((size_t)op->n_native * e);
+  void* can = w + 2 * align256((size_t)op->n_native * e);
+  const size_t cbytes = (size_t)op->n_cellwise * e;
+  if ((st = cuda_check(cudaMemcpyAsync(can, x_host, cbytes, cudaMemcpyHostToDevice, s), "mf_apply_host H2D"))) return st;
+  if ((st = mf_to_native(op, can, xn, stream))) return st;
+  if ((st = mf_apply(op, xn, yn, stream))) return st;
+  if ((st = mf_from_native(op, yn, can, stream))) return st;
+  if ((st = cuda_check(cudaMemcpyAsync(y_host, can, cbytes, cudaMemcpyDeviceToHost, s), "mf_apply_host D2H"))) return st;
+  return cuda_check(cudaStreamSynchronize(s), "mf_apply_host sync");
+}
+
+} // extern "C"

@@ -1,0 +1,581 @@
+// mf_cg.cu -- deterministic reductions, fused CG vector kernels and the CG / defect-correction
+// drivers.
+//
+// CG structure (Sec. 4, "the Krylov loop on split data" and the pairing of Lemma 1): the
+// iterate x and search direction p are consistent cell-wise vectors; every scalar is an
+// inner product of two cell-wise vectors taken so that each global node counts once (copies
+// weighted by 1/multiplicity, a power of two, so the weighting is exact).  With z = r (no
+// preconditioner) the monitored quantity <r, z>^{1/2} is the assembled Euclidean residual
+// norm.  Reductions run in FP64 in a fixed order (block tree, then the last block sums the
+// block partials in index order), so every scalar is bitwise reproducible.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "mf_internal.h"
+
+namespace mf {
+
+constexpr int RED_THREADS = 256;
+constexpr int RED_MAX_BLOCKS = 2048;
+constexpr int HIST_CAP = 65536;
+
+// Scratch of one reduction: a done-counter and the block partials.
+struct RedScratch {
+  unsigned int counter;
+  unsigned int pad[63];
+  double partial[RED_MAX_BLOCKS];
+};
+
+size_t reduce_scratch_bytes() { return sizeof(RedScratch); }
+
+// Device-resident CG scalars.
+struct CgState {
+  double rr;      // <r, r> (assembled)
+  double pq;      // <p, A p>
+  double alpha, beta;
+  double bnorm;   // ||b||
+  double tol2;    // (rtol * ||b||)^2
+  int it;         // iterations done
+  int flag;       // 0 running, 1 converged, 2 breakdown
+  int maxit;
+  int pad;
+};
+
+// Weight of native element e in an assembled inner product: 0 for padding, otherwise
+// 1 / (number of cells sharing the node).  split = 1: 1 for every real copy.
+template <int N>
+__device__ __forceinline__ double node_weight(const GridInfo& g, long long e, int split) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  const int lane = (int)(e & (BL - 1));
+  const long long row = e >> 5;
+  const int l = (int)(row % N3);
+  const long long t = row / N3;
+  const long long txy = (long long)g.ntx * g.nty;
+  const int tz = (int)(t / txy);
+  const long long r = t - (long long)tz * txy;
+  const int ty = (int)(r / g.ntx);
+  const int tx = (int)(r - (long long)ty * g.ntx);
+  const int cx = tx * TX + (lane & 3), cy = ty * TY + ((lane >> 2) & 3), cz = tz * TZ + (lane >> 4);
+  if (cx >= g.nx || cy >= g.ny || cz >= g.nz) return 0.0;
+  if (split) return 1.0;
+  const int i = l % N, j = (l / N) % N, k = l / N2;
+  const int m = (((i == 0 && cx > 0) || (i == N - 1 && cx < g.nx - 1)) ? 2 : 1) *
+                (((j == 0 && cy > 0) || (j == N - 1 && cy < g.ny - 1)) ? 2 : 1) *
+                (((k == 0 && cz > 0) || (k == N - 1 && cz < g.nz - 1)) ? 2 : 1);
+  return 1.0 / m;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block tree sum; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double ws[RED_THREADS / 32];
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  if (ln == 0) ws[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (w == 0) {
+    s = (ln < RED_THREADS / 32) ? ws[ln] : 0.0;
+    s = warp_sum(s);
+  }
+  __syncthreads();
+  return s;
+}
+
+// Called by every thread of every block after the block partial is known.  Returns true
+// in thread 0 of the last block to finish, with *total = sum of partials in index order.
+__device__ __forceinline__ bool last_block_total(RedScratch* sc, double part, double* total) {
+  __shared__ bool am_last;
+  if (threadIdx.x == 0) {
+    sc->partial[blockIdx.x] = part;
+    __threadfence();
+    const unsigned prev = atomicAdd(&sc->counter, 1u);
+    am_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  double s = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += RED_THREADS) s += ((volatile double*)sc->partial)[b];
+  s = block_sum(s);
+  if (threadIdx.x == 0) {
+    sc->counter = 0; // self-cleaning for the next launch
+    *total = s;
+  }
+  return threadIdx.x == 0;
+}
+
+static int red_blocks(long long n) {
+  long long b = (n + (long long)RED_THREADS * 8 - 1) / ((long long)RED_THREADS * 8);
+  if (b < 1) b = 1;
+  if (b > RED_MAX_BLOCKS) b = RED_MAX_BLOCKS;
+  return (int)b;
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(RED_THREADS) dot_kernel(const T* __restrict__ a, const T* __restrict__ b, long long n,
+                                                          GridInfo g, int split, RedScratch* sc, double* out) {
+  double s = 0.0;
+  for (long long e = blockIdx.x * (long long)RED_THREADS + threadIdx.x; e < n; e += (long long)gridDim.x * RED_THREADS)
+    s += node_weight<N>(g, e, split) * ((double)a[e] * (double)b[e]);
+  s = block_sum(s);
+  double tot;
+  if (last_block_total(sc, s, &tot)) *out = tot;
+}
+
+// alpha = rr / <p, q>
+template <typename T, int N>
+__global__ void __launch_bounds__(RED_THREADS) cg_pq_kernel(const T* __restrict__ p, const T* __restrict__ q, long long n,
+                                                            GridInfo g, RedScratch* sc, CgState* st) {
+  double s = 0.0;
+  for (long long e = blockIdx.x * (long long)RED_THREADS + threadIdx.x; e < n; e += (long long)gridDim.x * RED_THREADS)
+    s += node_weight<N>(g, e, 0) * ((double)p[e] * (double)q[e]);
+  s = block_sum(s);
+  double tot;
+  if (last_block_total(sc, s, &tot)) {
+    if (st->flag == 0) {
+      st->pq = tot;
+      if (!(tot > 0.0) || !isfinite(tot)) { st->flag = 2; st->alpha = 0.0; }
+      else st->alpha = st->rr / tot;
+    } else {
+      st->alpha = 0.0;
+    }
+  }
+}
+
+// x += alpha p ; r -= alpha q ; rr_new = <r, r> ; beta = rr_new / rr
+template <typename T, int N>
+__global__ void __launch_bounds__(RED_THREADS) cg_xr_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                                                            const T* __restrict__ q, long long n, GridInfo g,
+                                                            RedScratch* sc, CgState* st, double* hist) {
+  const double al = st->alpha;
+  const bool run = st->flag == 0;
+  double s = 0.0;
+  for (long long e = blockIdx.x * (long long)RED_THREADS + threadIdx.x; e < n; e += (long long)gridDim.x * RED_THREADS) {
+    T rv = r[e];
+    if (run) {
+      x[e] = (T)((double)x[e] + al * (double)p[e]);
+      rv = (T)((double)rv - al * (double)q[e]);
+      r[e] = rv;
+    }
+    s += node_weight<N>(g, e, 0) * ((double)rv * (double)rv);
+  }
+  s = block_sum(s);
+  double tot;
+  if (last_block_total(sc, s, &tot)) {
+    if (st->flag == 0) {
+      st->beta = tot / st->rr;
+      st->rr = tot;
+      st->it += 1;
+      if (hist && st->it < HIST_CAP) hist[st->it] = sqrt(tot) / st->bnorm;
+      if (tot <= st->tol2) st->flag = 1;
+      else if (!isfinite(tot)) st->flag = 2;
+      else if (st->it >= st->maxit) st->flag = 3;
+    } else {
+      st->beta = 0.0;
+    }
+  }
+}
+
+// p = r + beta p
+template <typename T>
+__global__ void cg_p_kernel(const T* __restrict__ r, T* __restrict__ p, long long n, const CgState* st, int was_running) {
+  (void)was_running;
+  const double be = st->beta;
+  if (st->flag != 0 && st->flag != 1) return;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    p[e] = (T)((double)r[e] + be * (double)p[e]);
+}
+
+// Small element-wise kernels of the drivers.
+template <typename T>
+__global__ void copy_kernel(const T* __restrict__ a, T* __restrict__ b, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) b[e] = a[e];
+}
+template <typename T>
+__global__ void zero_kernel(T* __restrict__ a, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) a[e] = T(0);
+}
+// r = b - q (FP64)
+__global__ void sub_kernel(const double* __restrict__ b, const double* __restrict__ q, double* __restrict__ r, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) r[e] = b[e] - q[e];
+}
+// r32 = r64 * scale
+__global__ void to32_kernel(const double* __restrict__ r, float* __restrict__ o, const double* rn2, long long n) {
+  const double sc = (*rn2 > 0.0) ? 1.0 / sqrt(*rn2) : 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) o[e] = (float)(r[e] * sc);
+}
+// x += sqrt(rn2) * d
+__global__ void axpy64_kernel(double* __restrict__ x, const float* __restrict__ d, const double* rn2, long long n) {
+  const double sc = sqrt(*rn2);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) x[e] += sc * (double)d[e];
+}
+// Dirichlet mask P b (zero constrained copies) -- used on the right-hand side
+template <typename T, int N>
+__global__ void mask_kernel(const T* __restrict__ b, T* __restrict__ o, long long n, GridInfo g) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int lane = (int)(e & (BL - 1));
+    const long long row = e >> 5;
+    const int l = (int)(row % N3);
+    const long long t = row / N3;
+    const long long txy = (long long)g.ntx * g.nty;
+    const int tz = (int)(t / txy);
+    const long long rr = t - (long long)tz * txy;
+    const int ty = (int)(rr / g.ntx), tx = (int)(rr - (long long)ty * g.ntx);
+    const int cx = tx * TX + (lane & 3), cy = ty * TY + ((lane >> 2) & 3), cz = tz * TZ + (lane >> 4);
+    const int i = l % N, j = (l / N) % N, k = l / N2;
+    const bool valid = cx < g.nx && cy < g.ny && cz < g.nz;
+    const bool bnd = g.bc && ((cx == 0 && i == 0) || (cx == g.nx - 1 && i == N - 1) || (cy == 0 && j == 0) ||
+                              (cy == g.ny - 1 && j == N - 1) || (cz == 0 && k == 0) || (cz == g.nz - 1 && k == N - 1));
+    o[e] = (valid && !bnd) ? b[e] : T(0);
+  }
+}
+
+static unsigned ew_blocks(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+// ------------------------------------------------------------------ typed dispatch helpers
+template <int N>
+static mf_status dot_n(const mf_operator* op, int elem, const void* a, const void* b, int split, double* out,
+                       RedScratch* sc, cudaStream_t s) {
+  const long long n = op->n_native;
+  const int bl = red_blocks(n);
+  if (elem == 8)
+    dot_kernel<double, N><<<bl, RED_THREADS, 0, s>>>((const double*)a, (const double*)b, n, op->g, split, sc, out);
+  else
+    dot_kernel<float, N><<<bl, RED_THREADS, 0, s>>>((const float*)a, (const float*)b, n, op->g, split, sc, out);
+  return cuda_check(cudaGetLastError(), "dot launch");
+}
+
+#define MF_SWITCH_N(n, fn, ...)                                          \
+  switch (n) {                                                           \
+    case 2: return fn<2>(__VA_ARGS__);                                   \
+    case 3: return fn<3>(__VA_ARGS__);                                   \
+    case 4: return fn<4>(__VA_ARGS__);                                   \
+    case 5: return fn<5>(__VA_ARGS__);                                   \
+    case 6: return fn<6>(__VA_ARGS__);                                   \
+    case 7: return fn<7>(__VA_ARGS__);                                   \
+    case 8: return fn<8>(__VA_ARGS__);                                   \
+    case 9: return fn<9>(__VA_ARGS__);                                   \
+    default: return set_error(MF_ERR_UNSUPPORTED, "n=%d not built", n);  \
+  }
+
+mf_status dot_launch(const mf_operator* op, int elem, const void* a, const void* b, int split, double* out, void* scratch,
+                     cudaStream_t s) {
+  MF_SWITCH_N(op->n, dot_n, op, elem, a, b, split, out, (RedScratch*)scratch, s);
+}
+
+template <typename T, int N>
+static mf_status mask_n(const mf_operator* op, const void* b, void* o, cudaStream_t s) {
+  const long long n = op->n_native;
+  mask_kernel<T, N><<<ew_blocks(n), 256, 0, s>>>((const T*)b, (T*)o, n, op->g);
+  return cuda_check(cudaGetLastError(), "mask launch");
+}
+template <int N>
+static mf_status mask_e(const mf_operator* op, int elem, const void* b, void* o, cudaStream_t s) {
+  return elem == 8 ? mask_n<double, N>(op, b, o, s) : mask_n<float, N>(op, b, o, s);
+}
+static mf_status launch_mask(const mf_operator* op, int elem, const void* b, void* o, cudaStream_t s) {
+  MF_SWITCH_N(op->n, mask_e, op, elem, b, o, s);
+}
+
+// One CG iteration's vector kernels (after q = A p).
+template <typename T, int N>
+static mf_status cg_vec_n(const mf_operator* op, T* x, T* r, T* p, T* q, RedScratch* sc1, RedScratch* sc2, CgState* st,
+                          double* hist, cudaStream_t s) {
+  const long long n = op->n_native;
+  const int bl = red_blocks(n);
+  cg_pq_kernel<T, N><<<bl, RED_THREADS, 0, s>>>(p, q, n, op->g, sc1, st);
+  cg_xr_kernel<T, N><<<bl, RED_THREADS, 0, s>>>(x, r, p, q, n, op->g, sc2, st, hist);
+  cg_p_kernel<T><<<ew_blocks(n), 256, 0, s>>>(r, p, n, st, 1);
+  return cuda_check(cudaGetLastError(), "cg vector launch");
+}
+template <int N>
+static mf_status cg_vec_e(const mf_operator* op, int elem, void* x, void* r, void* p, void* q, RedScratch* sc1,
+                          RedScratch* sc2, CgState* st, double* hist, cudaStream_t s) {
+  if (elem == 8) return cg_vec_n<double, N>(op, (double*)x, (double*)r, (double*)p, (double*)q, sc1, sc2, st, hist, s);
+  return cg_vec_n<float, N>(op, (float*)x, (float*)r, (float*)p, (float*)q, sc1, sc2, st, hist, s);
+}
+static mf_status launch_cg_vec(const mf_operator* op, int elem, void* x, void* r, void* p, void* q, RedScratch* sc1,
+                               RedScratch* sc2, CgState* st, double* hist, cudaStream_t s) {
+  MF_SWITCH_N(op->n, cg_vec_e, op, elem, x, r, p, q, sc1, sc2, st, hist, s);
+}
+
+// apply + duplicate summation with a given element type (selects the FP64 or FP32 view)
+static mf_status apply_elem(const mf_operator* op, int elem, const void* x, void* y, cudaStream_t s) {
+  mf_status st = launch_apply_split(op, elem, x, y, s);
+  if (st) return st;
+  return launch_dss(op, elem, y, s);
+}
+
+static size_t a256(size_t b) { return (b + 255) & ~size_t(255); }
+
+static thread_local double* g_hist_host = nullptr;
+static thread_local int g_hist_cap = 0;
+
+// Workspace layout of a solve.
+struct SolveWs {
+  CgState* st;
+  RedScratch *sc1, *sc2, *sc3;
+  double* hist;
+  double* scal; // misc FP64 scalars (residual norms)
+  void *r, *p, *q;          // CG vectors of the (inner) element type
+  void *r64, *q64, *b64;    // mixed: FP64 outer residual, A x, masked b
+  void* d32;                // mixed: inner solution
+};
+
+static size_t layout_ws(const mf_operator* op, int mixed, char* base, SolveWs* w) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* { char* p = base ? base + off : nullptr; off += a256(bytes); return p; };
+  const size_t n = (size_t)op->n_native;
+  const int elem = mixed ? 4 : (op->precision == MF_FP32 ? 4 : 8);
+  SolveWs t;
+  t.st = (CgState*)take(sizeof(CgState));
+  t.sc1 = (RedScratch*)take(sizeof(RedScratch));
+  t.sc2 = (RedScratch*)take(sizeof(RedScratch));
+  t.sc3 = (RedScratch*)take(sizeof(RedScratch));
+  t.hist = (double*)take(sizeof(double) * HIST_CAP);
+  t.scal = (double*)take(sizeof(double) * 16);
+  t.r = take(n * elem);
+  t.p = take(n * elem);
+  t.q = take(n * elem);
+  t.r64 = t.q64 = t.b64 = t.d32 = nullptr;
+  if (mixed) {
+    t.r64 = take(n * 8);
+    t.q64 = take(n * 8);
+    t.b64 = take(n * 8);
+    t.d32 = take(n * 4);
+  }
+  if (w) *w = t;
+  return off;
+}
+
+// Inner/plain CG: solves A x = rhs (rhs already masked) from x = 0 with vectors of `elem`.
+// Uses a CUDA graph of `chunk` iterations, reads the scalars back after each graph.
+static mf_status run_cg(const mf_operator* op, int elem, const void* rhs, void* x, double rtol, int maxit,
+                        const SolveWs& w, cudaStream_t s, int* iters_out, double* relres_out, int record,
+                        int* hist_off) {
+  mf_status st;
+  const long long n = op->n_native;
+  // x = 0, r = rhs, p = rhs, rr = <r, r>
+  if (elem == 8) {
+    zero_kernel<double><<<ew_blocks(n), 256, 0, s>>>((double*)x, n);
+    copy_kernel<double><<<ew_blocks(n), 256, 0, s>>>((const double*)rhs, (double*)w.r, n);
+    copy_kernel<double><<<ew_blocks(n), 256, 0, s>>>((const double*)rhs, (double*)w.p, n);
+  } else {
+    zero_kernel<float><<<ew_blocks(n), 256, 0, s>>>((float*)x, n);
+    copy_kernel<float><<<ew_blocks(n), 256, 0, s>>>((const float*)rhs, (float*)w.r, n);
+    copy_kernel<float><<<ew_blocks(n), 256, 0, s>>>((const float*)rhs, (float*)w.p, n);
+  }
+  if ((st = cuda_check(cudaGetLastError(), "cg init"))) return st;
+  if ((st = cuda_check(cudaMemsetAsync(w.sc1, 0, sizeof(unsigned) * 64, s), "memset"))) return st;
+  if ((st = cuda_check(cudaMemsetAsync(w.sc2, 0, sizeof(unsigned) * 64, s), "memset"))) return st;
+  if ((st = cuda_check(cudaMemsetAsync(w.sc3, 0, sizeof(unsigned) * 64, s), "memset"))) return st;
+  if ((st = dot_launch(op, elem, w.r, w.r, 0, w.scal, w.sc3, s))) return st;
+  double rr0 = 0.0;
+  if ((st = cuda_check(cudaMemcpyAsync(&rr0, w.scal, sizeof(double), cudaMemcpyDeviceToHost, s), "D2H"))) return st;
+  if ((st = cuda_check(cudaStreamSynchronize(s), "sync"))) return st;
+  if (!std::isfinite(rr0)) return set_error(MF_ERR_BREAKDOWN, "CG: non-finite right-hand side");
+  CgState h;
+  std::memset(&h, 0, sizeof(h));
+  h.rr = rr0;
+  h.bnorm = std::sqrt(rr0);
+  h.tol2 = (rtol * h.bnorm) * (rtol * h.bnorm);
+  h.maxit = maxit;
+  h.flag = (rr0 <= h.tol2 || rr0 == 0.0) ? 1 : 0;
+  if ((st = cuda_check(cudaMemcpyAsync(w.st, &h, sizeof(h), cudaMemcpyHostToDevice, s), "H2D"))) return st;
+  const int chunk = 20;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  int done_flag = h.flag;
+  int it = 0;
+  while (done_flag == 0) {
+    if (!exec) {
+      if ((st = cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture begin"))) return st;
+      mf_status cst = MF_OK;
+      for (int c = 0; c < chunk && cst == MF_OK; ++c) {
+        cst = apply_elem(op, elem, w.p, w.q, s);
+        if (cst == MF_OK) cst = launch_cg_vec(op, elem, x, w.r, w.p, w.q, w.sc1, w.sc2, w.st, w.hist, s);
+      }
+      cudaError_t e = cudaStreamEndCapture(s, &graph);
+      if (cst) { if (graph) cudaGraphDestroy(graph); return cst; }
+      if ((st = cuda_check(e, "capture end"))) return st;
+      if ((st = cuda_check(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate"))) { cudaGraphDestroy(graph); return st; }
+    }
+    if ((st = cuda_check(cudaGraphLaunch(exec, s), "graph launch"))) break;
+    if ((st = cuda_check(cudaMemcpyAsync(&h, w.st, sizeof(h), cudaMemcpyDeviceToHost, s), "D2H"))) break;
+    if ((st = cuda_check(cudaStreamSynchronize(s), "sync"))) break;
+    done_flag = h.flag;
+    it = h.it;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (st) return st;
+  it = h.it;
+  if (record && g_hist_host && hist_off) {
+    // hist[1..it] = relative residual per iteration of this run
+    int take = it;
+    if (take > HIST_CAP - 1) take = HIST_CAP - 1;
+    if (*hist_off + take + 1 > g_hist_cap) take = g_hist_cap - *hist_off - 1;
+    if (take > 0) {
+      st = cuda_check(cudaMemcpy(g_hist_host + *hist_off + 1, w.hist + 1, sizeof(double) * take, cudaMemcpyDeviceToHost), "hist D2H");
+      if (st) return st;
+    }
+    if (*hist_off < g_hist_cap) g_hist_host[*hist_off] = 1.0;
+    *hist_off += take + 1;
+  }
+  *iters_out = it;
+  *relres_out = (h.bnorm > 0) ? std::sqrt(h.rr) / h.bnorm : 0.0;
+  if (h.flag == 2) return set_error(MF_ERR_BREAKDOWN, "CG breakdown (p^T A p <= 0 or non-finite) at iteration %d", it);
+  if (h.flag == 3) return MF_ERR_NOT_CONVERGED;
+  return MF_OK;
+}
+
+} // namespace mf
+
+using namespace mf;
+
+extern "C" {
+
+size_t mf_reduce_workspace_bytes(const mf_operator* op) { return op ? sizeof(RedScratch) : 0; }
+
+mf_status mf_dot(const mf_operator* op, const void* a_dev, const void* b_dev, int split, double* result_dev,
+                 void* scratch_dev, size_t scratch_bytes, void* stream) {
+  if (!op || !a_dev || !b_dev || !result_dev) return set_error(MF_ERR_ARG, "mf_dot: NULL argument");
+  if (!scratch_dev || scratch_bytes < sizeof(RedScratch))
+    return set_error(MF_ERR_OOM, "mf_dot: scratch %zu < %zu bytes", scratch_bytes, sizeof(RedScratch));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  mf_status st = cuda_check(cudaMemsetAsync(scratch_dev, 0, sizeof(unsigned) * 64, s), "mf_dot memset");
+  if (st) return st;
+  return dot_launch(op, op->precision == MF_FP32 ? 4 : 8, a_dev, b_dev, split ? 1 : 0, result_dev, scratch_dev, s);
+}
+
+mf_status mf_cg_record_history(double* hist_host, int cap) {
+  g_hist_host = hist_host;
+  g_hist_cap = hist_host ? cap : 0;
+  return MF_OK;
+}
+
+size_t mf_cg_workspace_bytes(const mf_operator* op, int mixed) {
+  if (!op) return 0;
+  return layout_ws(op, mixed ? 1 : 0, nullptr, nullptr);
+}
+
+mf_status mf_cg_solve(const mf_operator* op, const void* b_dev, void* x_dev, double rtol, int maxit, int mixed,
+                      mf_solve_stats* stats, void* workspace_dev, size_t bytes, void* stream) {
+  if (!op || !b_dev || !x_dev) return set_error(MF_ERR_ARG, "mf_cg_solve: NULL argument");
+  if (!op->ready) return set_error(MF_ERR_ARG, "mf_cg_solve: operator not set up");
+  if (maxit < 0 || !(rtol >= 0.0)) return set_error(MF_ERR_ARG, "mf_cg_solve: bad rtol/maxit");
+  if (mixed && op->precision != MF_MIXED) return set_error(MF_ERR_ARG, "mf_cg_solve: mixed needs an MF_MIXED operator");
+  const size_t need = mf_cg_workspace_bytes(op, mixed);
+  if (!workspace_dev || bytes < need) return set_error(MF_ERR_OOM, "mf_cg_solve: workspace %zu < %zu", bytes, need);
+  if (reinterpret_cast<uintptr_t>(workspace_dev) & 255) return set_error(MF_ERR_ARG, "mf_cg_solve: workspace alignment");
+  // CUDA graph capture is not allowed on the legacy default stream: run on a private
+  // blocking stream (implicitly ordered with the legacy stream) when none is given.
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaStream_t own = nullptr;
+  if (s == nullptr) {
+    mf_status cs = cuda_check(cudaStreamCreateWithFlags(&own, cudaStreamDefault), "mf_cg_solve stream");
+    if (cs) return cs;
+    s = own;
+  }
+  struct StreamGuard {
+    cudaStream_t st;
+    ~StreamGuard() { if (st) { cudaStreamSynchronize(st); cudaStreamDestroy(st); } }
+  } guard{own};
+  SolveWs w;
+  layout_ws(op, mixed ? 1 : 0, static_cast<char*>(workspace_dev), &w);
+  const auto t0 = std::chrono::steady_clock::now();
+  mf_solve_stats out;
+  std::memset(&out, 0, sizeof(out));
+  out.check_every = 20;
+  mf_status st = MF_OK;
+  int hist_off = 0;
+  if (!mixed) {
+    const int elem = op->precision == MF_FP32 ? 4 : 8;
+    // rhs = P b into q (scratch), then solve
+    if ((st = launch_mask(op, elem, b_dev, w.q, s))) return st;
+    // run_cg copies rhs into r and p before touching q again
+    int it = 0;
+    double rel = 0.0;
+    st = run_cg(op, elem, w.q, x_dev, rtol, maxit, w, s, &it, &rel, 1, &hist_off);
+    out.iterations = it;
+    out.outer_iterations = 1;
+    out.rel_residual = rel;
+    if (st == MF_OK || st == MF_ERR_NOT_CONVERGED) {
+      // report the true residual ||P b - A x|| / ||P b|| in FP64 is only exact for FP64; keep recursive value
+    }
+  } else {
+    // FP64 defect correction with an FP32 inner CG (precision pattern of the solver)
+    const long long n = op->n_native;
+    double* x = static_cast<double*>(x_dev);
+    double* b = static_cast<double*>(w.b64);
+    double* r = static_cast<double*>(w.r64);
+    double* q = static_cast<double*>(w.q64);
+    if ((st = launch_mask(op, 8, b_dev, b, s))) return st;
+    zero_kernel<double><<<ew_blocks(n), 256, 0, s>>>(x, n);
+    if ((st = cuda_check(cudaMemsetAsync(w.sc3, 0, sizeof(unsigned) * 64, s), "memset"))) return st;
+    if ((st = dot_launch(op, 8, b, b, 0, w.scal + 1, w.sc3, s))) return st;
+    double bn2 = 0.0;
+    if ((st = cuda_check(cudaMemcpyAsync(&bn2, w.scal + 1, 8, cudaMemcpyDeviceToHost, s), "D2H"))) return st;
+    if ((st = cuda_check(cudaStreamSynchronize(s), "sync"))) return st;
+    if (!std::isfinite(bn2)) return set_error(MF_ERR_BREAKDOWN, "mf_cg_solve: non-finite right-hand side");
+    const double bn = std::sqrt(bn2);
+    const double inner_tol = 1e-4;
+    int total_it = 0, outer = 0;
+    double rel = bn > 0 ? 1.0 : 0.0;
+    const int max_outer = 60;
+    while (true) {
+      // r = b - A x  (FP64 apply)
+      if (outer == 0) {
+        copy_kernel<double><<<ew_blocks(n), 256, 0, s>>>(b, r, n);
+      } else {
+        if ((st = apply_elem(op, 8, x, q, s))) break;
+        sub_kernel<<<ew_blocks(n), 256, 0, s>>>(b, q, r, n);
+      }
+      // outer ||r||^2 lives in scal[2]: the inner CG uses scal[0] for its own norms
+      double* rn2_dev = w.scal + 2;
+      if ((st = dot_launch(op, 8, r, r, 0, rn2_dev, w.sc3, s))) break;
+      double rn2 = 0.0;
+      if ((st = cuda_check(cudaMemcpyAsync(&rn2, rn2_dev, 8, cudaMemcpyDeviceToHost, s), "D2H"))) break;
+      if ((st = cuda_check(cudaStreamSynchronize(s), "sync"))) break;
+      rel = bn > 0 ? std::sqrt(rn2) / bn : 0.0;
+      if (rel <= rtol || bn == 0.0) { st = MF_OK; break; }
+      if (outer >= max_outer || total_it >= maxit) { st = MF_ERR_NOT_CONVERGED; break; }
+      // inner: A32 d = r / ||r||
+      to32_kernel<<<ew_blocks(n), 256, 0, s>>>(r, static_cast<float*>(w.q), rn2_dev, n);
+      int it = 0;
+      double irel = 0.0;
+      const int inner_max = maxit - total_it;
+      mf_status ist = run_cg(op, 4, w.q, w.d32, inner_tol, inner_max, w, s, &it, &irel, 1, &hist_off);
+      total_it += it;
+      if (ist == MF_ERR_BREAKDOWN) { st = ist; break; }
+      if (ist != MF_OK && ist != MF_ERR_NOT_CONVERGED) { st = ist; break; }
+      axpy64_kernel<<<ew_blocks(n), 256, 0, s>>>(x, static_cast<const float*>(w.d32), rn2_dev, n);
+      ++outer;
+    }
+    out.iterations = total_it;
+    out.outer_iterations = outer;
+    out.rel_residual = rel;
+  }
+  cudaStreamSynchronize(s);
+  out.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  out.status = st;
+  if (stats) *stats = out;
+  if (st == MF_ERR_NOT_CONVERGED) set_error(st, "mf_cg_solve: not converged after %d iterations", out.iterations);
+  return st;
+}
+
+} // extern "C"

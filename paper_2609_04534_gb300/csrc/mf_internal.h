@@ -1,0 +1,122 @@
+// mf_internal.h -- internal types shared by the CUDA translation units of libmf.
+//
+// Native layout (the blocked [B, n_x, n_y, n_z, n_e] storage of Sec. 2, "storage layout as a
+// free parameter"): cells are grouped in tiles of BL = 32 spatially adjacent cells (a
+// TX x TY x TZ = 4 x 4 x 2 brick); inside a tile the cell lane is the fastest address, so a
+// warp reading one local DoF of 32 cells touches 32 consecutive words (the coalescing rule
+// of Sec. 6.4).  Element (tile t, local dof l, lane c) lives at (t * n^3 + l) * BL + c.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/mf.h"
+
+namespace mf {
+
+constexpr int TX = 4, TY = 4, TZ = 2, BL = TX * TY * TZ;
+constexpr int MAXN = 9;
+
+enum Path { PATH_CARTESIAN = 0, PATH_AFFINE = 1, PATH_CURVED = 2 };
+
+// Structured mesh + tile grid, passed by value to every kernel.
+struct GridInfo {
+  int nx, ny, nz;    // cells per axis
+  int ntx, nty, ntz; // tiles per axis
+  long long ntiles;
+  int bc;            // 1: homogeneous Dirichlet on the cube boundary
+};
+
+// 1D tables on the reference interval [0,1] (n = k+1):
+//   S[q][i]  = phi_i(x_q)             GLL Lagrange basis at Gauss points
+//   Dc[q][r] = psi_r'(x_q)            derivative of the Gauss-point Lagrange basis (collocation)
+//   W[q]                               Gauss weights
+//   M[i][j] = sum_q W_q S[q][i] S[q][j],  K[i][j] = sum_q W_q D[q][i] D[q][j]  (1D mass, stiffness)
+template <typename T, int N>
+struct Tab {
+  T S[N * N], Dc[N * N], W[N], M[N * N], K[N * N];
+};
+
+template <typename T, int N>
+struct ApplyArgs {
+  const T* __restrict__ x;
+  T* __restrict__ y;
+  const T* __restrict__ geom; // curved: [tile][comp][l][lane], 6 (Laplace) or 7 (Helmholtz) comps
+  GridInfo g;
+  T G[6];                     // affine: w-free metric w det J J^-1 J^-T (xx,xy,xz,yy,yz,zz)
+  T mdet;                     // affine: mass_coeff * |det J|
+  T gx, gy, gz, cmass;        // Cartesian: det/h_d^2 and mass_coeff * det
+  Tab<T, N> tab;
+};
+
+// Host-side double tables (any n <= MAXN).
+struct HostTables {
+  int n;
+  double nodes[MAXN], qx[MAXN], qw[MAXN];
+  double S[MAXN * MAXN], D[MAXN * MAXN], Dc[MAXN * MAXN], M[MAXN * MAXN], K[MAXN * MAXN];
+};
+int make_host_tables(int degree, HostTables* t);
+
+// One precision "view" of an operator: element type, geometry pointer, constants.
+struct View {
+  int elem_bytes = 8;   // 8 double, 4 float
+  void* geom = nullptr; // device, inside the caller workspace (curved only)
+  size_t geom_bytes = 0;
+};
+
+} // namespace mf
+
+struct mf_mesh {
+  int nx, ny, nz, geom;
+  double A[9], b[3], amp;
+};
+
+struct mf_operator {
+  mf_mesh mesh;
+  int degree, n, kind, precision, bc;
+  double mass;
+  int path;
+  mf::GridInfo g;
+  long long n_cellwise, n_unique, n_native;
+  mf::HostTables tab;
+  double G[6], mdet, gx, gy, gz, cmass; // affine / Cartesian constants (double)
+  mf::View v64, v32;                    // v64 used by FP64 + MIXED, v32 by FP32 + MIXED
+  void* workspace = nullptr;
+  size_t workspace_bytes = 0;
+  bool ready = false;
+};
+
+namespace mf {
+
+// error reporting (thread-local last error)
+mf_status set_error(mf_status code, const char* fmt, ...);
+mf_status cuda_check(cudaError_t e, const char* what);
+
+// Per-precision dispatch entry points (defined in the per-degree instantiation units).
+// elem: 8 or 4.  All return MF_OK or an error status.
+mf_status launch_apply_split(const mf_operator* op, int elem, const void* x, void* y, cudaStream_t s);
+mf_status launch_dss(const mf_operator* op, int elem, void* y, cudaStream_t s);
+mf_status launch_geometry(const mf_operator* op, int elem, void* geom, cudaStream_t s);
+mf_status launch_layout(const mf_operator* op, int elem, int mode, const void* in, void* out, cudaStream_t s);
+
+template <int N>
+mf_status apply_split_n(const mf_operator* op, int elem, const void* x, void* y, cudaStream_t s);
+template <int N>
+mf_status dss_n(const mf_operator* op, int elem, void* y, cudaStream_t s);
+template <int N>
+mf_status geometry_n(const mf_operator* op, int elem, void* geom, cudaStream_t s);
+template <int N>
+mf_status layout_n(const mf_operator* op, int elem, int mode, const void* in, void* out, cudaStream_t s);
+
+// layout modes
+enum { LAYOUT_TO_NATIVE = 0, LAYOUT_FROM_NATIVE = 1, LAYOUT_SCATTER_UNIQUE = 2, LAYOUT_GATHER_UNIQUE = 3 };
+
+// geometry components per point
+inline int geom_comps(const mf_operator* op) { return op->kind == MF_HELMHOLTZ ? 7 : 6; }
+
+// Reductions and CG vector kernels (mf_cg.cu)
+size_t reduce_scratch_bytes();
+mf_status dot_launch(const mf_operator* op, int elem, const void* a, const void* b, int split, double* out,
+                     void* scratch, cudaStream_t s);
+
+} // namespace mf

@@ -1,0 +1,579 @@
+// mf_kernels.cuh -- sum-factorised apply, duplicate summation (DSS), geometry and layout
+// kernels, templated on the element type T (double / float) and n = k+1.
+//
+// Included once per degree by mf_apply_k<k>.cu so the eight degrees compile in parallel.
+#pragma once
+#include "mf_internal.h"
+
+namespace mf {
+
+// Cells processed by one CTA of the apply kernels (a divisor of BL).  One thread owns one
+// pencil (a 1D line of n values) of one cell in every sweep, so a CTA has n^2 * CB threads.
+template <typename T, int N>
+struct Cfg {
+  static constexpr int CB = (N <= 4) ? 32 : (N <= 6) ? 16 : (N <= 8) ? 8 : (sizeof(T) == 4 ? 8 : 4);
+  static constexpr int NT = N * N * CB;
+};
+
+__device__ __forceinline__ void cell_of(const GridInfo& g, long long t, int lane, int& cx, int& cy, int& cz) {
+  long long txy = (long long)g.ntx * g.nty;
+  int tz = (int)(t / txy);
+  long long r = t - (long long)tz * txy;
+  int ty = (int)(r / g.ntx);
+  int tx = (int)(r - (long long)ty * g.ntx);
+  cx = tx * TX + (lane & 3);
+  cy = ty * TY + ((lane >> 2) & 3);
+  cz = tz * TZ + (lane >> 4);
+}
+
+__device__ __forceinline__ long long native_index(const GridInfo& g, int n3, int cx, int cy, int cz, int l) {
+  long long t = (long long)(cx / TX) + (long long)g.ntx * ((cy / TY) + (long long)g.nty * (cz / TZ));
+  int lane = (cx % TX) + TX * ((cy % TY) + TY * (cz % TZ));
+  return (t * n3 + l) * BL + lane;
+}
+
+template <int N>
+__device__ __forceinline__ bool on_cube_boundary(const GridInfo& g, int cx, int cy, int cz, int i, int j, int k) {
+  return (cx == 0 && i == 0) || (cx == g.nx - 1 && i == N - 1) || (cy == 0 && j == 0) ||
+         (cy == g.ny - 1 && j == N - 1) || (cz == 0 && k == 0) || (cz == g.nz - 1 && k == N - 1);
+}
+
+// Load the CB cells [lane0, lane0+CB) of tile t into smem as buf[l*CB + c] (cell fastest),
+// zeroing padding cells and, for Dirichlet, the constrained nodes (the P of P A P).
+template <typename T, int N, int CB, int NT>
+__device__ __forceinline__ void load_tile(const ApplyArgs<T, N>& a, long long t, int lane0, T* buf) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  const long long base = t * (long long)N3 * BL + lane0;
+  for (int idx = threadIdx.x; idx < N3 * CB; idx += NT) {
+    const int l = idx / CB, c = idx - l * CB;
+    int cx, cy, cz;
+    cell_of(a.g, t, lane0 + c, cx, cy, cz);
+    T v = T(0);
+    if (cx < a.g.nx && cy < a.g.ny && cz < a.g.nz) {
+      v = a.x[base + (long long)l * BL + c];
+      if (a.g.bc) {
+        const int i = l % N, j = (l / N) % N, k = l / N2;
+        if (on_cube_boundary<N>(a.g, cx, cy, cz, i, j, k)) v = T(0);
+      }
+    }
+    buf[idx] = v;
+  }
+}
+
+// Store one x-pencil (j, k) of cell c to global y, zeroing padding / constrained nodes.
+template <typename T, int N, int CB>
+__device__ __forceinline__ void store_xpencil(const ApplyArgs<T, N>& a, long long t, int lane0, int c, int j, int k,
+                                              const T* out) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  int cx, cy, cz;
+  cell_of(a.g, t, lane0 + c, cx, cy, cz);
+  const bool valid = cx < a.g.nx && cy < a.g.ny && cz < a.g.nz;
+  const long long base = t * (long long)N3 * BL + lane0 + c;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    T v = valid ? out[i] : T(0);
+    if (valid && a.g.bc && on_cube_boundary<N>(a.g, cx, cy, cz, i, j, k)) v = T(0);
+    a.y[base + (long long)(i + N * j + N2 * k) * BL] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Cartesian cells (axis-aligned affine): Sec. 3.1, Eq. (eval_pipeline), the seven-
+// contraction form  y = gx (M(x)M(x)K) x + gy (M(x)K(x)M) x + gz (K(x)M(x)M) x [+ c M(x)M(x)M x]
+// (Kronecker factors listed z, y, x).  x-sweep: M and K (2); y-sweep: M on Mx, K on Mx, M on
+// Kx (3); z-sweep: M on the combination and K on (M(x)M)x (2).
+// ---------------------------------------------------------------------------------------
+template <typename T, int N, int CB, bool HELM>
+__global__ void __launch_bounds__(N * N * CB) apply_cartesian(ApplyArgs<T, N> a) {
+  constexpr int N2 = N * N, N3 = N2 * N, NT = N2 * CB, GPT = BL / CB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* buf0 = reinterpret_cast<T*>(smem_raw);
+  T* buf1 = buf0 + N3 * CB;
+  const long long t = blockIdx.x / GPT;
+  const int lane0 = (blockIdx.x % GPT) * CB;
+  load_tile<T, N, CB, NT>(a, t, lane0, buf0);
+  __syncthreads();
+  const int c = threadIdx.x % CB, p = threadIdx.x / CB, pa = p % N, pb = p / N;
+  const T* M = a.tab.M;
+  const T* K = a.tab.K;
+  { // x: pencil (j=pa, k=pb)
+    T in[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) in[i] = buf0[(i + N * pa + N2 * pb) * CB + c];
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      T m = T(0), s = T(0);
+#pragma unroll
+      for (int i = 0; i < N; ++i) { m = fma(M[q * N + i], in[i], m); s = fma(K[q * N + i], in[i], s); }
+      buf0[(q + N * pa + N2 * pb) * CB + c] = m;
+      buf1[(q + N * pa + N2 * pb) * CB + c] = s;
+    }
+  }
+  __syncthreads();
+  { // y: pencil (i=pa, k=pb)
+    T am[N], ak[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      am[j] = buf0[(pa + N * j + N2 * pb) * CB + c];
+      ak[j] = buf1[(pa + N * j + N2 * pb) * CB + c];
+    }
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      T mm = T(0), km = T(0), mk = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        mm = fma(M[q * N + j], am[j], mm);
+        km = fma(K[q * N + j], am[j], km);
+        mk = fma(M[q * N + j], ak[j], mk);
+      }
+      T w = a.gx * mk + a.gy * km;
+      if (HELM) w = fma(a.cmass, mm, w);
+      buf0[(pa + N * q + N2 * pb) * CB + c] = w;
+      buf1[(pa + N * q + N2 * pb) * CB + c] = mm;
+    }
+  }
+  __syncthreads();
+  { // z: pencil (i=pa, j=pb); result rows go straight back to smem, then out by x-pencils
+    T w[N], mm[N], o[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      w[k] = buf0[(pa + N * pb + N2 * k) * CB + c];
+      mm[k] = buf1[(pa + N * pb + N2 * k) * CB + c];
+    }
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      T s = T(0), r = T(0);
+#pragma unroll
+      for (int k = 0; k < N; ++k) { s = fma(M[q * N + k], w[k], s); r = fma(K[q * N + k], mm[k], r); }
+      o[q] = fma(a.gz, r, s);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < N; ++q) buf0[(pa + N * pb + N2 * q) * CB + c] = o[q];
+  }
+  __syncthreads();
+  { // write out as x-pencils (j=pa, k=pb) so the Dirichlet mask indexes match
+    T o[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) o[i] = buf0[(i + N * pa + N2 * pb) * CB + c];
+    store_xpencil<T, N, CB>(a, t, lane0, c, pa, pb, o);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// General cells (affine with a full metric, or curved with per-point geometry):
+// interpolate to Gauss points with S (three sweeps), reference gradients by the collocation
+// derivative Dc (three sweeps), v = G grad u at every point (6 metric entries; Helmholtz adds
+// m u), then the transposes: Dc^T per direction summed, and S^T along z, y, x.
+// ---------------------------------------------------------------------------------------
+template <typename T, int N, int CB, bool CURVED, bool HELM>
+__global__ void __launch_bounds__(N * N * CB) apply_general(ApplyArgs<T, N> a) {
+  constexpr int N2 = N * N, N3 = N2 * N, NT = N2 * CB, GPT = BL / CB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* buf0 = reinterpret_cast<T*>(smem_raw);
+  T* buf1 = buf0 + N3 * CB;
+  const long long t = blockIdx.x / GPT;
+  const int lane0 = (blockIdx.x % GPT) * CB;
+  load_tile<T, N, CB, NT>(a, t, lane0, buf0);
+  __syncthreads();
+  const int c = threadIdx.x % CB, p = threadIdx.x / CB, pa = p % N, pb = p / N;
+  const T* S = a.tab.S;
+  const T* Dc = a.tab.Dc;
+  { // x-sweep with S, pencil (j=pa, k=pb), in place
+    T in[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) in[i] = buf0[(i + N * pa + N2 * pb) * CB + c];
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      T s = T(0);
+#pragma unroll
+      for (int i = 0; i < N; ++i) s = fma(S[q * N + i], in[i], s);
+      buf0[(q + N * pa + N2 * pb) * CB + c] = s;
+    }
+  }
+  __syncthreads();
+  { // y-sweep, pencil (i=pa, k=pb)
+    T in[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) in[j] = buf0[(pa + N * j + N2 * pb) * CB + c];
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      T s = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) s = fma(S[q * N + j], in[j], s);
+      buf0[(pa + N * q + N2 * pb) * CB + c] = s;
+    }
+  }
+  __syncthreads();
+  // z-sweep, pencil (i=pa, j=pb): values U and z-derivative stay in registers
+  T U[N], d3[N];
+  {
+    T in[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) in[k] = buf0[(pa + N * pb + N2 * k) * CB + c];
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < N; ++k) s = fma(S[q * N + k], in[k], s);
+      U[q] = s;
+    }
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      T s = T(0);
+#pragma unroll
+      for (int r = 0; r < N; ++r) s = fma(Dc[q * N + r], U[r], s);
+      d3[q] = s;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < N; ++q) buf0[(pa + N * pb + N2 * q) * CB + c] = U[q];
+  __syncthreads();
+  T d1[N], d2[N];
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    T s1 = T(0), s2 = T(0);
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      s1 = fma(Dc[pa * N + r], buf0[(r + N * pb + N2 * q) * CB + c], s1);
+      s2 = fma(Dc[pb * N + r], buf0[(pa + N * r + N2 * q) * CB + c], s2);
+    }
+    d1[q] = s1;
+    d2[q] = s2;
+  }
+  __syncthreads();
+  // quadrature points (pa, pb, q): v = G grad u
+  {
+    const long long gbase = (t * (HELM ? 7 : 6) * (long long)N3) * BL + lane0 + c;
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      const int l = pa + N * pb + N2 * q;
+      T g0, g1, g2, g3, g4, g5, m = T(0);
+      if (CURVED) {
+        const T* gp = a.geom + gbase + (long long)l * BL;
+        g0 = gp[0];
+        g1 = gp[(long long)1 * N3 * BL];
+        g2 = gp[(long long)2 * N3 * BL];
+        g3 = gp[(long long)3 * N3 * BL];
+        g4 = gp[(long long)4 * N3 * BL];
+        g5 = gp[(long long)5 * N3 * BL];
+        if (HELM) m = gp[(long long)6 * N3 * BL];
+      } else {
+        const T w = a.tab.W[pa] * a.tab.W[pb] * a.tab.W[q];
+        g0 = w * a.G[0]; g1 = w * a.G[1]; g2 = w * a.G[2];
+        g3 = w * a.G[3]; g4 = w * a.G[4]; g5 = w * a.G[5];
+        if (HELM) m = w * a.mdet;
+      }
+      const T v1 = g0 * d1[q] + g1 * d2[q] + g2 * d3[q];
+      const T v2 = g1 * d1[q] + g3 * d2[q] + g4 * d3[q];
+      const T v3 = g2 * d1[q] + g4 * d2[q] + g5 * d3[q];
+      buf0[l * CB + c] = v1;
+      buf1[l * CB + c] = v2;
+      d3[q] = v3;
+      U[q] = HELM ? m * U[q] : T(0);
+    }
+  }
+  __syncthreads();
+  // t = Dc^T_x v1 + Dc^T_y v2 + Dc^T_z v3 (+ m u) at points (pa, pb, q)
+  T tq[N];
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    T s = U[q];
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      s = fma(Dc[r * N + pa], buf0[(r + N * pb + N2 * q) * CB + c], s);
+      s = fma(Dc[r * N + pb], buf1[(pa + N * r + N2 * q) * CB + c], s);
+      s = fma(Dc[r * N + q], d3[r], s);
+    }
+    tq[q] = s;
+  }
+  __syncthreads();
+  // S^T along z, pencil (i=pa, j=pb)
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < N; ++q) s = fma(S[q * N + k], tq[q], s);
+    buf0[(pa + N * pb + N2 * k) * CB + c] = s;
+  }
+  __syncthreads();
+  { // S^T along y, pencil (i=pa, k=pb), in place
+    T in[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) in[q] = buf0[(pa + N * q + N2 * pb) * CB + c];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int q = 0; q < N; ++q) s = fma(S[q * N + j], in[q], s);
+      buf0[(pa + N * j + N2 * pb) * CB + c] = s;
+    }
+  }
+  __syncthreads();
+  { // S^T along x, pencil (j=pa, k=pb) -> global
+    T in[N], o[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) in[q] = buf0[(q + N * pa + N2 * pb) * CB + c];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      T s = T(0);
+#pragma unroll
+      for (int q = 0; q < N; ++q) s = fma(S[q * N + i], in[q], s);
+      o[i] = s;
+    }
+    store_xpencil<T, N, CB>(a, t, lane0, c, pa, pb, o);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Duplicate summation y <- G G^T y (Sec. 4: embedding G and assembly G^T) in the canonical
+// order of the dimension-split sweeps of Sec. 3: the copies of a node are summed pairwise
+// along x, then the x-sums along y, then along z.  One thread per global node; each copy
+// is read and written by exactly one thread, so no atomics and no races.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ int copies_1d(long long I, int ncell, int k, int* cell, int* loc) {
+  const long long c = I / k;
+  if (I - c * k == 0) {
+    if (c == 0) { cell[0] = 0; loc[0] = 0; return 1; }
+    if (c == ncell) { cell[0] = ncell - 1; loc[0] = k; return 1; }
+    cell[0] = (int)c - 1; loc[0] = k;
+    cell[1] = (int)c; loc[1] = 0;
+    return 2;
+  }
+  cell[0] = (int)c; loc[0] = (int)(I - c * k);
+  return 1;
+}
+
+template <typename T, int N>
+__global__ void dss_kernel(T* __restrict__ y, GridInfo g) {
+  constexpr int K = N - 1, N2 = N * N, N3 = N2 * N;
+  const long long NX = (long long)g.nx * K + 1, NY = (long long)g.ny * K + 1, NZ = (long long)g.nz * K + 1;
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gid >= NX * NY * NZ) return;
+  const long long I = gid % NX, J = (gid / NX) % NY, L = gid / (NX * NY);
+  int cx[2], ix[2], cy[2], iy[2], cz[2], iz[2];
+  const int mx = copies_1d(I, g.nx, K, cx, ix);
+  const int my = copies_1d(J, g.ny, K, cy, iy);
+  const int mz = copies_1d(L, g.nz, K, cz, iz);
+  const bool bnd = g.bc && (I == 0 || I == NX - 1 || J == 0 || J == NY - 1 || L == 0 || L == NZ - 1);
+  if (mx * my * mz == 1 && !bnd) return;
+  long long addr[8];
+  T s = T(0);
+  T sz[2];
+  for (int zz = 0; zz < mz; ++zz) {
+    T sy[2];
+    for (int yy = 0; yy < my; ++yy) {
+      T sx = T(0);
+      for (int xx = 0; xx < mx; ++xx) {
+        const long long ad = native_index(g, N3, cx[xx], cy[yy], cz[zz], ix[xx] + N * iy[yy] + N2 * iz[zz]);
+        addr[xx + 2 * (yy + 2 * zz)] = ad;
+        const T v = y[ad];
+        sx = (xx == 0) ? v : sx + v;
+      }
+      sy[yy] = sx;
+    }
+    sz[zz] = (my == 2) ? sy[0] + sy[1] : sy[0];
+  }
+  s = (mz == 2) ? sz[0] + sz[1] : sz[0];
+  if (bnd) s = T(0);
+  for (int zz = 0; zz < mz; ++zz)
+    for (int yy = 0; yy < my; ++yy)
+      for (int xx = 0; xx < mx; ++xx) y[addr[xx + 2 * (yy + 2 * zz)]] = s;
+}
+
+// ---------------------------------------------------------------------------------------
+// Per-point geometry of the curved map (Sec. 2: six metric entries plus det J per point):
+// G = w |det J| J^-1 J^-T (xx,xy,xz,yy,yz,zz) and, for Helmholtz, m = w |det J| c_m, computed
+// in FP64 from the analytic Jacobian and stored in T, layout [tile][comp][l][lane].
+// ---------------------------------------------------------------------------------------
+struct GeomArgs {
+  GridInfo g;
+  double qx[MAXN], qw[MAXN];
+  double amp, cm;
+  int comps;
+};
+
+template <typename T, int N>
+__global__ void geometry_kernel(T* __restrict__ geom, GeomArgs a) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  const long long total = a.g.ntiles * N3 * BL;
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int lane = (int)(e % BL);
+  const int l = (int)((e / BL) % N3);
+  const long long t = e / ((long long)BL * N3);
+  int cx, cy, cz;
+  cell_of(a.g, t, lane, cx, cy, cz);
+  double out[7] = {0, 0, 0, 0, 0, 0, 0};
+  if (cx < a.g.nx && cy < a.g.ny && cz < a.g.nz) {
+    const int i = l % N, j = (l / N) % N, k = l / N2;
+    const double xh[3] = {(cx + a.qx[i]) / a.g.nx, (cy + a.qx[j]) / a.g.ny, (cz + a.qx[k]) / a.g.nz};
+    const double h[3] = {1.0 / a.g.nx, 1.0 / a.g.ny, 1.0 / a.g.nz};
+    const double pi = 3.141592653589793238462643383279502884;
+    double sn[3], cs[3];
+    for (int d = 0; d < 3; ++d) sincospi(xh[d], &sn[d], &cs[d]);
+    const double gs[3] = {pi * cs[0] * sn[1] * sn[2], pi * sn[0] * cs[1] * sn[2], pi * sn[0] * sn[1] * cs[2]};
+    double J[3][3];
+    for (int r = 0; r < 3; ++r)
+      for (int d = 0; d < 3; ++d) J[r][d] = ((r == d) ? 1.0 : 0.0) * h[d] + a.amp * gs[d] * h[d];
+    const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    const double id = 1.0 / det;
+    double Ji[3][3]; // inverse
+    Ji[0][0] = c00 * id; Ji[1][0] = c01 * id; Ji[2][0] = c02 * id;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+    const double wd = a.qw[i] * a.qw[j] * a.qw[k] * fabs(det);
+    const int pr[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    for (int m = 0; m < 6; ++m) {
+      const int r = pr[m][0], s = pr[m][1];
+      out[m] = wd * (Ji[r][0] * Ji[s][0] + Ji[r][1] * Ji[s][1] + Ji[r][2] * Ji[s][2]);
+    }
+    out[6] = wd * a.cm;
+  }
+  for (int m = 0; m < a.comps; ++m) geom[((t * a.comps + m) * N3 + l) * BL + lane] = (T)out[m];
+}
+
+// ---------------------------------------------------------------------------------------
+// Layout conversion: canonical <-> native, unique -> native (gather G), native -> unique.
+// ---------------------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void layout_kernel(const T* __restrict__ in, T* __restrict__ out, GridInfo g, int mode) {
+  constexpr int K = N - 1, N2 = N * N, N3 = N2 * N;
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long NX = (long long)g.nx * K + 1, NY = (long long)g.ny * K + 1, NZ = (long long)g.nz * K + 1;
+  if (mode == LAYOUT_GATHER_UNIQUE) {
+    if (e >= NX * NY * NZ) return;
+    const long long I = e % NX, J = (e / NX) % NY, L = e / (NX * NY);
+    const int cx = (int)min(I / K, (long long)g.nx - 1), cy = (int)min(J / K, (long long)g.ny - 1),
+              cz = (int)min(L / K, (long long)g.nz - 1);
+    const int i = (int)(I - (long long)cx * K), j = (int)(J - (long long)cy * K), k = (int)(L - (long long)cz * K);
+    out[e] = in[native_index(g, N3, cx, cy, cz, i + N * j + N2 * k)];
+    return;
+  }
+  // the other modes run over native elements
+  if (e >= g.ntiles * N3 * BL) return;
+  const int lane = (int)(e % BL);
+  const int l = (int)((e / BL) % N3);
+  const long long t = e / ((long long)BL * N3);
+  int cx, cy, cz;
+  cell_of(g, t, lane, cx, cy, cz);
+  const bool valid = cx < g.nx && cy < g.ny && cz < g.nz;
+  const long long cell = ((long long)cz * g.ny + cy) * g.nx + cx;
+  if (mode == LAYOUT_TO_NATIVE) {
+    out[e] = valid ? in[cell * N3 + l] : T(0);
+  } else if (mode == LAYOUT_FROM_NATIVE) {
+    if (valid) out[cell * N3 + l] = in[e];
+  } else { // LAYOUT_SCATTER_UNIQUE
+    if (!valid) { out[e] = T(0); return; }
+    const int i = l % N, j = (l / N) % N, k = l / N2;
+    const long long I = (long long)cx * K + i, J = (long long)cy * K + j, L = (long long)cz * K + k;
+    out[e] = in[I + NX * (J + NY * L)];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Host-side launchers for one degree.
+// ---------------------------------------------------------------------------------------
+template <typename T, int N>
+static void fill_args(const mf_operator* op, ApplyArgs<T, N>& a) {
+  a.g = op->g;
+  for (int m = 0; m < 6; ++m) a.G[m] = (T)op->G[m];
+  a.mdet = (T)op->mdet;
+  a.gx = (T)op->gx; a.gy = (T)op->gy; a.gz = (T)op->gz; a.cmass = (T)op->cmass;
+  const HostTables& h = op->tab;
+  for (int q = 0; q < N; ++q) {
+    a.tab.W[q] = (T)h.qw[q];
+    for (int i = 0; i < N; ++i) {
+      a.tab.S[q * N + i] = (T)h.S[q * MAXN + i];
+      a.tab.Dc[q * N + i] = (T)h.Dc[q * MAXN + i];
+      a.tab.M[q * N + i] = (T)h.M[q * MAXN + i];
+      a.tab.K[q * N + i] = (T)h.K[q * MAXN + i];
+    }
+  }
+}
+
+template <typename T, int N>
+static mf_status apply_split_t(const mf_operator* op, const void* x, void* y, cudaStream_t s) {
+  using C = Cfg<T, N>;
+  ApplyArgs<T, N> a;
+  fill_args<T, N>(op, a);
+  a.x = static_cast<const T*>(x);
+  a.y = static_cast<T*>(y);
+  a.geom = static_cast<const T*>(sizeof(T) == 8 ? op->v64.geom : op->v32.geom);
+  const size_t smem = 2 * sizeof(T) * N * N * N * C::CB;
+  const long long blocks = op->g.ntiles * (BL / C::CB);
+  if (blocks <= 0) return MF_OK;
+  const bool helm = op->kind == MF_HELMHOLTZ;
+  void (*k)(ApplyArgs<T, N>) = nullptr;
+  if (op->path == PATH_CARTESIAN) k = helm ? apply_cartesian<T, N, C::CB, true> : apply_cartesian<T, N, C::CB, false>;
+  else if (op->path == PATH_AFFINE) k = helm ? apply_general<T, N, C::CB, false, true> : apply_general<T, N, C::CB, false, false>;
+  else k = helm ? apply_general<T, N, C::CB, true, true> : apply_general<T, N, C::CB, true, false>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(apply)");
+  }
+  k<<<(unsigned)blocks, C::NT, smem, s>>>(a);
+  return cuda_check(cudaGetLastError(), "apply launch");
+}
+
+template <int N>
+mf_status apply_split_n(const mf_operator* op, int elem, const void* x, void* y, cudaStream_t s) {
+  return elem == 8 ? apply_split_t<double, N>(op, x, y, s) : apply_split_t<float, N>(op, x, y, s);
+}
+
+template <int N>
+mf_status dss_n(const mf_operator* op, int elem, void* y, cudaStream_t s) {
+  const long long total = op->n_unique;
+  const int thr = 256;
+  const long long blocks = (total + thr - 1) / thr;
+  if (elem == 8) dss_kernel<double, N><<<(unsigned)blocks, thr, 0, s>>>(static_cast<double*>(y), op->g);
+  else dss_kernel<float, N><<<(unsigned)blocks, thr, 0, s>>>(static_cast<float*>(y), op->g);
+  return cuda_check(cudaGetLastError(), "dss launch");
+}
+
+template <int N>
+mf_status geometry_n(const mf_operator* op, int elem, void* geom, cudaStream_t s) {
+  GeomArgs a;
+  a.g = op->g;
+  for (int q = 0; q < N; ++q) { a.qx[q] = op->tab.qx[q]; a.qw[q] = op->tab.qw[q]; }
+  a.amp = op->mesh.amp;
+  a.cm = op->kind == MF_HELMHOLTZ ? op->mass : 0.0;
+  a.comps = geom_comps(op);
+  const long long total = op->g.ntiles * (long long)N * N * N * BL;
+  const int thr = 256;
+  const long long blocks = (total + thr - 1) / thr;
+  if (elem == 8) geometry_kernel<double, N><<<(unsigned)blocks, thr, 0, s>>>(static_cast<double*>(geom), a);
+  else geometry_kernel<float, N><<<(unsigned)blocks, thr, 0, s>>>(static_cast<float*>(geom), a);
+  return cuda_check(cudaGetLastError(), "geometry launch");
+}
+
+template <int N>
+mf_status layout_n(const mf_operator* op, int elem, int mode, const void* in, void* out, cudaStream_t s) {
+  const long long total = (mode == LAYOUT_GATHER_UNIQUE) ? op->n_unique : op->g.ntiles * (long long)N * N * N * BL;
+  const int thr = 256;
+  const long long blocks = (total + thr - 1) / thr;
+  if (blocks == 0) return MF_OK;
+  if (elem == 8)
+    layout_kernel<double, N><<<(unsigned)blocks, thr, 0, s>>>(static_cast<const double*>(in), static_cast<double*>(out), op->g, mode);
+  else
+    layout_kernel<float, N><<<(unsigned)blocks, thr, 0, s>>>(static_cast<const float*>(in), static_cast<float*>(out), op->g, mode);
+  return cuda_check(cudaGetLastError(), "layout launch");
+}
+
+} // namespace mf
+
+#define MF_INSTANTIATE_DEGREE(NN)                                                                        \
+  namespace mf {                                                                                        \
+  template mf_status apply_split_n<NN>(const mf_operator*, int, const void*, void*, cudaStream_t);      \
+  template mf_status dss_n<NN>(const mf_operator*, int, void*, cudaStream_t);                           \
+  template mf_status geometry_n<NN>(const mf_operator*, int, void*, cudaStream_t);                      \
+  template mf_status layout_n<NN>(const mf_operator*, int, int, const void*, void*, cudaStream_t);      \
+  }

@@ -1,0 +1,221 @@
+"""GPU parity of mf_apply / mf_apply_split / mf_dss / layout helpers against the FP64 oracle.
+
+Tolerances (relative max-norm max|y - y_ref| / max|y_ref|): FP64 1e-12, FP32 1e-5.
+Meshes span several 4x4x2 tiles with ragged tails in every direction.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2609_04534_gb300 as mf
+from paper_2609_04534_gb300 import inputs
+from tests._gpu import DevOp, oracle_op, rel_max
+
+pytestmark = pytest.mark.gpu
+
+TOL = {mf.MF_FP64: 1e-12, mf.MF_FP32: 1e-5}
+
+VARIANTS = [
+    # geom, kind, bc, precision
+    ("cart", mf.MF_LAPLACE, 0, mf.MF_FP64),
+    ("curved", mf.MF_HELMHOLTZ, 1, mf.MF_FP64),
+    ("shear", mf.MF_LAPLACE, 0, mf.MF_FP64),
+    ("stretch", mf.MF_HELMHOLTZ, 0, mf.MF_FP64),
+    ("curved", mf.MF_LAPLACE, 0, mf.MF_FP32),
+    ("cart", mf.MF_HELMHOLTZ, 1, mf.MF_FP32),
+    ("shear", mf.MF_HELMHOLTZ, 1, mf.MF_FP32),
+]
+
+
+def run_parity(oracle, dims, k, geom, kind, bc, prec, seed=3):
+    nx, ny, nz = dims
+    d = DevOp(nx, ny, nz, k, geom, kind, 1.0, prec, bc)
+    o = oracle_op(oracle, nx, ny, nz, k, geom, 1.0 if kind == mf.MF_HELMHOLTZ else 0.0, bc)
+    xu = inputs.random_unique(nx, ny, nz, k, seed)
+    if prec == mf.MF_FP32:
+        xu = xu.astype(np.float32).astype(np.float64)  # both sides see the same rounded input
+    xn = d.native_from_unique(xu)
+    y = d.apply(xn)
+    ycan = d.canonical_from_native(y)
+    yref = o.scatter(o.apply(xu))
+    err = rel_max(ycan, yref)
+    # padding lanes are zero, every real copy written (no NaN left from the poisoned buffer)
+    yh = y.double().cpu().numpy()
+    assert np.isfinite(yh).all()
+    d.close()
+    return err, ycan, yref
+
+
+@pytest.mark.parametrize("k", range(1, 9))
+@pytest.mark.parametrize("geom,kind,bc,prec", VARIANTS)
+def test_apply_parity_ragged(oracle, k, geom, kind, bc, prec):
+    dims = (5, 6, 3) if k <= 5 else (5, 2, 3)
+    err, _, _ = run_parity(oracle, dims, k, geom, kind, bc, prec)
+    assert err <= TOL[prec], err
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_config1_q2_laplace_8cubed(oracle, bc):
+    """Q2 Laplace, affine unit cube 8x8x8, FP64, x uniform[-1,1] seed 0: one y = A x."""
+    err, _, _ = run_parity(oracle, (8, 8, 8), 2, "cart", mf.MF_LAPLACE, bc, mf.MF_FP64, seed=0)
+    assert err <= 1e-12, err
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (1, 1, 2), (3, 1, 1), (4, 4, 2), (9, 1, 5)])
+@pytest.mark.parametrize("k", [1, 4])
+def test_apply_small_and_degenerate_meshes(oracle, dims, k):
+    for geom in ("cart", "curved"):
+        err, _, _ = run_parity(oracle, dims, k, geom, mf.MF_HELMHOLTZ, 0, mf.MF_FP64)
+        assert err <= 1e-12, (geom, err)
+
+
+@pytest.mark.parametrize("k", [1, 3, 8])
+@pytest.mark.parametrize("prec", [mf.MF_FP64, mf.MF_FP32])
+def test_output_is_consistent_and_deterministic(k, prec):
+    """Every copy of a shared node is bitwise equal after the duplicate summation, and two
+    applies give bitwise identical results."""
+    d = DevOp(5, 6, 3, k, "curved", mf.MF_HELMHOLTZ, 1.0, prec, 0)
+    xn = d.native_from_unique(inputs.random_unique(5, 6, 3, k, 11))
+    y1 = d.apply(xn)
+    y2 = d.apply(xn)
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)
+    rebuilt = d.native_from_unique(d.unique_from_native(y1))
+    assert torch.equal(rebuilt, y1)
+    d.close()
+
+
+@pytest.mark.parametrize("k", [2, 5])
+def test_split_apply_is_local_operator(oracle, k):
+    """mf_apply_split returns A_K x_K per cell (Eq. (split_operator)); mf_dss of it equals mf_apply."""
+    dims = (5, 6, 3)
+    d = DevOp(*dims, k, "curved", mf.MF_LAPLACE, 1.0, mf.MF_FP64, 0)
+    o = oracle_op(oracle, *dims, k, "curved", 0.0, 0)
+    xu = inputs.random_unique(*dims, k, 5)
+    xn = d.native_from_unique(xu)
+    ys = d.apply(xn, split=True)
+    ref = o.apply_cells(o.scatter(xu), np.arange(o.ncells)).ravel()
+    assert rel_max(d.canonical_from_native(ys), ref) <= 1e-12
+    mf.mf_dss(d.op, ys.data_ptr())
+    assert torch.equal(ys, d.apply(xn))
+    d.close()
+
+
+def test_layout_round_trip():
+    d = DevOp(5, 6, 3, 3, "cart")
+    can = torch.arange(d.n_cw, dtype=torch.float64, device="cuda")
+    nat = torch.full((d.n_native,), -1.0, dtype=torch.float64, device="cuda")
+    mf.mf_to_native(d.op, can.data_ptr(), nat.data_ptr())
+    back = torch.zeros(d.n_cw, dtype=torch.float64, device="cuda")
+    mf.mf_from_native(d.op, nat.data_ptr(), back.data_ptr())
+    torch.cuda.synchronize()
+    assert torch.equal(back, can)
+    # native holds every canonical value exactly once; padding lanes are zero
+    npad = d.n_native - d.n_cw
+    assert int((nat == 0).sum()) == npad + 1
+    assert torch.equal(torch.sort(nat).values[npad:], can)
+    d.close()
+
+
+@pytest.mark.parametrize("prec", [mf.MF_FP64, mf.MF_FP32])
+def test_dot_products(oracle, prec):
+    """Assembled dot over unique nodes (1/multiplicity weights) and the Lemma 1 pairing of a
+    split dual with a consistent primal."""
+    dims, k = (5, 6, 3), 3
+    d = DevOp(*dims, k, "curved", mf.MF_HELMHOLTZ, 1.0, prec, 0)
+    o = oracle_op(oracle, *dims, k, "curved", 1.0, 0)
+    a = inputs.random_unique(*dims, k, 21)
+    b = inputs.random_unique(*dims, k, 22)
+    if prec == mf.MF_FP32:
+        a = a.astype(np.float32).astype(np.float64)
+        b = b.astype(np.float32).astype(np.float64)
+    an, bn = d.native_from_unique(a), d.native_from_unique(b)
+    got = d.dot(an, bn)
+    assert abs(got - a @ b) <= 1e-13 * np.abs(a * b).sum()
+    ys = d.apply(an, split=True)
+    pair = d.dot(ys, bn, split=1)
+    ref = o.apply(a) @ b
+    assert abs(pair - ref) <= TOL[prec] * np.abs(o.apply(a)).max() * np.abs(b).sum()
+    d.close()
+
+
+@pytest.mark.parametrize("k", [3, 4])
+@pytest.mark.parametrize("prec", [mf.MF_FP64, mf.MF_FP32])
+def test_full_size_curved_64cubed_sampled(oracle, k, prec):
+    """Q3/Q4 Laplace on the curved 64^3 mesh, seed 1, FP64 and FP32: sampled global nodes are
+    compared with the oracle's sum of the local results of the cells sharing them."""
+    N = 64
+    d = DevOp(N, N, N, k, "curved", mf.MF_LAPLACE, 1.0, prec, 0)
+    xu = inputs.random_unique(N, N, N, k, 1)
+    if prec == mf.MF_FP32:
+        xu = xu.astype(np.float32).astype(np.float64)
+    y = d.unique_from_native(d.apply(d.native_from_unique(xu)))
+    o = oracle_op(oracle, N, N, N, k, "curved", 0.0, 0)
+    check_sampled(o, xu, y, TOL[prec], seed=k)
+    d.close()
+
+
+def check_sampled(o, xu, y, tol, seed, nsample=120):
+    k, n = o.k, o.k + 1
+    NX, NY = o.nx * k + 1, o.ny * k + 1
+    rng = np.random.default_rng(seed)
+    nodes = rng.integers(0, o.n_unique, nsample)
+    nodes[:4] = [0, o.n_unique - 1, (o.n_unique // 2), NX * NY + NX + 1]
+    cells, locs = [], []
+    for g in nodes:
+        I, J, L = g % NX, (g // NX) % NY, g // (NX * NY)
+        lst = []
+        for cx, i in _copies(I, o.nx, k):
+            for cy, j in _copies(J, o.ny, k):
+                for cz, l in _copies(L, o.nz, k):
+                    lst.append(((cz * o.ny + cy) * o.nx + cx, i + n * (j + n * l)))
+        locs.append(lst)
+        cells += [c for c, _ in lst]
+    ucells = np.unique(np.array(cells, dtype=np.int64))
+    # canonical cell-wise x only for the needed cells
+    xcw = np.zeros((o.ncells, n ** 3))
+    dofs = _cell_dofs_subset(o, ucells)
+    xcw[ucells] = xu[dofs]
+    yl = o.apply_cells(xcw.ravel(), ucells)
+    pos = {c: m for m, c in enumerate(ucells)}
+    ref = np.array([sum(yl[pos[c], l] for c, l in lst) for lst in locs])
+    got = y[nodes]
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= tol * scale, (np.abs(got - ref).max() / scale)
+
+
+def _copies(I, nc, k):
+    c = I // k
+    if I % k == 0:
+        out = []
+        if c > 0:
+            out.append((c - 1, k))
+        if c < nc:
+            out.append((c, 0))
+        return out
+    return [(c, I - c * k)]
+
+
+def _cell_dofs_subset(o, cells):
+    k, n = o.k, o.k + 1
+    NX, NY = o.nx * k + 1, o.ny * k + 1
+    cx = cells % o.nx
+    cy = (cells // o.nx) % o.ny
+    cz = cells // (o.nx * o.ny)
+    i = np.arange(n)
+    I = cx[:, None, None, None] * k + i[None, None, None, :]
+    J = cy[:, None, None, None] * k + i[None, None, :, None]
+    L = cz[:, None, None, None] * k + i[None, :, None, None]
+    return (I + NX * (J + NY * L)).reshape(len(cells), -1)
+
+
+@pytest.mark.parametrize("k,N", [(1, 184), (3, 92), (7, 46), (8, 41)])
+def test_full_size_helmholtz_sweep_sampled(oracle, k, N):
+    """Degree sweep: Helmholtz (M + K) on the affine unit cube with ~50M cell-wise DoFs,
+    FP64, seed 2 -- sampled against the oracle."""
+    d = DevOp(N, N, N, k, "cart", mf.MF_HELMHOLTZ, 1.0, mf.MF_FP64, 0)
+    xu = inputs.random_unique(N, N, N, k, 2)
+    y = d.unique_from_native(d.apply(d.native_from_unique(xu)))
+    o = oracle_op(oracle, N, N, N, k, "cart", 1.0, 0)
+    check_sampled(o, xu, y, 1e-12, seed=k, nsample=60)
+    d.close()

@@ -1,0 +1,99 @@
+"""GPU CG and mixed-precision defect correction against the oracle's textbook CG."""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2609_04534_gb300 as mf
+from paper_2609_04534_gb300 import inputs
+from tests._gpu import DevOp, oracle_op, rel_max
+
+pytestmark = pytest.mark.gpu
+
+
+def solve(d, b, rtol, maxit, mixed, hist_cap=0):
+    x = torch.zeros(d.n_native, dtype=d.dtype, device="cuda")
+    ws = torch.empty(mf.mf_cg_workspace_bytes(d.op, mixed), dtype=torch.uint8, device="cuda")
+    hist = np.zeros(max(hist_cap, 1))
+    if hist_cap:
+        mf.mf_cg_record_history(hist.ctypes.data, hist_cap)
+    try:
+        st = mf.mf_cg_solve(d.op, b.data_ptr(), x.data_ptr(), rtol, maxit, mixed, ws.data_ptr(), ws.numel(),
+                            allow_not_converged=True)
+    finally:
+        mf.mf_cg_record_history(None, 0)
+    return x, st, hist
+
+
+def test_config1_50_cg_iterations(oracle):
+    """Q2 Laplace 8^3, Dirichlet, b = A x_true with x_true the seed-0 random vector masked at
+    the boundary; 50 CG iterations from 0.  Per-iteration relative residuals and x_50 agree
+    with the oracle within 1e-10."""
+    N, k = 8, 2
+    d = DevOp(N, N, N, k, "cart", mf.MF_LAPLACE, 1.0, mf.MF_FP64, 1)
+    o = oracle_op(oracle, N, N, N, k, "cart", 0.0, 1)
+    xt = inputs.random_unique(N, N, N, k, 0)
+    xt[o.boundary_mask()] = 0.0
+    b_ref = o.apply(xt)
+    x_ref, h_ref = o.cg(b_ref, maxit=50, rtol=0.0)
+    b = d.apply(d.native_from_unique(xt))
+    x, st, h = solve(d, b, 0.0, 50, 0, hist_cap=64)
+    assert st["iterations"] == 50
+    np.testing.assert_allclose(h[:51], h_ref, rtol=1e-10, atol=0)
+    assert rel_max(d.unique_from_native(x), x_ref) <= 1e-10
+    d.close()
+
+
+@pytest.mark.parametrize("geom,k", [("curved", 2), ("cart", 3)])
+def test_fp64_cg_converges_to_oracle_solution(oracle, geom, k):
+    N = 5
+    d = DevOp(N, N, N, k, geom, mf.MF_LAPLACE, 1.0, mf.MF_FP64, 1)
+    o = oracle_op(oracle, N, N, N, k, geom, 0.0, 1)
+    bu = inputs.random_unique(N, N, N, k, 7)
+    x, st, _ = solve(d, d.native_from_unique(bu), 1e-10, 5000, 0)
+    assert st["code"] == mf.MF_OK and st["rel_residual"] <= 1e-10
+    xg = d.unique_from_native(x)
+    bm = np.where(o.boundary_mask(), 0.0, bu)
+    res = np.linalg.norm(bm - o.apply(xg)) / np.linalg.norm(bm)
+    assert res <= 2e-10
+    d.close()
+
+
+@pytest.mark.parametrize("geom,kind", [("curved", mf.MF_LAPLACE), ("shear", mf.MF_HELMHOLTZ)])
+def test_mixed_precision_defect_correction(oracle, geom, kind):
+    """FP32 inner CG inside FP64 defect correction reaches the FP64 tolerance 1e-10 (true
+    residual checked by the oracle) and matches the FP64 solve."""
+    N, k = 6, 3
+    d = DevOp(N, N, N, k, geom, kind, 1.0, mf.MF_MIXED, 1)
+    o = oracle_op(oracle, N, N, N, k, geom, 1.0 if kind == mf.MF_HELMHOLTZ else 0.0, 1)
+    bu = inputs.random_unique(N, N, N, k, 9)
+    b = d.native_from_unique(bu)
+    x, st, _ = solve(d, b, 1e-10, 20000, 1)
+    assert st["code"] == mf.MF_OK, st
+    assert st["outer_iterations"] >= 2
+    xg = d.unique_from_native(x)
+    bm = np.where(o.boundary_mask(), 0.0, bu)
+    res = np.linalg.norm(bm - o.apply(xg)) / np.linalg.norm(bm)
+    assert res <= 2e-10, res
+    x64, st64, _ = solve(d, b, 1e-10, 20000, 0)
+    assert st64["code"] == mf.MF_OK
+    assert rel_max(xg, d.unique_from_native(x64)) <= 1e-7
+    d.close()
+
+
+def test_breakdown_is_reported():
+    """An all-zero operator (Laplace on a 1x1x1 Dirichlet mesh of degree 1 has no free node)
+    gives x = 0 immediately; a non-finite right-hand side reports a breakdown, not a hang."""
+    d = DevOp(1, 1, 1, 1, "cart", mf.MF_LAPLACE, 1.0, mf.MF_FP64, 1)
+    b = torch.zeros(d.n_native, dtype=torch.float64, device="cuda")
+    x, st, _ = solve(d, b, 1e-10, 10, 0)
+    assert st["code"] == mf.MF_OK and st["iterations"] == 0
+    d.close()
+    d = DevOp(3, 3, 3, 2, "cart", mf.MF_LAPLACE, 1.0, mf.MF_FP64, 0)
+    b = d.native_from_unique(inputs.random_unique(3, 3, 3, 2, 1))
+    b[5] = float("inf")
+    with pytest.raises(mf.MfError) as e:
+        solve(d, b, 1e-10, 10, 0)
+    assert e.value.code == mf.MF_ERR_BREAKDOWN
+    d.close()

@@ -1,0 +1,104 @@
+"""CPU-side checks of the C ABI: the library loads, exports every entry point declared in
+include/mf.h, and validates arguments on the host (no GPU compute is called here)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import paper_2609_04534_gb300 as mf
+from paper_2609_04534_gb300 import build as mfbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    mfbuild.build()
+    return mf.lib()
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(mf_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_functions()
+    assert "mf_apply" in names and "mf_cg_solve" in names
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_mesh_argument_validation(L):
+    with pytest.raises(mf.MfError) as e:
+        mf.mf_mesh_create(0, 4, 4)
+    assert e.value.code == mf.MF_ERR_ARG
+    with pytest.raises(mf.MfError):
+        mf.mf_mesh_create(4, 4, 4, 7)
+    with pytest.raises(mf.MfError):
+        mf.mf_mesh_create(4, 4, 4, mf.MF_CURVED_SIN, None, 0.5)  # would fold the mesh
+    m = mf.mf_mesh_create(4, 4, 4, mf.MF_CURVED_SIN, None, 0.1)
+    mf.mf_mesh_destroy(m)
+
+
+def test_operator_argument_validation_and_info(L):
+    m = mf.mf_mesh_create(5, 6, 3)
+    for bad in [dict(degree=0), dict(degree=9), dict(degree=2, kind=5), dict(degree=2, precision=9),
+                dict(degree=2, bc=3)]:
+        kw = dict(kind=mf.MF_LAPLACE, precision=mf.MF_FP64, bc=mf.MF_BC_NONE)
+        kw.update(bad)
+        with pytest.raises(mf.MfError) as e:
+            mf.mf_operator_create(m, kw.pop("degree"), **kw)
+        assert e.value.code == mf.MF_ERR_ARG
+    op = mf.mf_operator_create(m, 3)
+    info = mf.mf_operator_info(op)
+    assert info["n_cellwise"] == 5 * 6 * 3 * 64
+    assert info["n_unique"] == 16 * 19 * 10
+    # tiles of 4x4x2 cells: ceil(5/4)*ceil(6/4)*ceil(3/2) = 2*2*2 tiles of 32 lanes
+    assert info["n_native"] == 8 * 32 * 64
+    assert info["path"] == 0 and info["geom_bytes"] == 0
+    assert info["algorithmic_bytes_per_apply"] == 16 * info["n_cellwise"]
+    mf.mf_operator_destroy(op)
+    mc = mf.mf_mesh_create(5, 6, 3, mf.MF_CURVED_SIN, None, 0.1)
+    op = mf.mf_operator_create(mc, 4, mf.MF_HELMHOLTZ, 1.0, mf.MF_MIXED, mf.MF_BC_DIRICHLET0)
+    info = mf.mf_operator_info(op)
+    assert info["path"] == 2
+    assert info["geom_bytes"] == 7 * info["n_native"] * (8 + 4)
+    assert info["algorithmic_bytes_per_apply"] == (16 + 7 * 8) * info["n_cellwise"]
+    # not set up yet: apply must refuse without touching the GPU
+    with pytest.raises(mf.MfError) as e:
+        mf.mf_apply(op, 16, 32)
+    assert e.value.code == mf.MF_ERR_ARG
+    # workspace too small
+    with pytest.raises(mf.MfError) as e:
+        mf.mf_operator_setup(op, 256, 1024)
+    assert e.value.code == mf.MF_ERR_OOM
+    assert mf.mf_cg_workspace_bytes(op, 1) > mf.mf_cg_workspace_bytes(op, 0) > 0
+    mf.mf_operator_destroy(op)
+    mf.mf_mesh_destroy(mc)
+    mf.mf_mesh_destroy(m)
+
+
+def test_sheared_affine_selects_general_path(L):
+    m = mf.mf_mesh_create(2, 2, 2, mf.MF_AFFINE, [1, 0.3, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0])
+    op = mf.mf_operator_create(m, 2)
+    assert mf.mf_operator_info(op)["path"] == 1
+    mf.mf_operator_destroy(op)
+    mf.mf_mesh_destroy(m)
+    m = mf.mf_mesh_create(2, 2, 2, mf.MF_AFFINE, [0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0])
+    with pytest.raises(mf.MfError):
+        mf.mf_operator_create(m, 2)
+    mf.mf_mesh_destroy(m)
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    monkeypatch.setattr(mf, "_lib", None)
+    monkeypatch.setattr(mf, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(ImportError):
+        mf.lib()
