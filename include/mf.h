@@ -138,6 +138,19 @@ size_t mf_reduce_workspace_bytes(const mf_operator* op);
 mf_status mf_dot(const mf_operator* op, const void* a_dev, const void* b_dev, int split, double* result_dev,
                  void* scratch_dev, size_t scratch_bytes, void* stream);
 
+/* Allocation-free variant of mf_dot (the paper has no counterpart: it is a service for
+ * callers that may not allocate device memory where they reduce, e.g. a solver inside a
+ * host application whose device memory belongs to another allocator, or a time-critical
+ * loop that avoids cudaMalloc because it may synchronise the device).  Same result as
+ * mf_dot within rounding (same weights, FP64 accumulation, fixed order; a different CTA
+ * split).  Its scratch is a 512 KiB static device array inside libmf (held by every GPU
+ * that loads the library until exit): vectors with n_native > 134,217,728 elements are
+ * rejected with MF_ERR_ARG.  The first call on a device looks up that array's address with
+ * the device current; make it before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU race, so serialise them.  Calls no allocating routine. */
+mf_status mf_dot_noalloc(const mf_operator* op, const void* a_dev, const void* b_dev, int split, double* result_dev,
+                         void* stream);
+
 /* ------------------------------------------------------------------ CG solver
  * Unpreconditioned CG on (P A P) x = P b from x = 0 for consistent native b, to
  * ||b - A x|| <= rtol ||b|| (assembled Euclidean norm = the pairing <r, r> of Sec. 4) or

@@ -73,6 +73,7 @@ def lib() -> C.CDLL:
     L.mf_reduce_workspace_bytes.argtypes = [vp]
     L.mf_reduce_workspace_bytes.restype = sz
     L.mf_dot.argtypes = [vp, vp, vp, i32, vp, vp, sz, vp]
+    L.mf_dot_noalloc.argtypes = [vp, vp, vp, i32, vp, vp]
     L.mf_cg_workspace_bytes.argtypes = [vp, i32]
     L.mf_cg_workspace_bytes.restype = sz
     L.mf_cg_solve.argtypes = [vp, vp, vp, d, i32, i32, C.POINTER(mf_solve_stats), vp, sz, vp]
@@ -172,6 +173,11 @@ def mf_reduce_workspace_bytes(op) -> int:
 def mf_dot(op, a_ptr: int, b_ptr: int, result_ptr: int, scratch_ptr: int, scratch_bytes: int, split: int = 0,
            stream: int = 0) -> None:
     _check(lib().mf_dot(op, a_ptr, b_ptr, split, result_ptr, scratch_ptr, scratch_bytes, stream or None))
+
+
+def mf_dot_noalloc(op, a_ptr: int, b_ptr: int, result_ptr: int, split: int = 0, stream: int = 0) -> None:
+    """mf_dot without caller scratch (static device scratch inside libmf; see include/mf.h)."""
+    _check(lib().mf_dot_noalloc(op, a_ptr, b_ptr, split, result_ptr, stream or None))
 
 
 def mf_cg_workspace_bytes(op, mixed: int = 0) -> int:
