@@ -17,7 +17,7 @@ MF_OK, MF_ERR_ARG, MF_ERR_OOM, MF_ERR_CUDA = 0, -1, -2, -3
 MF_ERR_NOT_CONVERGED, MF_ERR_BREAKDOWN, MF_ERR_TIMEOUT, MF_ERR_BUSY, MF_ERR_UNSUPPORTED = -4, -5, -6, -7, -8
 MF_AFFINE, MF_CURVED_SIN = 0, 1
 MF_LAPLACE, MF_HELMHOLTZ = 0, 1
-MF_FP64, MF_FP32, MF_MIXED = 0, 1, 2
+MF_FP64, MF_FP32, MF_MIXED, MF_FP64_DFMA = 0, 1, 2, 3
 MF_BC_NONE, MF_BC_DIRICHLET0 = 0, 1
 
 _STATUS = {0: "MF_OK", -1: "MF_ERR_ARG", -2: "MF_ERR_OOM", -3: "MF_ERR_CUDA", -4: "MF_ERR_NOT_CONVERGED",

@@ -97,7 +97,7 @@ mf_status mf_operator_create(const mf_mesh* mesh, int degree, int kind, double m
   *out = nullptr;
   if (degree < 1 || degree > 8) return set_error(MF_ERR_ARG, "mf_operator_create: degree %d not in 1..8", degree);
   if (kind != MF_LAPLACE && kind != MF_HELMHOLTZ) return set_error(MF_ERR_ARG, "mf_operator_create: kind %d", kind);
-  if (precision != MF_FP64 && precision != MF_FP32 && precision != MF_MIXED)
+  if (precision != MF_FP64 && precision != MF_FP32 && precision != MF_MIXED && precision != MF_FP64_DFMA)
     return set_error(MF_ERR_ARG, "mf_operator_create: precision %d", precision);
   if (bc != MF_BC_NONE && bc != MF_BC_DIRICHLET0) return set_error(MF_ERR_ARG, "mf_operator_create: bc %d", bc);
   mf_operator* op = new (std::nothrow) mf_operator;
@@ -211,8 +211,8 @@ mf_status mf_operator_setup(mf_operator* op, void* workspace_dev, size_t bytes, 
   op->workspace = workspace_dev;
   op->workspace_bytes = bytes;
   if (op->path == PATH_CURVED) {
-    if (op->v64.geom) { mf_status st = launch_geometry(op, 8, op->v64.geom, s); if (st) return st; }
-    if (op->v32.geom) { mf_status st = launch_geometry(op, 4, op->v32.geom, s); if (st) return st; }
+    if (op->v64.geom) { mf_status st = launch_geometry(op, fp64_view(op), op->v64.geom, s); if (st) return st; }
+    if (op->v32.geom) { mf_status st = launch_geometry(op, VK_F32, op->v32.geom, s); if (st) return st; }
   }
   op->ready = true;
   return MF_OK;
@@ -247,7 +247,7 @@ mf_status mf_apply_split(const mf_operator* op, const void* x_dev, void* y_dev, 
   mf_status st = check_ready(op, "mf_apply_split");
   if (st) return st;
   if (!x_dev || !y_dev || x_dev == y_dev) return set_error(MF_ERR_ARG, "mf_apply_split: bad vectors");
-  return launch_apply_split(op, elem_of(op), x_dev, y_dev, static_cast<cudaStream_t>(stream));
+  return launch_apply_split(op, view_of_elem(op, elem_of(op)), x_dev, y_dev, static_cast<cudaStream_t>(stream));
 }
 
 mf_status mf_dss(const mf_operator* op, void* y_dev, void* stream) {

@@ -48,23 +48,25 @@ struct CgState {
 template <int N>
 __device__ __forceinline__ double node_weight(const GridInfo& g, long long e, int split) {
   constexpr int N2 = N * N, N3 = N2 * N;
+  // tile indices fit in 32 bits (n_native < 2^31 * 32): keep the divisions 32-bit
   const int lane = (int)(e & (BL - 1));
-  const long long row = e >> 5;
-  const int l = (int)(row % N3);
-  const long long t = row / N3;
-  const long long txy = (long long)g.ntx * g.nty;
-  const int tz = (int)(t / txy);
-  const long long r = t - (long long)tz * txy;
-  const int ty = (int)(r / g.ntx);
-  const int tx = (int)(r - (long long)ty * g.ntx);
+  const unsigned row = (unsigned)(e >> 5);
+  const int t = (int)(row / (unsigned)N3);
+  const int l = (int)(row - (unsigned)t * (unsigned)N3);
+  const int txy = g.ntx * g.nty;
+  const int tz = t / txy;
+  const int r = t - tz * txy;
+  const int ty = r / g.ntx;
+  const int tx = r - ty * g.ntx;
   const int cx = tx * TX + (lane & 3), cy = ty * TY + ((lane >> 2) & 3), cz = tz * TZ + (lane >> 4);
   if (cx >= g.nx || cy >= g.ny || cz >= g.nz) return 0.0;
   if (split) return 1.0;
   const int i = l % N, j = (l / N) % N, k = l / N2;
-  const int m = (((i == 0 && cx > 0) || (i == N - 1 && cx < g.nx - 1)) ? 2 : 1) *
-                (((j == 0 && cy > 0) || (j == N - 1 && cy < g.ny - 1)) ? 2 : 1) *
-                (((k == 0 && cz > 0) || (k == N - 1 && cz < g.nz - 1)) ? 2 : 1);
-  return 1.0 / m;
+  const int sh = (((i == 0 && cx > 0) || (i == N - 1 && cx < g.nx - 1)) ? 1 : 0) +
+                 (((j == 0 && cy > 0) || (j == N - 1 && cy < g.ny - 1)) ? 1 : 0) +
+                 (((k == 0 && cz > 0) || (k == N - 1 && cz < g.nz - 1)) ? 1 : 0);
+  // 1 / multiplicity = 2^-sh, selected (a double division costs tens of FP64-pipe slots)
+  return sh == 0 ? 1.0 : (sh == 1 ? 0.5 : (sh == 2 ? 0.25 : 0.125));
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -223,13 +225,13 @@ __global__ void mask_kernel(const T* __restrict__ b, T* __restrict__ o, long lon
   constexpr int N2 = N * N, N3 = N2 * N;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const int lane = (int)(e & (BL - 1));
-    const long long row = e >> 5;
-    const int l = (int)(row % N3);
-    const long long t = row / N3;
-    const long long txy = (long long)g.ntx * g.nty;
-    const int tz = (int)(t / txy);
-    const long long rr = t - (long long)tz * txy;
-    const int ty = (int)(rr / g.ntx), tx = (int)(rr - (long long)ty * g.ntx);
+    const unsigned row = (unsigned)(e >> 5);
+    const int t = (int)(row / (unsigned)N3);
+    const int l = (int)(row - (unsigned)t * (unsigned)N3);
+    const int txy = g.ntx * g.nty;
+    const int tz = t / txy;
+    const int rr = t - tz * txy;
+    const int ty = rr / g.ntx, tx = rr - ty * g.ntx;
     const int cx = tx * TX + (lane & 3), cy = ty * TY + ((lane >> 2) & 3), cz = tz * TZ + (lane >> 4);
     const int i = l % N, j = (l / N) % N, k = l / N2;
     const bool valid = cx < g.nx && cy < g.ny && cz < g.nz;
@@ -315,7 +317,7 @@ static mf_status launch_cg_vec(const mf_operator* op, int elem, void* x, void* r
 
 // apply + duplicate summation with a given element type (selects the FP64 or FP32 view)
 static mf_status apply_elem(const mf_operator* op, int elem, const void* x, void* y, cudaStream_t s) {
-  mf_status st = launch_apply_split(op, elem, x, y, s);
+  mf_status st = launch_apply_split(op, view_of_elem(op, elem), x, y, s);
   if (st) return st;
   return launch_dss(op, elem, y, s);
 }

@@ -37,10 +37,13 @@ struct Tab {
   T S[N * N], Dc[N * N], W[N], M[N * N], K[N * N];
 };
 
-template <typename T, int N>
+// Precision views of an operator: storage type of the vectors / compute type of the apply.
+enum ViewKind { VK_F64 = 0, VK_DD = 1, VK_F32 = 2 };
+
+template <typename S, typename T, int N>
 struct ApplyArgs {
-  const T* __restrict__ x;
-  T* __restrict__ y;
+  const S* __restrict__ x;
+  S* __restrict__ y;
   const T* __restrict__ geom; // curved: [tile][comp][l][lane], 6 (Laplace) or 7 (Helmholtz) comps
   GridInfo g;
   T G[6];                     // affine: w-free metric w det J J^-1 J^-T (xx,xy,xz,yy,yz,zz)
@@ -94,17 +97,18 @@ mf_status cuda_check(cudaError_t e, const char* what);
 
 // Per-precision dispatch entry points (defined in the per-degree instantiation units).
 // elem: 8 or 4.  All return MF_OK or an error status.
-mf_status launch_apply_split(const mf_operator* op, int elem, const void* x, void* y, cudaStream_t s);
+// apply / geometry take a ViewKind; dss / layout / reductions take the element size.
+mf_status launch_apply_split(const mf_operator* op, int vk, const void* x, void* y, cudaStream_t s);
 mf_status launch_dss(const mf_operator* op, int elem, void* y, cudaStream_t s);
-mf_status launch_geometry(const mf_operator* op, int elem, void* geom, cudaStream_t s);
+mf_status launch_geometry(const mf_operator* op, int vk, void* geom, cudaStream_t s);
 mf_status launch_layout(const mf_operator* op, int elem, int mode, const void* in, void* out, cudaStream_t s);
 
 template <int N>
-mf_status apply_split_n(const mf_operator* op, int elem, const void* x, void* y, cudaStream_t s);
+mf_status apply_split_n(const mf_operator* op, int vk, const void* x, void* y, cudaStream_t s);
 template <int N>
 mf_status dss_n(const mf_operator* op, int elem, void* y, cudaStream_t s);
 template <int N>
-mf_status geometry_n(const mf_operator* op, int elem, void* geom, cudaStream_t s);
+mf_status geometry_n(const mf_operator* op, int vk, void* geom, cudaStream_t s);
 template <int N>
 mf_status layout_n(const mf_operator* op, int elem, int mode, const void* in, void* out, cudaStream_t s);
 
@@ -113,6 +117,11 @@ enum { LAYOUT_TO_NATIVE = 0, LAYOUT_FROM_NATIVE = 1, LAYOUT_SCATTER_UNIQUE = 2, 
 
 // geometry components per point
 inline int geom_comps(const mf_operator* op) { return op->kind == MF_HELMHOLTZ ? 7 : 6; }
+
+// View kind of the FP64 apply (double-float compute unless native DFMA was requested) and
+// the view kind matching an element size.
+inline int fp64_view(const mf_operator* op) { return op->precision == MF_FP64_DFMA ? VK_F64 : VK_DD; }
+inline int view_of_elem(const mf_operator* op, int elem) { return elem == 8 ? fp64_view(op) : VK_F32; }
 
 // Reductions and CG vector kernels (mf_cg.cu)
 size_t reduce_scratch_bytes();

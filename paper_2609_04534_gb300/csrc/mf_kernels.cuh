@@ -1,8 +1,10 @@
 // mf_kernels.cuh -- sum-factorised apply, duplicate summation (DSS), geometry and layout
-// kernels, templated on the element type T (double / float) and n = k+1.
+// kernels.  The apply kernels are templated on the storage type S of the vectors (double /
+// float), the compute type T (double, float, or double-float dd) and n = k+1.
 //
 // Included once per degree by mf_apply_k<k>.cu so the eight degrees compile in parallel.
 #pragma once
+#include "mf_dd.cuh"
 #include "mf_internal.h"
 
 namespace mf {
@@ -15,12 +17,13 @@ struct Cfg {
   static constexpr int NT = N * N * CB;
 };
 
-__device__ __forceinline__ void cell_of(const GridInfo& g, long long t, int lane, int& cx, int& cy, int& cz) {
-  long long txy = (long long)g.ntx * g.nty;
-  int tz = (int)(t / txy);
-  long long r = t - (long long)tz * txy;
-  int ty = (int)(r / g.ntx);
-  int tx = (int)(r - (long long)ty * g.ntx);
+__device__ __forceinline__ void cell_of(const GridInfo& g, long long t64, int lane, int& cx, int& cy, int& cz) {
+  const int t = (int)t64; // tile counts are below 2^31 (checked at mesh creation)
+  const int txy = g.ntx * g.nty;
+  const int tz = t / txy;
+  const int r = t - tz * txy;
+  const int ty = r / g.ntx;
+  const int tx = r - ty * g.ntx;
   cx = tx * TX + (lane & 3);
   cy = ty * TY + ((lane >> 2) & 3);
   cz = tz * TZ + (lane >> 4);
@@ -40,8 +43,8 @@ __device__ __forceinline__ bool on_cube_boundary(const GridInfo& g, int cx, int 
 
 // Load the CB cells [lane0, lane0+CB) of tile t into smem as buf[l*CB + c] (cell fastest),
 // zeroing padding cells and, for Dirichlet, the constrained nodes (the P of P A P).
-template <typename T, int N, int CB, int NT>
-__device__ __forceinline__ void load_tile(const ApplyArgs<T, N>& a, long long t, int lane0, T* buf) {
+template <typename S, typename T, int N, int CB, int NT>
+__device__ __forceinline__ void load_tile(const ApplyArgs<S, T, N>& a, long long t, int lane0, T* buf) {
   constexpr int N2 = N * N, N3 = N2 * N;
   const long long base = t * (long long)N3 * BL + lane0;
   for (int idx = threadIdx.x; idx < N3 * CB; idx += NT) {
@@ -50,7 +53,7 @@ __device__ __forceinline__ void load_tile(const ApplyArgs<T, N>& a, long long t,
     cell_of(a.g, t, lane0 + c, cx, cy, cz);
     T v = T(0);
     if (cx < a.g.nx && cy < a.g.ny && cz < a.g.nz) {
-      v = a.x[base + (long long)l * BL + c];
+      v = to_compute<T, S>(a.x[base + (long long)l * BL + c]);
       if (a.g.bc) {
         const int i = l % N, j = (l / N) % N, k = l / N2;
         if (on_cube_boundary<N>(a.g, cx, cy, cz, i, j, k)) v = T(0);
@@ -61,8 +64,8 @@ __device__ __forceinline__ void load_tile(const ApplyArgs<T, N>& a, long long t,
 }
 
 // Store one x-pencil (j, k) of cell c to global y, zeroing padding / constrained nodes.
-template <typename T, int N, int CB>
-__device__ __forceinline__ void store_xpencil(const ApplyArgs<T, N>& a, long long t, int lane0, int c, int j, int k,
+template <typename S, typename T, int N, int CB>
+__device__ __forceinline__ void store_xpencil(const ApplyArgs<S, T, N>& a, long long t, int lane0, int c, int j, int k,
                                               const T* out) {
   constexpr int N2 = N * N, N3 = N2 * N;
   int cx, cy, cz;
@@ -71,8 +74,8 @@ __device__ __forceinline__ void store_xpencil(const ApplyArgs<T, N>& a, long lon
   const long long base = t * (long long)N3 * BL + lane0 + c;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    T v = valid ? out[i] : T(0);
-    if (valid && a.g.bc && on_cube_boundary<N>(a.g, cx, cy, cz, i, j, k)) v = T(0);
+    S v = valid ? to_storage<S, T>(out[i]) : S(0);
+    if (valid && a.g.bc && on_cube_boundary<N>(a.g, cx, cy, cz, i, j, k)) v = S(0);
     a.y[base + (long long)(i + N * j + N2 * k) * BL] = v;
   }
 }
@@ -83,15 +86,15 @@ __device__ __forceinline__ void store_xpencil(const ApplyArgs<T, N>& a, long lon
 // (Kronecker factors listed z, y, x).  x-sweep: M and K (2); y-sweep: M on Mx, K on Mx, M on
 // Kx (3); z-sweep: M on the combination and K on (M(x)M)x (2).
 // ---------------------------------------------------------------------------------------
-template <typename T, int N, int CB, bool HELM>
-__global__ void __launch_bounds__(N * N * CB) apply_cartesian(ApplyArgs<T, N> a) {
+template <typename S, typename T, int N, int CB, bool HELM>
+__global__ void __launch_bounds__(N * N * CB) apply_cartesian(ApplyArgs<S, T, N> a) {
   constexpr int N2 = N * N, N3 = N2 * N, NT = N2 * CB, GPT = BL / CB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* buf0 = reinterpret_cast<T*>(smem_raw);
   T* buf1 = buf0 + N3 * CB;
   const long long t = blockIdx.x / GPT;
   const int lane0 = (blockIdx.x % GPT) * CB;
-  load_tile<T, N, CB, NT>(a, t, lane0, buf0);
+  load_tile<S, T, N, CB, NT>(a, t, lane0, buf0);
   __syncthreads();
   const int c = threadIdx.x % CB, p = threadIdx.x / CB, pa = p % N, pb = p / N;
   const T* M = a.tab.M;
@@ -105,8 +108,8 @@ __global__ void __launch_bounds__(N * N * CB) apply_cartesian(ApplyArgs<T, N> a)
       T m = T(0), s = T(0);
 #pragma unroll
       for (int i = 0; i < N; ++i) { m = fma(M[q * N + i], in[i], m); s = fma(K[q * N + i], in[i], s); }
-      buf0[(q + N * pa + N2 * pb) * CB + c] = m;
-      buf1[(q + N * pa + N2 * pb) * CB + c] = s;
+      buf0[(q + N * pa + N2 * pb) * CB + c] = finish(m);
+      buf1[(q + N * pa + N2 * pb) * CB + c] = finish(s);
     }
   }
   __syncthreads();
@@ -126,9 +129,10 @@ __global__ void __launch_bounds__(N * N * CB) apply_cartesian(ApplyArgs<T, N> a)
         km = fma(K[q * N + j], am[j], km);
         mk = fma(M[q * N + j], ak[j], mk);
       }
-      T w = a.gx * mk + a.gy * km;
+      mm = finish(mm);
+      T w = fma(a.gx, finish(mk), a.gy * finish(km));
       if (HELM) w = fma(a.cmass, mm, w);
-      buf0[(pa + N * q + N2 * pb) * CB + c] = w;
+      buf0[(pa + N * q + N2 * pb) * CB + c] = finish(w);
       buf1[(pa + N * q + N2 * pb) * CB + c] = mm;
     }
   }
@@ -145,7 +149,7 @@ __global__ void __launch_bounds__(N * N * CB) apply_cartesian(ApplyArgs<T, N> a)
       T s = T(0), r = T(0);
 #pragma unroll
       for (int k = 0; k < N; ++k) { s = fma(M[q * N + k], w[k], s); r = fma(K[q * N + k], mm[k], r); }
-      o[q] = fma(a.gz, r, s);
+      o[q] = finish(fma(a.gz, finish(r), s));
     }
     __syncthreads();
 #pragma unroll
@@ -156,7 +160,7 @@ __global__ void __launch_bounds__(N * N * CB) apply_cartesian(ApplyArgs<T, N> a)
     T o[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) o[i] = buf0[(i + N * pa + N2 * pb) * CB + c];
-    store_xpencil<T, N, CB>(a, t, lane0, c, pa, pb, o);
+    store_xpencil<S, T, N, CB>(a, t, lane0, c, pa, pb, o);
   }
 }
 
@@ -166,18 +170,18 @@ __global__ void __launch_bounds__(N * N * CB) apply_cartesian(ApplyArgs<T, N> a)
 // derivative Dc (three sweeps), v = G grad u at every point (6 metric entries; Helmholtz adds
 // m u), then the transposes: Dc^T per direction summed, and S^T along z, y, x.
 // ---------------------------------------------------------------------------------------
-template <typename T, int N, int CB, bool CURVED, bool HELM>
-__global__ void __launch_bounds__(N * N * CB) apply_general(ApplyArgs<T, N> a) {
+template <typename S, typename T, int N, int CB, bool CURVED, bool HELM>
+__global__ void __launch_bounds__(N * N * CB) apply_general(ApplyArgs<S, T, N> a) {
   constexpr int N2 = N * N, N3 = N2 * N, NT = N2 * CB, GPT = BL / CB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* buf0 = reinterpret_cast<T*>(smem_raw);
   T* buf1 = buf0 + N3 * CB;
   const long long t = blockIdx.x / GPT;
   const int lane0 = (blockIdx.x % GPT) * CB;
-  load_tile<T, N, CB, NT>(a, t, lane0, buf0);
+  load_tile<S, T, N, CB, NT>(a, t, lane0, buf0);
   __syncthreads();
   const int c = threadIdx.x % CB, p = threadIdx.x / CB, pa = p % N, pb = p / N;
-  const T* S = a.tab.S;
+  const T* Sm = a.tab.S;
   const T* Dc = a.tab.Dc;
   { // x-sweep with S, pencil (j=pa, k=pb), in place
     T in[N];
@@ -187,8 +191,8 @@ __global__ void __launch_bounds__(N * N * CB) apply_general(ApplyArgs<T, N> a) {
     for (int q = 0; q < N; ++q) {
       T s = T(0);
 #pragma unroll
-      for (int i = 0; i < N; ++i) s = fma(S[q * N + i], in[i], s);
-      buf0[(q + N * pa + N2 * pb) * CB + c] = s;
+      for (int i = 0; i < N; ++i) s = fma(Sm[q * N + i], in[i], s);
+      buf0[(q + N * pa + N2 * pb) * CB + c] = finish(s);
     }
   }
   __syncthreads();
@@ -200,8 +204,8 @@ __global__ void __launch_bounds__(N * N * CB) apply_general(ApplyArgs<T, N> a) {
     for (int q = 0; q < N; ++q) {
       T s = T(0);
 #pragma unroll
-      for (int j = 0; j < N; ++j) s = fma(S[q * N + j], in[j], s);
-      buf0[(pa + N * q + N2 * pb) * CB + c] = s;
+      for (int j = 0; j < N; ++j) s = fma(Sm[q * N + j], in[j], s);
+      buf0[(pa + N * q + N2 * pb) * CB + c] = finish(s);
     }
   }
   __syncthreads();
@@ -215,15 +219,15 @@ __global__ void __launch_bounds__(N * N * CB) apply_general(ApplyArgs<T, N> a) {
     for (int q = 0; q < N; ++q) {
       T s = T(0);
 #pragma unroll
-      for (int k = 0; k < N; ++k) s = fma(S[q * N + k], in[k], s);
-      U[q] = s;
+      for (int k = 0; k < N; ++k) s = fma(Sm[q * N + k], in[k], s);
+      U[q] = finish(s);
     }
 #pragma unroll
     for (int q = 0; q < N; ++q) {
       T s = T(0);
 #pragma unroll
       for (int r = 0; r < N; ++r) s = fma(Dc[q * N + r], U[r], s);
-      d3[q] = s;
+      d3[q] = finish(s);
     }
   }
   __syncthreads();
@@ -239,8 +243,8 @@ __global__ void __launch_bounds__(N * N * CB) apply_general(ApplyArgs<T, N> a) {
       s1 = fma(Dc[pa * N + r], buf0[(r + N * pb + N2 * q) * CB + c], s1);
       s2 = fma(Dc[pb * N + r], buf0[(pa + N * r + N2 * q) * CB + c], s2);
     }
-    d1[q] = s1;
-    d2[q] = s2;
+    d1[q] = finish(s1);
+    d2[q] = finish(s2);
   }
   __syncthreads();
   // quadrature points (pa, pb, q): v = G grad u
@@ -265,9 +269,9 @@ __global__ void __launch_bounds__(N * N * CB) apply_general(ApplyArgs<T, N> a) {
         g3 = w * a.G[3]; g4 = w * a.G[4]; g5 = w * a.G[5];
         if (HELM) m = w * a.mdet;
       }
-      const T v1 = g0 * d1[q] + g1 * d2[q] + g2 * d3[q];
-      const T v2 = g1 * d1[q] + g3 * d2[q] + g4 * d3[q];
-      const T v3 = g2 * d1[q] + g4 * d2[q] + g5 * d3[q];
+      const T v1 = finish(fma(g0, d1[q], fma(g1, d2[q], g2 * d3[q])));
+      const T v2 = finish(fma(g1, d1[q], fma(g3, d2[q], g4 * d3[q])));
+      const T v3 = finish(fma(g2, d1[q], fma(g4, d2[q], g5 * d3[q])));
       buf0[l * CB + c] = v1;
       buf1[l * CB + c] = v2;
       d3[q] = v3;
@@ -286,7 +290,7 @@ __global__ void __launch_bounds__(N * N * CB) apply_general(ApplyArgs<T, N> a) {
       s = fma(Dc[r * N + pb], buf1[(pa + N * r + N2 * q) * CB + c], s);
       s = fma(Dc[r * N + q], d3[r], s);
     }
-    tq[q] = s;
+    tq[q] = finish(s);
   }
   __syncthreads();
   // S^T along z, pencil (i=pa, j=pb)
@@ -294,8 +298,8 @@ __global__ void __launch_bounds__(N * N * CB) apply_general(ApplyArgs<T, N> a) {
   for (int k = 0; k < N; ++k) {
     T s = T(0);
 #pragma unroll
-    for (int q = 0; q < N; ++q) s = fma(S[q * N + k], tq[q], s);
-    buf0[(pa + N * pb + N2 * k) * CB + c] = s;
+    for (int q = 0; q < N; ++q) s = fma(Sm[q * N + k], tq[q], s);
+    buf0[(pa + N * pb + N2 * k) * CB + c] = finish(s);
   }
   __syncthreads();
   { // S^T along y, pencil (i=pa, k=pb), in place
@@ -306,8 +310,8 @@ __global__ void __launch_bounds__(N * N * CB) apply_general(ApplyArgs<T, N> a) {
     for (int j = 0; j < N; ++j) {
       T s = T(0);
 #pragma unroll
-      for (int q = 0; q < N; ++q) s = fma(S[q * N + j], in[q], s);
-      buf0[(pa + N * j + N2 * pb) * CB + c] = s;
+      for (int q = 0; q < N; ++q) s = fma(Sm[q * N + j], in[q], s);
+      buf0[(pa + N * j + N2 * pb) * CB + c] = finish(s);
     }
   }
   __syncthreads();
@@ -319,10 +323,10 @@ __global__ void __launch_bounds__(N * N * CB) apply_general(ApplyArgs<T, N> a) {
     for (int i = 0; i < N; ++i) {
       T s = T(0);
 #pragma unroll
-      for (int q = 0; q < N; ++q) s = fma(S[q * N + i], in[q], s);
-      o[i] = s;
+      for (int q = 0; q < N; ++q) s = fma(Sm[q * N + i], in[q], s);
+      o[i] = finish(s);
     }
-    store_xpencil<T, N, CB>(a, t, lane0, c, pa, pb, o);
+    store_xpencil<S, T, N, CB>(a, t, lane0, c, pa, pb, o);
   }
 }
 
@@ -387,6 +391,14 @@ __global__ void dss_kernel(T* __restrict__ y, GridInfo g) {
 // G = w |det J| J^-1 J^-T (xx,xy,xz,yy,yz,zz) and, for Helmholtz, m = w |det J| c_m, computed
 // in FP64 from the analytic Jacobian and stored in T, layout [tile][comp][l][lane].
 // ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T geom_value(double v) { return (T)v; }
+template <>
+__device__ __forceinline__ dd geom_value<dd>(double v) {
+  const float h = __double2float_rn(v);
+  return dd(h, __double2float_rn(v - (double)h));
+}
+
 struct GeomArgs {
   GridInfo g;
   double qx[MAXN], qw[MAXN];
@@ -438,7 +450,7 @@ __global__ void geometry_kernel(T* __restrict__ geom, GeomArgs a) {
     }
     out[6] = wd * a.cm;
   }
-  for (int m = 0; m < a.comps; ++m) geom[((t * a.comps + m) * N3 + l) * BL + lane] = (T)out[m];
+  for (int m = 0; m < a.comps; ++m) geom[((t * a.comps + m) * N3 + l) * BL + lane] = geom_value<T>(out[m]);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -482,40 +494,46 @@ __global__ void layout_kernel(const T* __restrict__ in, T* __restrict__ out, Gri
 // ---------------------------------------------------------------------------------------
 // Host-side launchers for one degree.
 // ---------------------------------------------------------------------------------------
-template <typename T, int N>
-static void fill_args(const mf_operator* op, ApplyArgs<T, N>& a) {
+template <typename S, typename T, int N>
+static void fill_args(const mf_operator* op, ApplyArgs<S, T, N>& a) {
   a.g = op->g;
-  for (int m = 0; m < 6; ++m) a.G[m] = (T)op->G[m];
-  a.mdet = (T)op->mdet;
-  a.gx = (T)op->gx; a.gy = (T)op->gy; a.gz = (T)op->gz; a.cmass = (T)op->cmass;
+  for (int m = 0; m < 6; ++m) a.G[m] = host_from_double<T>(op->G[m]);
+  a.mdet = host_from_double<T>(op->mdet);
+  a.gx = host_from_double<T>(op->gx);
+  a.gy = host_from_double<T>(op->gy);
+  a.gz = host_from_double<T>(op->gz);
+  a.cmass = host_from_double<T>(op->cmass);
   const HostTables& h = op->tab;
   for (int q = 0; q < N; ++q) {
-    a.tab.W[q] = (T)h.qw[q];
+    a.tab.W[q] = host_from_double<T>(h.qw[q]);
     for (int i = 0; i < N; ++i) {
-      a.tab.S[q * N + i] = (T)h.S[q * MAXN + i];
-      a.tab.Dc[q * N + i] = (T)h.Dc[q * MAXN + i];
-      a.tab.M[q * N + i] = (T)h.M[q * MAXN + i];
-      a.tab.K[q * N + i] = (T)h.K[q * MAXN + i];
+      a.tab.S[q * N + i] = host_from_double<T>(h.S[q * MAXN + i]);
+      a.tab.Dc[q * N + i] = host_from_double<T>(h.Dc[q * MAXN + i]);
+      a.tab.M[q * N + i] = host_from_double<T>(h.M[q * MAXN + i]);
+      a.tab.K[q * N + i] = host_from_double<T>(h.K[q * MAXN + i]);
     }
   }
 }
 
-template <typename T, int N>
-static mf_status apply_split_t(const mf_operator* op, const void* x, void* y, cudaStream_t s) {
+template <typename S, typename T, int N>
+static mf_status apply_split_t(const mf_operator* op, const void* x, void* y, const void* geom, cudaStream_t s) {
   using C = Cfg<T, N>;
-  ApplyArgs<T, N> a;
-  fill_args<T, N>(op, a);
-  a.x = static_cast<const T*>(x);
-  a.y = static_cast<T*>(y);
-  a.geom = static_cast<const T*>(sizeof(T) == 8 ? op->v64.geom : op->v32.geom);
+  ApplyArgs<S, T, N> a;
+  fill_args<S, T, N>(op, a);
+  a.x = static_cast<const S*>(x);
+  a.y = static_cast<S*>(y);
+  a.geom = static_cast<const T*>(geom);
   const size_t smem = 2 * sizeof(T) * N * N * N * C::CB;
   const long long blocks = op->g.ntiles * (BL / C::CB);
   if (blocks <= 0) return MF_OK;
   const bool helm = op->kind == MF_HELMHOLTZ;
-  void (*k)(ApplyArgs<T, N>) = nullptr;
-  if (op->path == PATH_CARTESIAN) k = helm ? apply_cartesian<T, N, C::CB, true> : apply_cartesian<T, N, C::CB, false>;
-  else if (op->path == PATH_AFFINE) k = helm ? apply_general<T, N, C::CB, false, true> : apply_general<T, N, C::CB, false, false>;
-  else k = helm ? apply_general<T, N, C::CB, true, true> : apply_general<T, N, C::CB, true, false>;
+  void (*k)(ApplyArgs<S, T, N>) = nullptr;
+  if (op->path == PATH_CARTESIAN)
+    k = helm ? apply_cartesian<S, T, N, C::CB, true> : apply_cartesian<S, T, N, C::CB, false>;
+  else if (op->path == PATH_AFFINE)
+    k = helm ? apply_general<S, T, N, C::CB, false, true> : apply_general<S, T, N, C::CB, false, false>;
+  else
+    k = helm ? apply_general<S, T, N, C::CB, true, true> : apply_general<S, T, N, C::CB, true, false>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(apply)");
@@ -524,9 +542,13 @@ static mf_status apply_split_t(const mf_operator* op, const void* x, void* y, cu
   return cuda_check(cudaGetLastError(), "apply launch");
 }
 
+// vk: VK_F64 (double storage, native FP64 compute), VK_DD (double storage, double-float
+// compute), VK_F32 (float storage and compute).
 template <int N>
-mf_status apply_split_n(const mf_operator* op, int elem, const void* x, void* y, cudaStream_t s) {
-  return elem == 8 ? apply_split_t<double, N>(op, x, y, s) : apply_split_t<float, N>(op, x, y, s);
+mf_status apply_split_n(const mf_operator* op, int vk, const void* x, void* y, cudaStream_t s) {
+  if (vk == VK_F64) return apply_split_t<double, double, N>(op, x, y, op->v64.geom, s);
+  if (vk == VK_DD) return apply_split_t<double, dd, N>(op, x, y, op->v64.geom, s);
+  return apply_split_t<float, float, N>(op, x, y, op->v32.geom, s);
 }
 
 template <int N>
@@ -540,7 +562,7 @@ mf_status dss_n(const mf_operator* op, int elem, void* y, cudaStream_t s) {
 }
 
 template <int N>
-mf_status geometry_n(const mf_operator* op, int elem, void* geom, cudaStream_t s) {
+mf_status geometry_n(const mf_operator* op, int vk, void* geom, cudaStream_t s) {
   GeomArgs a;
   a.g = op->g;
   for (int q = 0; q < N; ++q) { a.qx[q] = op->tab.qx[q]; a.qw[q] = op->tab.qw[q]; }
@@ -550,7 +572,8 @@ mf_status geometry_n(const mf_operator* op, int elem, void* geom, cudaStream_t s
   const long long total = op->g.ntiles * (long long)N * N * N * BL;
   const int thr = 256;
   const long long blocks = (total + thr - 1) / thr;
-  if (elem == 8) geometry_kernel<double, N><<<(unsigned)blocks, thr, 0, s>>>(static_cast<double*>(geom), a);
+  if (vk == VK_F64) geometry_kernel<double, N><<<(unsigned)blocks, thr, 0, s>>>(static_cast<double*>(geom), a);
+  else if (vk == VK_DD) geometry_kernel<dd, N><<<(unsigned)blocks, thr, 0, s>>>(static_cast<dd*>(geom), a);
   else geometry_kernel<float, N><<<(unsigned)blocks, thr, 0, s>>>(static_cast<float*>(geom), a);
   return cuda_check(cudaGetLastError(), "geometry launch");
 }

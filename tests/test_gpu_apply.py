@@ -13,7 +13,7 @@ from tests._gpu import DevOp, oracle_op, rel_max
 
 pytestmark = pytest.mark.gpu
 
-TOL = {mf.MF_FP64: 1e-12, mf.MF_FP32: 1e-5}
+TOL = {mf.MF_FP64: 1e-12, mf.MF_FP64_DFMA: 1e-12, mf.MF_FP32: 1e-5}
 
 VARIANTS = [
     # geom, kind, bc, precision
@@ -24,6 +24,9 @@ VARIANTS = [
     ("curved", mf.MF_LAPLACE, 0, mf.MF_FP32),
     ("cart", mf.MF_HELMHOLTZ, 1, mf.MF_FP32),
     ("shear", mf.MF_HELMHOLTZ, 1, mf.MF_FP32),
+    ("curved", mf.MF_HELMHOLTZ, 1, mf.MF_FP64_DFMA),
+    ("cart", mf.MF_LAPLACE, 0, mf.MF_FP64_DFMA),
+    ("shear", mf.MF_HELMHOLTZ, 0, mf.MF_FP64_DFMA),
 ]
 
 
@@ -140,7 +143,7 @@ def test_dot_products(oracle, prec):
 
 
 @pytest.mark.parametrize("k", [3, 4])
-@pytest.mark.parametrize("prec", [mf.MF_FP64, mf.MF_FP32])
+@pytest.mark.parametrize("prec", [mf.MF_FP64, mf.MF_FP32, mf.MF_FP64_DFMA])
 def test_full_size_curved_64cubed_sampled(oracle, k, prec):
     """Q3/Q4 Laplace on the curved 64^3 mesh, seed 1, FP64 and FP32: sampled global nodes are
     compared with the oracle's sum of the local results of the cells sharing them."""
@@ -209,11 +212,12 @@ def _cell_dofs_subset(o, cells):
     return (I + NX * (J + NY * L)).reshape(len(cells), -1)
 
 
-@pytest.mark.parametrize("k,N", [(1, 184), (3, 92), (7, 46), (8, 41)])
-def test_full_size_helmholtz_sweep_sampled(oracle, k, N):
+@pytest.mark.parametrize("k,N", [(1, 184), (2, 123), (3, 92), (4, 74), (5, 61), (6, 53), (7, 46), (8, 41)])
+@pytest.mark.parametrize("prec", [mf.MF_FP64, mf.MF_FP64_DFMA])
+def test_full_size_helmholtz_sweep_sampled(oracle, k, N, prec):
     """Degree sweep: Helmholtz (M + K) on the affine unit cube with ~50M cell-wise DoFs,
     FP64, seed 2 -- sampled against the oracle."""
-    d = DevOp(N, N, N, k, "cart", mf.MF_HELMHOLTZ, 1.0, mf.MF_FP64, 0)
+    d = DevOp(N, N, N, k, "cart", mf.MF_HELMHOLTZ, 1.0, prec, 0)
     xu = inputs.random_unique(N, N, N, k, 2)
     y = d.unique_from_native(d.apply(d.native_from_unique(xu)))
     o = oracle_op(oracle, N, N, N, k, "cart", 1.0, 0)
