@@ -113,6 +113,13 @@ def make_op(mf, torch, N, k, geom, kind, prec, bc, stream):
     return mesh, op, info, ws
 
 
+def autotune(mf, torch, op, x, stream):
+    y = torch.empty_like(x)
+    v = mf.mf_operator_autotune(op, x.data_ptr(), y.data_ptr(), 3, stream)
+    del y
+    return v
+
+
 def random_native(mf, torch, op, info, N, k, seed, dtype, stream):
     from paper_2609_04534_gb300 import inputs
 
@@ -240,6 +247,107 @@ def profile_apply(args):
     mf.mf_mesh_destroy(mesh)
 
 
+def solve_run(args):
+    """Mixed-precision Poisson solve: Q4 on the curved N^3 mesh (default 96^3), manufactured
+    u = sin(2 pi x) sin(2 pi y) sin(2 pi z), FP32 apply inside FP64 defect correction to
+    relative residual 1e-10, against plain FP64 CG (double-float apply) on the same problem."""
+    import torch
+
+    import paper_2609_04534_gb300 as mf
+
+    N, k = args.solve_n, 4
+    stream = torch.cuda.Stream()
+    s = stream.cuda_stream
+    out = {"metric": "solved DoF/s at relative residual 1e-10", "workload":
+           f"Q4 Poisson curved {N}^3, manufactured sin(2 pi x)sin(2 pi y)sin(2 pi z), Dirichlet"}
+    mesh, op, info, ws = make_op(mf, torch, N, k, mf.MF_CURVED_SIN, mf.MF_LAPLACE, mf.MF_MIXED, 1, s)
+    b = torch.empty(info["n_native"], dtype=torch.float64, device="cuda")
+    sc = torch.empty(mf.mf_manufactured_workspace_bytes(op), dtype=torch.uint8, device="cuda")
+    t0 = time.perf_counter()
+    mf.mf_rhs_manufactured(op, 2.0, b.data_ptr(), sc.data_ptr(), sc.numel(), s)
+    stream.synchronize()
+    out["rhs_setup_s"] = time.perf_counter() - t0
+    x = torch.zeros_like(b)
+    autotune(mf, torch, op, b, s)
+    l2 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for mixed in (1, 0):
+        cws = torch.empty(mf.mf_cg_workspace_bytes(op, mixed), dtype=torch.uint8, device="cuda")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        st = mf.mf_cg_solve(op, b.data_ptr(), x.data_ptr(), 1e-10, 400000, mixed, cws.data_ptr(), cws.numel(), s,
+                            allow_not_converged=True)
+        ev[1].record(stream)
+        ev[1].synchronize()
+        t = ev[0].elapsed_time(ev[1]) / 1e3
+        mf.mf_error_manufactured(op, 2.0, x.data_ptr(), l2.data_ptr(), sc.data_ptr(), sc.numel(), s)
+        stream.synchronize()
+        out["mixed" if mixed else "fp64"] = {
+            "status": st["code"], "iterations": st["iterations"], "outer": st["outer_iterations"],
+            "rel_residual": st["rel_residual"], "seconds": t,
+            "solved_gdofs_cellwise": info["n_cellwise"] / t / 1e9, "solved_gdofs_unique": info["n_unique"] / t / 1e9,
+            "l2_error": float(l2.item()) ** 0.5}
+        del cws
+        torch.cuda.empty_cache()
+    out["n_cellwise"], out["n_unique"] = info["n_cellwise"], info["n_unique"]
+    out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    print(json.dumps(out), flush=True)
+    mf.mf_operator_destroy(op)
+    mf.mf_mesh_destroy(mesh)
+
+
+def serve_run(args):
+    """Serving stream: NREQ Poisson CG solve requests, mesh N^3 with N log-uniform in [4, 64],
+    degree uniform in {2..6}, affine or curved 50/50, manufactured right-hand side, FP32 apply
+    in FP64 refinement to 1e-10; seed 4.  Reports p50/p99 latency (submit -> result) and
+    solved DoF/s over the makespan."""
+    import torch
+
+    import paper_2609_04534_gb300 as mf
+
+    rng = np.random.default_rng(4)
+    n = args.serve
+    Ns = np.rint(np.exp(rng.uniform(np.log(4), np.log(64), n))).astype(int)
+    ks = rng.integers(2, 7, n)
+    geo = rng.integers(0, 2, n)
+    arena = torch.empty(int(120 * 2**30), dtype=torch.uint8, device="cuda")
+    sv = mf.mf_server_create(arena.data_ptr(), arena.numel(), max_slots=64, autotune=1)
+    reqs = [mf.make_request(int(N), int(N), int(N), int(k), geometry=mf.MF_CURVED_SIN if g else mf.MF_AFFINE,
+                            rhs=mf.MF_RHS_MANUFACTURED, rtol=1e-10, maxit=400000, mixed=1)
+            for N, k, g in zip(Ns, ks, geo)]
+    rate = args.rate
+    gaps = rng.exponential(1.0 / rate, n) if rate > 0 else np.zeros(n)
+    t0 = time.perf_counter()
+    tickets, results = [], {}
+    nxt = 0.0
+    for i, r in enumerate(reqs):
+        nxt += gaps[i]
+        while time.perf_counter() - t0 < nxt:
+            time.sleep(0.0005)
+        tickets.append(mf.mf_batch_submit(sv, r))
+    while len(results) < n:
+        for t in tickets:
+            if t not in results:
+                res = mf.mf_batch_poll(sv, t)
+                if res is not None:
+                    results[t] = res
+        time.sleep(0.001)
+    makespan = time.perf_counter() - t0
+    st = mf.mf_server_stats(sv)
+    mf.mf_server_destroy(sv)
+    rs = [results[t] for t in tickets]
+    lat = np.array([r["latency"] for r in rs])
+    ok = [r for r in rs if r["status"] == 0]
+    out = {"metric": "serving: solved DoF/s and p50/p99 latency at 1e-10", "requests": n,
+           "arrival_rate_per_s": rate if rate > 0 else "all at t=0 (closed burst)", "ok": len(ok),
+           "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+           "makespan_s": makespan,
+           "solved_gdofs_cellwise": sum(r["n_cellwise"] for r in ok) / makespan / 1e9,
+           "solved_gdofs_unique": sum(r["n_unique"] for r in ok) / makespan / 1e9,
+           "max_rel_residual": max(r["rel_residual"] for r in ok) if ok else None,
+           "arena_peak_gb": st["arena_peak"] / 2**30, "slots": 64}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -252,9 +360,19 @@ def main():
     ap.add_argument("--profile-apply", default=None, metavar="N,k,geom,prec,kind",
                     help="only run a few applies of one case (for ncu), e.g. 32,4,curved,fp64,laplace")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--serve", type=int, default=0, metavar="NREQ",
+                    help="serving run: NREQ solve requests with Poisson arrivals (prints its own JSON line)")
+    ap.add_argument("--rate", type=float, default=0.0, help="serving arrival rate (requests/s); 0 = measure capacity")
+    ap.add_argument("--solve-n", type=int, default=96, help="cells per axis of the --solve mesh")
     args = ap.parse_args()
     if args.profile_apply:
         profile_apply(args)
+        return
+    if args.solve:
+        solve_run(args)
+        return
+    if args.serve:
+        serve_run(args)
         return
     if args.warmup < 3:
         args.warmup = 3
@@ -289,6 +407,7 @@ def main():
         y = torch.empty_like(b)
         cws = torch.empty(mf.mf_cg_workspace_bytes(op, 0), dtype=torch.uint8, device="cuda")
     stream.synchronize()
+    variant = autotune(mf, torch, op, b, s)
     # warm-up (also builds and caches the solve's graph path once)
     mf.mf_cg_solve(op, b.data_ptr(), x.data_ptr(), 0.0, args.warmup, 0, cws.data_ptr(), cws.numel(), s,
                    allow_not_converged=True)
@@ -370,6 +489,7 @@ def main():
             with torch.cuda.stream(stream):
                 xx = random_native(mf, torch, op, info, 64, kk, 1, dt, s)
                 yy = torch.empty_like(xx)
+            autotune(mf, torch, op, xx, s)
             t = time_apply(mf, torch, op, xx, yy, stream, 20, 3)
             ta, td = time_kernels(mf, torch, op, xx, yy, stream, 5)
             gd = info["n_cellwise"] / t / 1e9
@@ -391,6 +511,7 @@ def main():
                 with torch.cuda.stream(stream):
                     xx = random_native(mf, torch, op, info, NN, kk, 2, torch.float64, s)
                     yy = torch.empty_like(xx)
+                autotune(mf, torch, op, xx, s)
                 t = time_apply(mf, torch, op, xx, yy, stream, 10, 3)
                 gd = info["n_cellwise"] / t / 1e9
                 ent["n_cellwise"] = info["n_cellwise"]
@@ -423,6 +544,7 @@ def main():
             "apply_only": {"gdofs": round(ncw / t_apply / 1e9, 4), "hbm_frac_of_measured": round(hbm_frac_apply, 4),
                            "apply_kernel_ms": round(t_split * 1e3, 4), "dss_kernel_ms": round(t_dss * 1e3, 4)},
             "roofline": roof,
+            "apply_variant": variant,
             "applies_64cubed_curved": applies,
             "helmholtz_sweep_50M": sweep,
             "cpu_baseline": cpu,

@@ -49,6 +49,7 @@ typedef int mf_status;
 #define MF_ERR_TIMEOUT (-6)       /* a bounded wait gave up */
 #define MF_ERR_BUSY (-7)          /* request still pending / queue full */
 #define MF_ERR_UNSUPPORTED (-8)   /* combination not built */
+#define MF_ERR_CANCELLED (-9)     /* request cancelled before it finished */
 
 enum { MF_AFFINE = 0, MF_CURVED_SIN = 1 };
 enum { MF_LAPLACE = 0, MF_HELMHOLTZ = 1 };
@@ -105,6 +106,19 @@ mf_status mf_operator_info(const mf_operator* op, mf_info* info);
  * must outlive the operator. */
 mf_status mf_operator_setup(mf_operator* op, void* workspace_dev, size_t bytes, void* stream);
 
+/* Autotuner: times each launch configuration of the apply kernel (variant 0: n^2 x CB
+ * threads per CTA, two CTAs per SM; variant 1: half the cells per CTA, three CTAs per SM)
+ * with `reps` applies of x_dev into y_dev (both native vectors of this operator; y is
+ * overwritten) and keeps the fastest.  The choice is cached per (device, degree, path,
+ * kind, precision) for the life of the process, so later operators of the same class reuse
+ * it without timing.  Synchronises `stream`.  Results do not depend on the variant (each
+ * thread runs the same arithmetic), only speed does. */
+mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, int reps, void* stream);
+/* Forces a launch variant (0 or 1) for every precision view; returns MF_ERR_ARG otherwise. */
+mf_status mf_operator_set_variant(mf_operator* op, int variant);
+/* Variant in use for the operator's main precision view (-1 for a NULL operator). */
+int mf_operator_get_variant(const mf_operator* op);
+
 /* ------------------------------------------------------------------ layout helpers */
 /* canonical cell-wise -> native and back (device pointers, operator element type). */
 mf_status mf_to_native(const mf_operator* op, const void* canonical_dev, void* native_dev, void* stream);
@@ -133,6 +147,20 @@ mf_status mf_dss(const mf_operator* op, void* y_dev, void* stream);
 size_t mf_apply_host_workspace_bytes(const mf_operator* op);
 mf_status mf_apply_host(const mf_operator* op, const void* x_host, void* y_host, void* workspace_dev, size_t bytes,
                         void* stream);
+
+/* ------------------------------------------------------------------ manufactured workload
+ * u = sin(freq pi x) sin(freq pi y) sin(freq pi z) on the unit cube (homogeneous Dirichlet data
+ * for integer freq), f = -Lap u + c_m u.  mf_rhs_manufactured writes the consistent assembled
+ * load vector b_i = int f phi_i (Gauss rule of the operator, k+1 points per direction; masked
+ * for MF_BC_DIRICHLET0).  mf_error_manufactured writes sum_K int_K (u - u_h)^2 (the squared L2
+ * error of the native vector u_h) to *l2sq_dev.  Both evaluate u at the physical quadrature
+ * points in double-float arithmetic and need mf_manufactured_workspace_bytes() of scratch.
+ * Affine maps must be axis-aligned (MF_ERR_UNSUPPORTED otherwise). */
+size_t mf_manufactured_workspace_bytes(const mf_operator* op);
+mf_status mf_rhs_manufactured(const mf_operator* op, double freq, void* b_dev, void* scratch_dev, size_t scratch_bytes,
+                              void* stream);
+mf_status mf_error_manufactured(const mf_operator* op, double freq, const void* u_dev, double* l2sq_dev,
+                                void* scratch_dev, size_t scratch_bytes, void* stream);
 
 /* ------------------------------------------------------------------ reductions
  * Assembled inner product of two consistent native vectors (each unique node counted once:
@@ -178,6 +206,70 @@ mf_status mf_cg_solve(const mf_operator* op, const void* b_dev, void* x_dev, dou
 /* Records up to `cap` relative residual norms (one per iteration, FP64) of the next
  * mf_cg_solve on this thread into hist_host; pass NULL to stop recording. */
 mf_status mf_cg_record_history(double* hist_host, int cap);
+
+/* ------------------------------------------------------------------ serving
+ * Continuous-batching solve server.  Requests are queued by mf_batch_submit and admitted in
+ * arrival order whenever one of max_slots slots and enough of the caller's device arena are
+ * free (a request that does not fit yet does not block smaller ones behind it).  An admitted
+ * request keeps its geometry, vectors and CG state resident in its arena block and runs on
+ * its slot's CUDA stream as graph chunks of CG iterations, so the work of all active
+ * requests overlaps on the GPU; a native scheduler thread advances each request when its
+ * scalars have landed and admits new ones as slots and memory free up.  Every request solves
+ * the homogeneous Dirichlet problem on the unit cube with the given operator; mixed = 1 runs
+ * FP32 applies inside FP64 defect correction (else FP64 CG).  The arena is the only device
+ * memory used (pinned host memory holds per-slot scalars); it must outlive the server. */
+enum { MF_RHS_MANUFACTURED = 0, MF_RHS_RANDOM = 1 };
+
+typedef struct {
+  int32_t max_slots;        /* concurrent requests (default 32, at most 256) */
+  int32_t queue_capacity;   /* pending requests before MF_ERR_BUSY (default 100000) */
+  int32_t chunk_iterations; /* CG iterations per graph launch (default 20) */
+  int32_t autotune;         /* 1: autotune the apply of each new operator class */
+  double inner_rtol;        /* mixed: inner FP32 CG tolerance (default 1e-4) */
+} mf_server_config;
+
+typedef struct {
+  int32_t nx, ny, nz, degree, kind, geometry;
+  double mass_coeff, curve_amp;
+  int32_t rhs;              /* MF_RHS_MANUFACTURED (u = prod sin(freq pi x_d)) or MF_RHS_RANDOM */
+  double freq;              /* manufactured frequency */
+  uint64_t seed;            /* random right-hand side: splitmix64 stream on unique DoFs */
+  double rtol;              /* relative residual target (assembled Euclidean norm) */
+  int32_t maxit;            /* CG iterations cap (inner iterations for mixed) */
+  int32_t mixed;
+  double* x_out_host;       /* optional: receives the solution on unique DoFs (n_unique doubles) */
+} mf_request;
+
+typedef struct {
+  int32_t status;           /* MF_ERR_BUSY while queued or running; then the solve status */
+  int32_t iterations, outer_iterations;
+  double rel_residual;
+  double l2_error;          /* manufactured right-hand side: ||u - u_h||_L2, else -1 */
+  double t_submit, t_admit, t_done, latency; /* seconds since server creation; latency = done - submit */
+  int64_t n_cellwise, n_unique;
+  size_t device_bytes;      /* arena bytes the request held */
+} mf_result;
+
+typedef struct {
+  int64_t pending, active, admitted, completed;
+  size_t arena_bytes, arena_used, arena_peak;
+} mf_server_stats_t;
+
+mf_status mf_server_create(const mf_server_config* cfg, void* arena_dev, size_t arena_bytes, mf_server** out);
+/* Validates and queues a request; MF_ERR_OOM if it can never fit in the arena, MF_ERR_BUSY if
+ * the queue is full. */
+mf_status mf_batch_submit(mf_server* server, const mf_request* req, uint64_t* ticket);
+/* MF_ERR_BUSY (res->status too) while pending; MF_OK once finished, after which the ticket
+ * is forgotten (res->status holds the solve's own status). */
+mf_status mf_batch_poll(mf_server* server, uint64_t ticket, mf_result* res);
+/* Marks a request cancelled: dropped if still queued, stopped at its next chunk if running
+ * (final status MF_ERR_CANCELLED). */
+mf_status mf_batch_cancel(mf_server* server, uint64_t ticket);
+/* Waits (bounded) until no request is queued or running; MF_ERR_TIMEOUT otherwise. */
+mf_status mf_server_drain(mf_server* server, double timeout_s);
+mf_status mf_server_stats(mf_server* server, mf_server_stats_t* out);
+/* Cancels outstanding work, waits for the slot streams and frees host resources. */
+void mf_server_destroy(mf_server* server);
 
 #ifdef __cplusplus
 }

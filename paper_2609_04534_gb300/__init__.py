@@ -15,13 +15,16 @@ LIB_PATH = os.path.join(_HERE, "libmf.so")
 
 MF_OK, MF_ERR_ARG, MF_ERR_OOM, MF_ERR_CUDA = 0, -1, -2, -3
 MF_ERR_NOT_CONVERGED, MF_ERR_BREAKDOWN, MF_ERR_TIMEOUT, MF_ERR_BUSY, MF_ERR_UNSUPPORTED = -4, -5, -6, -7, -8
+MF_ERR_CANCELLED = -9
+MF_RHS_MANUFACTURED, MF_RHS_RANDOM = 0, 1
 MF_AFFINE, MF_CURVED_SIN = 0, 1
 MF_LAPLACE, MF_HELMHOLTZ = 0, 1
 MF_FP64, MF_FP32, MF_MIXED, MF_FP64_DFMA = 0, 1, 2, 3
 MF_BC_NONE, MF_BC_DIRICHLET0 = 0, 1
 
 _STATUS = {0: "MF_OK", -1: "MF_ERR_ARG", -2: "MF_ERR_OOM", -3: "MF_ERR_CUDA", -4: "MF_ERR_NOT_CONVERGED",
-           -5: "MF_ERR_BREAKDOWN", -6: "MF_ERR_TIMEOUT", -7: "MF_ERR_BUSY", -8: "MF_ERR_UNSUPPORTED"}
+           -5: "MF_ERR_BREAKDOWN", -6: "MF_ERR_TIMEOUT", -7: "MF_ERR_BUSY", -8: "MF_ERR_UNSUPPORTED",
+           -9: "MF_ERR_CANCELLED"}
 
 
 class MfError(RuntimeError):
@@ -40,6 +43,31 @@ class mf_info(C.Structure):
 class mf_solve_stats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("outer_iterations", C.c_int32), ("rel_residual", C.c_double),
                 ("seconds", C.c_double), ("status", C.c_int32), ("check_every", C.c_int32)]
+
+
+class mf_server_config(C.Structure):
+    _fields_ = [("max_slots", C.c_int32), ("queue_capacity", C.c_int32), ("chunk_iterations", C.c_int32),
+                ("autotune", C.c_int32), ("inner_rtol", C.c_double)]
+
+
+class mf_request(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("degree", C.c_int32),
+                ("kind", C.c_int32), ("geometry", C.c_int32), ("mass_coeff", C.c_double),
+                ("curve_amp", C.c_double), ("rhs", C.c_int32), ("freq", C.c_double), ("seed", C.c_uint64),
+                ("rtol", C.c_double), ("maxit", C.c_int32), ("mixed", C.c_int32),
+                ("x_out_host", C.c_void_p)]
+
+
+class mf_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("outer_iterations", C.c_int32),
+                ("rel_residual", C.c_double), ("l2_error", C.c_double), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double), ("latency", C.c_double),
+                ("n_cellwise", C.c_int64), ("n_unique", C.c_int64), ("device_bytes", C.c_size_t)]
+
+
+class mf_server_stats_t(C.Structure):
+    _fields_ = [("pending", C.c_int64), ("active", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("arena_bytes", C.c_size_t), ("arena_used", C.c_size_t), ("arena_peak", C.c_size_t)]
 
 
 _lib = None
@@ -74,10 +102,26 @@ def lib() -> C.CDLL:
     L.mf_reduce_workspace_bytes.restype = sz
     L.mf_dot.argtypes = [vp, vp, vp, i32, vp, vp, sz, vp]
     L.mf_dot_noalloc.argtypes = [vp, vp, vp, i32, vp, vp]
+    L.mf_operator_autotune.argtypes = [vp, vp, vp, i32, vp]
+    L.mf_operator_set_variant.argtypes = [vp, i32]
+    L.mf_operator_get_variant.argtypes = [vp]
+    L.mf_operator_get_variant.restype = i32
+    L.mf_manufactured_workspace_bytes.argtypes = [vp]
+    L.mf_manufactured_workspace_bytes.restype = sz
+    L.mf_rhs_manufactured.argtypes = [vp, d, vp, vp, sz, vp]
+    L.mf_error_manufactured.argtypes = [vp, d, vp, vp, vp, sz, vp]
     L.mf_cg_workspace_bytes.argtypes = [vp, i32]
     L.mf_cg_workspace_bytes.restype = sz
     L.mf_cg_solve.argtypes = [vp, vp, vp, d, i32, i32, C.POINTER(mf_solve_stats), vp, sz, vp]
     L.mf_cg_record_history.argtypes = [vp, i32]
+    L.mf_server_create.argtypes = [C.POINTER(mf_server_config), vp, sz, C.POINTER(vp)]
+    L.mf_batch_submit.argtypes = [vp, C.POINTER(mf_request), C.POINTER(C.c_uint64)]
+    L.mf_batch_poll.argtypes = [vp, C.c_uint64, C.POINTER(mf_result)]
+    L.mf_batch_cancel.argtypes = [vp, C.c_uint64]
+    L.mf_server_drain.argtypes = [vp, d]
+    L.mf_server_stats.argtypes = [vp, C.POINTER(mf_server_stats_t)]
+    L.mf_server_destroy.argtypes = [vp]
+    L.mf_server_destroy.restype = None
     _lib = L
     return L
 
@@ -127,6 +171,19 @@ def mf_operator_info(op) -> dict:
 
 def mf_operator_setup(op, workspace_ptr: int, nbytes: int, stream: int = 0) -> None:
     _check(lib().mf_operator_setup(op, workspace_ptr or None, nbytes, stream or None))
+
+
+def mf_operator_autotune(op, x_ptr: int, y_ptr: int, reps: int = 3, stream: int = 0) -> int:
+    _check(lib().mf_operator_autotune(op, x_ptr, y_ptr, reps, stream or None))
+    return int(lib().mf_operator_get_variant(op))
+
+
+def mf_operator_set_variant(op, variant: int) -> None:
+    _check(lib().mf_operator_set_variant(op, variant))
+
+
+def mf_operator_get_variant(op) -> int:
+    return int(lib().mf_operator_get_variant(op))
 
 
 # ---------------------------------------------------------------- vectors
@@ -180,6 +237,19 @@ def mf_dot_noalloc(op, a_ptr: int, b_ptr: int, result_ptr: int, split: int = 0, 
     _check(lib().mf_dot_noalloc(op, a_ptr, b_ptr, split, result_ptr, stream or None))
 
 
+def mf_manufactured_workspace_bytes(op) -> int:
+    return int(lib().mf_manufactured_workspace_bytes(op))
+
+
+def mf_rhs_manufactured(op, freq: float, b_ptr: int, scratch_ptr: int, scratch_bytes: int, stream: int = 0) -> None:
+    _check(lib().mf_rhs_manufactured(op, freq, b_ptr, scratch_ptr, scratch_bytes, stream or None))
+
+
+def mf_error_manufactured(op, freq: float, u_ptr: int, l2sq_ptr: int, scratch_ptr: int, scratch_bytes: int,
+                          stream: int = 0) -> None:
+    _check(lib().mf_error_manufactured(op, freq, u_ptr, l2sq_ptr, scratch_ptr, scratch_bytes, stream or None))
+
+
 def mf_cg_workspace_bytes(op, mixed: int = 0) -> int:
     return int(lib().mf_cg_workspace_bytes(op, mixed))
 
@@ -198,3 +268,52 @@ def mf_cg_solve(op, b_ptr: int, x_ptr: int, rtol: float, maxit: int, mixed: int,
 
 def mf_cg_record_history(hist_ptr: int | None, cap: int) -> None:
     _check(lib().mf_cg_record_history(hist_ptr, cap))
+
+
+# ---------------------------------------------------------------- serving
+def mf_server_create(arena_ptr: int, arena_bytes: int, max_slots: int = 32, queue_capacity: int = 0,
+                     chunk_iterations: int = 20, autotune: int = 0, inner_rtol: float = 1e-4):
+    cfg = mf_server_config(max_slots, queue_capacity, chunk_iterations, autotune, inner_rtol)
+    h = C.c_void_p()
+    _check(lib().mf_server_create(C.byref(cfg), arena_ptr, arena_bytes, C.byref(h)))
+    return h.value
+
+
+def make_request(nx, ny, nz, degree, kind=MF_LAPLACE, geometry=MF_AFFINE, mass_coeff=1.0, curve_amp=0.1,
+                 rhs=MF_RHS_MANUFACTURED, freq=2.0, seed=0, rtol=1e-10, maxit=200000, mixed=1, x_out_ptr=None):
+    return mf_request(nx, ny, nz, degree, kind, geometry, mass_coeff, curve_amp, rhs, freq, seed, rtol, maxit, mixed,
+                      x_out_ptr)
+
+
+def mf_batch_submit(server, req: mf_request) -> int:
+    t = C.c_uint64()
+    _check(lib().mf_batch_submit(server, C.byref(req), C.byref(t)))
+    return int(t.value)
+
+
+def mf_batch_poll(server, ticket: int):
+    """Returns None while the request is pending, else a dict of its mf_result."""
+    r = mf_result()
+    code = lib().mf_batch_poll(server, ticket, C.byref(r))
+    if code == MF_ERR_BUSY:
+        return None
+    _check(code)
+    return {f: getattr(r, f) for f, _ in mf_result._fields_}
+
+
+def mf_batch_cancel(server, ticket: int) -> None:
+    _check(lib().mf_batch_cancel(server, ticket))
+
+
+def mf_server_drain(server, timeout_s: float) -> None:
+    _check(lib().mf_server_drain(server, timeout_s))
+
+
+def mf_server_stats(server) -> dict:
+    st = mf_server_stats_t()
+    _check(lib().mf_server_stats(server, C.byref(st)))
+    return {f: getattr(st, f) for f, _ in mf_server_stats_t._fields_}
+
+
+def mf_server_destroy(server) -> None:
+    lib().mf_server_destroy(server)

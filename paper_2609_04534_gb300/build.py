@@ -19,6 +19,8 @@ INC = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INC, "-I", CSRC]
+# extra nvcc flags for tuning sweeps, e.g. MF_NVCC_FLAGS="-DMF_APPLY_MIN_BLOCKS=2"
+EXTRA = os.environ.get("MF_NVCC_FLAGS", "").split()
 
 
 def nvcc() -> str:
@@ -39,7 +41,7 @@ def _compile(src: str, extra) -> str:
     obj = os.path.join(OBJ, os.path.basename(src) + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= _deps_mtime():
         return obj
-    cmd = [nvcc(), *ARCH, *COMMON, *extra, "-c", src, "-o", obj + ".tmp"]
+    cmd = [nvcc(), *ARCH, *COMMON, *EXTRA, *extra, "-c", src, "-o", obj + ".tmp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")

@@ -3,7 +3,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 
 #include "mf_internal.h"
 
@@ -287,6 +290,64 @@ mf_status mf_apply_host(const mf_operator* op, const void* x_host, void* y_host,
   if ((st = mf_from_native(op, yn, can, stream))) return st;
   if ((st = cuda_check(cudaMemcpyAsync(y_host, can, cbytes, cudaMemcpyDeviceToHost, s), "mf_apply_host D2H"))) return st;
   return cuda_check(cudaStreamSynchronize(s), "mf_apply_host sync");
+}
+
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int, int>, int> g_tune_cache; // (device, n, path, kind, view) -> variant
+
+mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, int reps, void* stream) {
+  mf_status st = check_ready(op, "mf_operator_autotune");
+  if (st) return st;
+  if (!x_dev || !y_dev || x_dev == y_dev) return set_error(MF_ERR_ARG, "mf_operator_autotune: bad vectors");
+  if (reps < 1) reps = 3;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  if ((st = cuda_check(cudaGetDevice(&dev), "cudaGetDevice"))) return st;
+  const int vk = view_of_elem(op, elem_of(op));
+  const auto key = std::make_tuple(dev, op->n, op->path, op->kind, vk);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      op->variant[vk] = it->second;
+      return MF_OK;
+    }
+  }
+  cudaEvent_t e0, e1;
+  if ((st = cuda_check(cudaEventCreate(&e0), "event"))) return st;
+  if ((st = cuda_check(cudaEventCreate(&e1), "event"))) { cudaEventDestroy(e0); return st; }
+  float best = 1e30f;
+  int best_v = 0;
+  for (int v = 0; v < 2 && st == MF_OK; ++v) {
+    op->variant[vk] = v;
+    st = launch_apply_split(op, vk, x_dev, y_dev, s); // warm-up
+    if (st) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && st == MF_OK; ++r) st = launch_apply_split(op, vk, x_dev, y_dev, s);
+    cudaEventRecord(e1, s);
+    if (st) break;
+    if ((st = cuda_check(cudaEventSynchronize(e1), "autotune sync"))) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; best_v = v; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  op->variant[vk] = best_v;
+  if (st) return st;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = best_v;
+  return MF_OK;
+}
+
+mf_status mf_operator_set_variant(mf_operator* op, int variant) {
+  if (!op || variant < 0 || variant > 1) return set_error(MF_ERR_ARG, "mf_operator_set_variant: bad argument");
+  op->variant[VK_F64] = op->variant[VK_DD] = op->variant[VK_F32] = variant;
+  return MF_OK;
+}
+
+int mf_operator_get_variant(const mf_operator* op) {
+  return op ? op->variant[view_of_elem(op, elem_of(op))] : -1;
 }
 
 } // extern "C"

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "mf_internal.h"
+#include "mf_solver.h"
 
 namespace mf {
 
@@ -30,18 +31,7 @@ struct RedScratch {
 
 size_t reduce_scratch_bytes() { return sizeof(RedScratch); }
 
-// Device-resident CG scalars.
-struct CgState {
-  double rr;      // <r, r> (assembled)
-  double pq;      // <p, A p>
-  double alpha, beta;
-  double bnorm;   // ||b||
-  double tol2;    // (rtol * ||b||)^2
-  int it;         // iterations done
-  int flag;       // 0 running, 1 converged, 2 breakdown
-  int maxit;
-  int pad;
-};
+
 
 // Weight of native element e in an assembled inner product: 0 for padding, otherwise
 // 1 / (number of cells sharing the node).  split = 1: 1 for every real copy.
@@ -327,18 +317,7 @@ static size_t a256(size_t b) { return (b + 255) & ~size_t(255); }
 static thread_local double* g_hist_host = nullptr;
 static thread_local int g_hist_cap = 0;
 
-// Workspace layout of a solve.
-struct SolveWs {
-  CgState* st;
-  RedScratch *sc1, *sc2, *sc3;
-  double* hist;
-  double* scal; // misc FP64 scalars (residual norms)
-  void *r, *p, *q;          // CG vectors of the (inner) element type
-  void *r64, *q64, *b64;    // mixed: FP64 outer residual, A x, masked b
-  void* d32;                // mixed: inner solution
-};
-
-static size_t layout_ws(const mf_operator* op, int mixed, char* base, SolveWs* w) {
+size_t solve_ws_layout(const mf_operator* op, int mixed, char* base, SolveWs* w) {
   size_t off = 0;
   auto take = [&](size_t bytes) -> char* { char* p = base ? base + off : nullptr; off += a256(bytes); return p; };
   const size_t n = (size_t)op->n_native;
@@ -364,85 +343,189 @@ static size_t layout_ws(const mf_operator* op, int mixed, char* base, SolveWs* w
   return off;
 }
 
-// Inner/plain CG: solves A x = rhs (rhs already masked) from x = 0 with vectors of `elem`.
-// Uses a CUDA graph of `chunk` iterations, reads the scalars back after each graph.
-static mf_status run_cg(const mf_operator* op, int elem, const void* rhs, void* x, double rtol, int maxit,
-                        const SolveWs& w, cudaStream_t s, int* iters_out, double* relres_out, int record,
-                        int* hist_off) {
-  mf_status st;
-  const long long n = op->n_native;
-  // x = 0, r = rhs, p = rhs, rr = <r, r>
-  if (elem == 8) {
-    zero_kernel<double><<<ew_blocks(n), 256, 0, s>>>((double*)x, n);
-    copy_kernel<double><<<ew_blocks(n), 256, 0, s>>>((const double*)rhs, (double*)w.r, n);
-    copy_kernel<double><<<ew_blocks(n), 256, 0, s>>>((const double*)rhs, (double*)w.p, n);
-  } else {
-    zero_kernel<float><<<ew_blocks(n), 256, 0, s>>>((float*)x, n);
-    copy_kernel<float><<<ew_blocks(n), 256, 0, s>>>((const float*)rhs, (float*)w.r, n);
-    copy_kernel<float><<<ew_blocks(n), 256, 0, s>>>((const float*)rhs, (float*)w.p, n);
-  }
-  if ((st = cuda_check(cudaGetLastError(), "cg init"))) return st;
-  if ((st = cuda_check(cudaMemsetAsync(w.sc1, 0, sizeof(unsigned) * 64, s), "memset"))) return st;
-  if ((st = cuda_check(cudaMemsetAsync(w.sc2, 0, sizeof(unsigned) * 64, s), "memset"))) return st;
-  if ((st = cuda_check(cudaMemsetAsync(w.sc3, 0, sizeof(unsigned) * 64, s), "memset"))) return st;
-  if ((st = dot_launch(op, elem, w.r, w.r, 0, w.scal, w.sc3, s))) return st;
-  double rr0 = 0.0;
-  if ((st = cuda_check(cudaMemcpyAsync(&rr0, w.scal, sizeof(double), cudaMemcpyDeviceToHost, s), "D2H"))) return st;
-  if ((st = cuda_check(cudaStreamSynchronize(s), "sync"))) return st;
-  if (!std::isfinite(rr0)) return set_error(MF_ERR_BREAKDOWN, "CG: non-finite right-hand side");
+// CG state from the first residual norm (kept on the device: no host round trip).
+__global__ void init_state_kernel(CgState* st, const double* rr0, double rtol, int maxit) {
+  const double rr = *rr0;
   CgState h;
-  std::memset(&h, 0, sizeof(h));
-  h.rr = rr0;
-  h.bnorm = std::sqrt(rr0);
+  h.rr = rr;
+  h.pq = h.alpha = h.beta = 0.0;
+  h.bnorm = sqrt(rr);
   h.tol2 = (rtol * h.bnorm) * (rtol * h.bnorm);
+  h.it = 0;
   h.maxit = maxit;
-  h.flag = (rr0 <= h.tol2 || rr0 == 0.0) ? 1 : 0;
-  if ((st = cuda_check(cudaMemcpyAsync(w.st, &h, sizeof(h), cudaMemcpyHostToDevice, s), "H2D"))) return st;
-  const int chunk = 20;
-  cudaGraphExec_t exec = nullptr;
-  cudaGraph_t graph = nullptr;
-  int done_flag = h.flag;
-  int it = 0;
-  while (done_flag == 0) {
-    if (!exec) {
-      if ((st = cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture begin"))) return st;
-      mf_status cst = MF_OK;
-      for (int c = 0; c < chunk && cst == MF_OK; ++c) {
-        cst = apply_elem(op, elem, w.p, w.q, s);
-        if (cst == MF_OK) cst = launch_cg_vec(op, elem, x, w.r, w.p, w.q, w.sc1, w.sc2, w.st, w.hist, s);
-      }
-      cudaError_t e = cudaStreamEndCapture(s, &graph);
-      if (cst) { if (graph) cudaGraphDestroy(graph); return cst; }
-      if ((st = cuda_check(e, "capture end"))) return st;
-      if ((st = cuda_check(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate"))) { cudaGraphDestroy(graph); return st; }
-    }
-    if ((st = cuda_check(cudaGraphLaunch(exec, s), "graph launch"))) break;
-    if ((st = cuda_check(cudaMemcpyAsync(&h, w.st, sizeof(h), cudaMemcpyDeviceToHost, s), "D2H"))) break;
-    if ((st = cuda_check(cudaStreamSynchronize(s), "sync"))) break;
-    done_flag = h.flag;
-    it = h.it;
+  h.pad = 0;
+  h.flag = !isfinite(rr) ? 2 : ((rr <= h.tol2 || rr == 0.0) ? 1 : (maxit <= 0 ? 3 : 0));
+  *st = h;
+}
+
+// ---------------------------------------------------------------- solver engine
+// Phase machine shared by the synchronous mf_cg_solve and the server.  Every phase enqueues
+// its GPU work and one small device-to-host copy into the host mirror; the caller advances
+// the engine once that copy has landed (stream synchronise, or an event recorded after it).
+
+// start an inner (or plain) CG on rhs (already masked) into x_in with tolerance rtol
+static mf_status eng_inner_start(SolverEngine* e, const void* rhs, void* x_in, double rtol, int maxit) {
+  const long long n = e->op->n_native;
+  cudaStream_t s = e->s;
+  const int el = e->elem_in;
+  if (el == 8) {
+    zero_kernel<double><<<ew_blocks(n), 256, 0, s>>>((double*)x_in, n);
+    copy_kernel<double><<<ew_blocks(n), 256, 0, s>>>((const double*)rhs, (double*)e->w.r, n);
+    copy_kernel<double><<<ew_blocks(n), 256, 0, s>>>((const double*)rhs, (double*)e->w.p, n);
+  } else {
+    zero_kernel<float><<<ew_blocks(n), 256, 0, s>>>((float*)x_in, n);
+    copy_kernel<float><<<ew_blocks(n), 256, 0, s>>>((const float*)rhs, (float*)e->w.r, n);
+    copy_kernel<float><<<ew_blocks(n), 256, 0, s>>>((const float*)rhs, (float*)e->w.p, n);
   }
-  if (exec) cudaGraphExecDestroy(exec);
-  if (graph) cudaGraphDestroy(graph);
+  mf_status st = cuda_check(cudaGetLastError(), "cg init");
   if (st) return st;
-  it = h.it;
-  if (record && g_hist_host && hist_off) {
-    // hist[1..it] = relative residual per iteration of this run
-    int take = it;
-    if (take > HIST_CAP - 1) take = HIST_CAP - 1;
-    if (*hist_off + take + 1 > g_hist_cap) take = g_hist_cap - *hist_off - 1;
-    if (take > 0) {
-      st = cuda_check(cudaMemcpy(g_hist_host + *hist_off + 1, w.hist + 1, sizeof(double) * take, cudaMemcpyDeviceToHost), "hist D2H");
-      if (st) return st;
+  if ((st = dot_launch(e->op, el, e->w.r, e->w.r, 0, e->w.scal, e->w.sc3, s))) return st;
+  init_state_kernel<<<1, 1, 0, s>>>(e->w.st, e->w.scal, rtol, maxit);
+  if ((st = cuda_check(cudaGetLastError(), "init state"))) return st;
+  e->phase = PH_INNER;
+  return cuda_check(cudaMemcpyAsync(&e->hm->st, e->w.st, sizeof(CgState), cudaMemcpyDeviceToHost, s), "state D2H");
+}
+
+static mf_status eng_chunk(SolverEngine* e) {
+  cudaStream_t s = e->s;
+  mf_status st;
+  if (!e->exec) {
+    if ((st = cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture begin"))) return st;
+    mf_status cst = MF_OK;
+    for (int c = 0; c < e->chunk && cst == MF_OK; ++c) {
+      cst = apply_elem(e->op, e->elem_in, e->w.p, e->w.q, s);
+      if (cst == MF_OK)
+        cst = launch_cg_vec(e->op, e->elem_in, e->x_in, e->w.r, e->w.p, e->w.q, e->w.sc1, e->w.sc2, e->w.st, e->w.hist, s);
     }
-    if (*hist_off < g_hist_cap) g_hist_host[*hist_off] = 1.0;
-    *hist_off += take + 1;
+    cudaError_t ce = cudaStreamEndCapture(s, &e->graph);
+    if (cst) {
+      if (e->graph) { cudaGraphDestroy(e->graph); e->graph = nullptr; }
+      return cst;
+    }
+    if ((st = cuda_check(ce, "capture end"))) return st;
+    if ((st = cuda_check(cudaGraphInstantiate(&e->exec, e->graph, 0), "graph instantiate"))) return st;
   }
-  *iters_out = it;
-  *relres_out = (h.bnorm > 0) ? std::sqrt(h.rr) / h.bnorm : 0.0;
-  if (h.flag == 2) return set_error(MF_ERR_BREAKDOWN, "CG breakdown (p^T A p <= 0 or non-finite) at iteration %d", it);
-  if (h.flag == 3) return MF_ERR_NOT_CONVERGED;
+  if ((st = cuda_check(cudaGraphLaunch(e->exec, s), "graph launch"))) return st;
+  return cuda_check(cudaMemcpyAsync(&e->hm->st, e->w.st, sizeof(CgState), cudaMemcpyDeviceToHost, s), "state D2H");
+}
+
+// mixed: r64 = b - A x (or b when x = 0); ||b||^2 and ||r||^2 to the host mirror
+static mf_status eng_outer_residual(SolverEngine* e, bool first) {
+  const long long n = e->op->n_native;
+  cudaStream_t s = e->s;
+  mf_status st;
+  double* b = (double*)e->w.b64;
+  double* r = (double*)e->w.r64;
+  if (first) {
+    copy_kernel<double><<<ew_blocks(n), 256, 0, s>>>(b, r, n);
+    if ((st = dot_launch(e->op, 8, b, b, 0, e->w.scal + 1, e->w.sc3, s))) return st;
+  } else {
+    if ((st = apply_elem(e->op, 8, e->x, e->w.q64, s))) return st;
+    sub_kernel<<<ew_blocks(n), 256, 0, s>>>(b, (const double*)e->w.q64, r, n);
+  }
+  if ((st = dot_launch(e->op, 8, r, r, 0, e->w.scal + 2, e->w.sc3, s))) return st;
+  e->phase = PH_OUTER;
+  return cuda_check(cudaMemcpyAsync(&e->hm->bn2, e->w.scal + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, s),
+                    "residual D2H");
+}
+
+mf_status engine_init(SolverEngine* e, const mf_operator* op, int mixed, const void* b, void* x, double rtol, int maxit,
+                      void* ws, cudaStream_t s, HostMirror* hm) {
+  e->op = op;
+  e->mixed = mixed;
+  e->elem_in = mixed ? 4 : (op->precision == MF_FP32 ? 4 : 8);
+  e->s = s;
+  solve_ws_layout(op, mixed, static_cast<char*>(ws), &e->w);
+  e->b = b;
+  e->x = x;
+  e->x_in = mixed ? e->w.d32 : x;
+  e->rtol = rtol;
+  e->maxit = maxit;
+  e->hm = hm;
+  e->phase = 0;
+  e->total_it = e->outer = 0;
+  e->bn = e->rel = 0.0;
+  e->status = MF_OK;
+  e->exec = nullptr;
+  e->graph = nullptr;
+  e->cancel = false;
   return MF_OK;
+}
+
+mf_status engine_start(SolverEngine* e) {
+  mf_status st;
+  const long long n = e->op->n_native;
+  // the reductions find their last CTA with a counter that must start at zero (it resets
+  // itself after every launch); the workspace may hold anything
+  for (RedScratch* sc : {e->w.sc1, e->w.sc2, e->w.sc3})
+    if ((st = cuda_check(cudaMemsetAsync(sc, 0, sizeof(unsigned) * 64, e->s), "counter clear"))) return st;
+  if (!e->mixed) {
+    if ((st = launch_mask(e->op, e->elem_in, e->b, e->w.q, e->s))) return st;
+    return eng_inner_start(e, e->w.q, e->x, e->rtol, e->maxit);
+  }
+  if ((st = launch_mask(e->op, 8, e->b, e->w.b64, e->s))) return st;
+  zero_kernel<double><<<ew_blocks(n), 256, 0, e->s>>>((double*)e->x, n);
+  return eng_outer_residual(e, true);
+}
+
+static void eng_record_history(SolverEngine* e, int it) {
+  if (!e->record || !g_hist_host) return;
+  int take = it;
+  if (take > HIST_CAP - 1) take = HIST_CAP - 1;
+  if (e->hist_off + take + 1 > g_hist_cap) take = g_hist_cap - e->hist_off - 1;
+  if (e->hist_off < g_hist_cap) g_hist_host[e->hist_off] = 1.0;
+  if (take > 0) cudaMemcpy(g_hist_host + e->hist_off + 1, e->w.hist + 1, sizeof(double) * take, cudaMemcpyDeviceToHost);
+  e->hist_off += take + 1;
+}
+
+static mf_status eng_finish(SolverEngine* e, mf_status st) {
+  e->status = st;
+  e->phase = PH_DONE;
+  return MF_OK;
+}
+
+mf_status engine_advance(SolverEngine* e) {
+  if (e->phase == PH_DONE) return MF_OK;
+  mf_status st;
+  const long long n = e->op->n_native;
+  if (e->phase == PH_INNER) {
+    const CgState& h = e->hm->st;
+    if (h.flag == 0 && !e->cancel) return eng_chunk(e);
+    eng_record_history(e, h.it);
+    e->total_it += h.it;
+    if (!e->mixed) {
+      e->rel = (h.bnorm > 0) ? std::sqrt(h.rr) / h.bnorm : 0.0;
+      if (e->cancel) return eng_finish(e, MF_ERR_BUSY);
+      if (h.flag == 2)
+        return eng_finish(e, set_error(MF_ERR_BREAKDOWN, "CG breakdown (p^T A p <= 0 or non-finite) at iteration %d", h.it));
+      return eng_finish(e, h.flag == 3 ? MF_ERR_NOT_CONVERGED : MF_OK);
+    }
+    if (h.flag == 2) return eng_finish(e, set_error(MF_ERR_BREAKDOWN, "inner CG breakdown at iteration %d", h.it));
+    axpy64_kernel<<<ew_blocks(n), 256, 0, e->s>>>((double*)e->x, (const float*)e->w.d32, e->w.scal + 2, n);
+    e->outer += 1;
+    return eng_outer_residual(e, false);
+  }
+  if (e->phase == PH_OUTER) {
+    const double bn2 = e->hm->bn2, rn2 = e->hm->rn2;
+    if (!std::isfinite(bn2) || !std::isfinite(rn2))
+      return eng_finish(e, set_error(MF_ERR_BREAKDOWN, "mf_cg_solve: non-finite residual"));
+    e->bn = std::sqrt(bn2);
+    e->rel = e->bn > 0 ? std::sqrt(rn2) / e->bn : 0.0;
+    if (e->rel <= e->rtol || e->bn == 0.0) return eng_finish(e, MF_OK);
+    if (e->cancel) return eng_finish(e, MF_ERR_BUSY);
+    if (e->outer >= e->max_outer || e->total_it >= e->maxit) return eng_finish(e, MF_ERR_NOT_CONVERGED);
+    to32_kernel<<<ew_blocks(n), 256, 0, e->s>>>((const double*)e->w.r64, (float*)e->w.q, e->w.scal + 2, n);
+    if ((st = cuda_check(cudaGetLastError(), "to32"))) return st;
+    return eng_inner_start(e, e->w.q, e->w.d32, e->inner_rtol, e->maxit - e->total_it);
+  }
+  return set_error(MF_ERR_ARG, "solver engine: advance before start");
+}
+
+void engine_release(SolverEngine* e) {
+  if (e->exec) cudaGraphExecDestroy(e->exec);
+  if (e->graph) cudaGraphDestroy(e->graph);
+  e->exec = nullptr;
+  e->graph = nullptr;
 }
 
 } // namespace mf
@@ -472,7 +555,7 @@ mf_status mf_cg_record_history(double* hist_host, int cap) {
 
 size_t mf_cg_workspace_bytes(const mf_operator* op, int mixed) {
   if (!op) return 0;
-  return layout_ws(op, mixed ? 1 : 0, nullptr, nullptr);
+  return solve_ws_layout(op, mixed ? 1 : 0, nullptr, nullptr);
 }
 
 mf_status mf_cg_solve(const mf_operator* op, const void* b_dev, void* x_dev, double rtol, int maxit, int mixed,
@@ -495,84 +578,38 @@ mf_status mf_cg_solve(const mf_operator* op, const void* b_dev, void* x_dev, dou
   }
   struct StreamGuard {
     cudaStream_t st;
-    ~StreamGuard() { if (st) { cudaStreamSynchronize(st); cudaStreamDestroy(st); } }
+    ~StreamGuard() {
+      if (st) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
+    }
   } guard{own};
-  SolveWs w;
-  layout_ws(op, mixed ? 1 : 0, static_cast<char*>(workspace_dev), &w);
   const auto t0 = std::chrono::steady_clock::now();
+  HostMirror hm;
+  std::memset(&hm, 0, sizeof(hm));
+  SolverEngine e;
+  engine_init(&e, op, mixed ? 1 : 0, b_dev, x_dev, rtol, maxit, workspace_dev, s, &hm);
+  e.record = g_hist_host != nullptr;
+  mf_status st = engine_start(&e);
+  // every advance either finishes or moves the iteration count forward by a chunk; bound the
+  // host loop anyway so that a device state that stops changing cannot spin it forever
+  const long long max_steps = 2LL * ((long long)maxit / e.chunk + 2) * (e.max_outer + 2) + 16;
+  long long steps = 0;
+  while (st == MF_OK && e.phase != PH_DONE) {
+    if ((st = cuda_check(cudaStreamSynchronize(s), "mf_cg_solve sync"))) break;
+    if (++steps > max_steps) {
+      st = set_error(MF_ERR_TIMEOUT, "mf_cg_solve: no progress after %lld steps", steps);
+      break;
+    }
+    st = engine_advance(&e);
+  }
+  engine_release(&e);
+  cudaStreamSynchronize(s);
+  if (st == MF_OK) st = e.status;
   mf_solve_stats out;
   std::memset(&out, 0, sizeof(out));
-  out.check_every = 20;
-  mf_status st = MF_OK;
-  int hist_off = 0;
-  if (!mixed) {
-    const int elem = op->precision == MF_FP32 ? 4 : 8;
-    // rhs = P b into q (scratch), then solve
-    if ((st = launch_mask(op, elem, b_dev, w.q, s))) return st;
-    // run_cg copies rhs into r and p before touching q again
-    int it = 0;
-    double rel = 0.0;
-    st = run_cg(op, elem, w.q, x_dev, rtol, maxit, w, s, &it, &rel, 1, &hist_off);
-    out.iterations = it;
-    out.outer_iterations = 1;
-    out.rel_residual = rel;
-    if (st == MF_OK || st == MF_ERR_NOT_CONVERGED) {
-      // report the true residual ||P b - A x|| / ||P b|| in FP64 is only exact for FP64; keep recursive value
-    }
-  } else {
-    // FP64 defect correction with an FP32 inner CG (precision pattern of the solver)
-    const long long n = op->n_native;
-    double* x = static_cast<double*>(x_dev);
-    double* b = static_cast<double*>(w.b64);
-    double* r = static_cast<double*>(w.r64);
-    double* q = static_cast<double*>(w.q64);
-    if ((st = launch_mask(op, 8, b_dev, b, s))) return st;
-    zero_kernel<double><<<ew_blocks(n), 256, 0, s>>>(x, n);
-    if ((st = cuda_check(cudaMemsetAsync(w.sc3, 0, sizeof(unsigned) * 64, s), "memset"))) return st;
-    if ((st = dot_launch(op, 8, b, b, 0, w.scal + 1, w.sc3, s))) return st;
-    double bn2 = 0.0;
-    if ((st = cuda_check(cudaMemcpyAsync(&bn2, w.scal + 1, 8, cudaMemcpyDeviceToHost, s), "D2H"))) return st;
-    if ((st = cuda_check(cudaStreamSynchronize(s), "sync"))) return st;
-    if (!std::isfinite(bn2)) return set_error(MF_ERR_BREAKDOWN, "mf_cg_solve: non-finite right-hand side");
-    const double bn = std::sqrt(bn2);
-    const double inner_tol = 1e-4;
-    int total_it = 0, outer = 0;
-    double rel = bn > 0 ? 1.0 : 0.0;
-    const int max_outer = 60;
-    while (true) {
-      // r = b - A x  (FP64 apply)
-      if (outer == 0) {
-        copy_kernel<double><<<ew_blocks(n), 256, 0, s>>>(b, r, n);
-      } else {
-        if ((st = apply_elem(op, 8, x, q, s))) break;
-        sub_kernel<<<ew_blocks(n), 256, 0, s>>>(b, q, r, n);
-      }
-      // outer ||r||^2 lives in scal[2]: the inner CG uses scal[0] for its own norms
-      double* rn2_dev = w.scal + 2;
-      if ((st = dot_launch(op, 8, r, r, 0, rn2_dev, w.sc3, s))) break;
-      double rn2 = 0.0;
-      if ((st = cuda_check(cudaMemcpyAsync(&rn2, rn2_dev, 8, cudaMemcpyDeviceToHost, s), "D2H"))) break;
-      if ((st = cuda_check(cudaStreamSynchronize(s), "sync"))) break;
-      rel = bn > 0 ? std::sqrt(rn2) / bn : 0.0;
-      if (rel <= rtol || bn == 0.0) { st = MF_OK; break; }
-      if (outer >= max_outer || total_it >= maxit) { st = MF_ERR_NOT_CONVERGED; break; }
-      // inner: A32 d = r / ||r||
-      to32_kernel<<<ew_blocks(n), 256, 0, s>>>(r, static_cast<float*>(w.q), rn2_dev, n);
-      int it = 0;
-      double irel = 0.0;
-      const int inner_max = maxit - total_it;
-      mf_status ist = run_cg(op, 4, w.q, w.d32, inner_tol, inner_max, w, s, &it, &irel, 1, &hist_off);
-      total_it += it;
-      if (ist == MF_ERR_BREAKDOWN) { st = ist; break; }
-      if (ist != MF_OK && ist != MF_ERR_NOT_CONVERGED) { st = ist; break; }
-      axpy64_kernel<<<ew_blocks(n), 256, 0, s>>>(x, static_cast<const float*>(w.d32), rn2_dev, n);
-      ++outer;
-    }
-    out.iterations = total_it;
-    out.outer_iterations = outer;
-    out.rel_residual = rel;
-  }
-  cudaStreamSynchronize(s);
+  out.iterations = e.total_it;
+  out.outer_iterations = mixed ? e.outer : 1;
+  out.rel_residual = e.rel;
+  out.check_every = e.chunk;
   out.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   out.status = st;
   if (stats) *stats = out;

@@ -87,6 +87,7 @@ struct mf_operator {
   void* workspace = nullptr;
   size_t workspace_bytes = 0;
   bool ready = false;
+  int variant[3] = {0, 0, 0}; // apply launch variant per ViewKind (autotuned)
 };
 
 namespace mf {

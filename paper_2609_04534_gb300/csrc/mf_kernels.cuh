@@ -11,9 +11,14 @@ namespace mf {
 
 // Cells processed by one CTA of the apply kernels (a divisor of BL).  One thread owns one
 // pencil (a 1D line of n values) of one cell in every sweep, so a CTA has n^2 * CB threads.
-template <typename T, int N>
+// Launch configurations of the apply kernels, chosen per operator by the autotuner
+// (mf_operator_autotune): variant 0 = CB0 cells per CTA with registers capped for 2 resident
+// CTAs per SM; variant 1 = CB0/2 cells per CTA, capped for 3 resident CTAs per SM.
+template <typename T, int N, int V>
 struct Cfg {
-  static constexpr int CB = (N <= 4) ? 32 : (N <= 6) ? 16 : (N <= 8) ? 8 : (sizeof(T) == 4 ? 8 : 4);
+  static constexpr int CB0 = (N <= 4) ? 32 : (N <= 6) ? 16 : (N <= 8) ? 8 : (sizeof(T) == 4 ? 8 : 4);
+  static constexpr int CB = V == 0 ? CB0 : ((CB0 / 2) >= 4 ? (CB0 / 2) : 4);
+  static constexpr int MINB = V == 0 ? 2 : 3;
   static constexpr int NT = N * N * CB;
 };
 
@@ -86,8 +91,8 @@ __device__ __forceinline__ void store_xpencil(const ApplyArgs<S, T, N>& a, long 
 // (Kronecker factors listed z, y, x).  x-sweep: M and K (2); y-sweep: M on Mx, K on Mx, M on
 // Kx (3); z-sweep: M on the combination and K on (M(x)M)x (2).
 // ---------------------------------------------------------------------------------------
-template <typename S, typename T, int N, int CB, bool HELM>
-__global__ void __launch_bounds__(N * N * CB) apply_cartesian(ApplyArgs<S, T, N> a) {
+template <typename S, typename T, int N, int CB, int MINB, bool HELM>
+__global__ void __launch_bounds__(N * N * CB, MINB) apply_cartesian(ApplyArgs<S, T, N> a) {
   constexpr int N2 = N * N, N3 = N2 * N, NT = N2 * CB, GPT = BL / CB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* buf0 = reinterpret_cast<T*>(smem_raw);
@@ -170,8 +175,8 @@ __global__ void __launch_bounds__(N * N * CB) apply_cartesian(ApplyArgs<S, T, N>
 // derivative Dc (three sweeps), v = G grad u at every point (6 metric entries; Helmholtz adds
 // m u), then the transposes: Dc^T per direction summed, and S^T along z, y, x.
 // ---------------------------------------------------------------------------------------
-template <typename S, typename T, int N, int CB, bool CURVED, bool HELM>
-__global__ void __launch_bounds__(N * N * CB) apply_general(ApplyArgs<S, T, N> a) {
+template <typename S, typename T, int N, int CB, int MINB, bool CURVED, bool HELM>
+__global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T, N> a) {
   constexpr int N2 = N * N, N3 = N2 * N, NT = N2 * CB, GPT = BL / CB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* buf0 = reinterpret_cast<T*>(smem_raw);
@@ -515,9 +520,9 @@ static void fill_args(const mf_operator* op, ApplyArgs<S, T, N>& a) {
   }
 }
 
-template <typename S, typename T, int N>
-static mf_status apply_split_t(const mf_operator* op, const void* x, void* y, const void* geom, cudaStream_t s) {
-  using C = Cfg<T, N>;
+template <typename S, typename T, int N, int V>
+static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, const void* geom, cudaStream_t s) {
+  using C = Cfg<T, N, V>;
   ApplyArgs<S, T, N> a;
   fill_args<S, T, N>(op, a);
   a.x = static_cast<const S*>(x);
@@ -529,11 +534,11 @@ static mf_status apply_split_t(const mf_operator* op, const void* x, void* y, co
   const bool helm = op->kind == MF_HELMHOLTZ;
   void (*k)(ApplyArgs<S, T, N>) = nullptr;
   if (op->path == PATH_CARTESIAN)
-    k = helm ? apply_cartesian<S, T, N, C::CB, true> : apply_cartesian<S, T, N, C::CB, false>;
+    k = helm ? apply_cartesian<S, T, N, C::CB, C::MINB, true> : apply_cartesian<S, T, N, C::CB, C::MINB, false>;
   else if (op->path == PATH_AFFINE)
-    k = helm ? apply_general<S, T, N, C::CB, false, true> : apply_general<S, T, N, C::CB, false, false>;
+    k = helm ? apply_general<S, T, N, C::CB, C::MINB, false, true> : apply_general<S, T, N, C::CB, C::MINB, false, false>;
   else
-    k = helm ? apply_general<S, T, N, C::CB, true, true> : apply_general<S, T, N, C::CB, true, false>;
+    k = helm ? apply_general<S, T, N, C::CB, C::MINB, true, true> : apply_general<S, T, N, C::CB, C::MINB, true, false>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(apply)");
@@ -542,13 +547,20 @@ static mf_status apply_split_t(const mf_operator* op, const void* x, void* y, co
   return cuda_check(cudaGetLastError(), "apply launch");
 }
 
+template <typename S, typename T, int N>
+static mf_status apply_split_t(const mf_operator* op, int variant, const void* x, void* y, const void* geom,
+                               cudaStream_t s) {
+  return variant == 1 ? apply_split_v<S, T, N, 1>(op, x, y, geom, s) : apply_split_v<S, T, N, 0>(op, x, y, geom, s);
+}
+
 // vk: VK_F64 (double storage, native FP64 compute), VK_DD (double storage, double-float
 // compute), VK_F32 (float storage and compute).
 template <int N>
 mf_status apply_split_n(const mf_operator* op, int vk, const void* x, void* y, cudaStream_t s) {
-  if (vk == VK_F64) return apply_split_t<double, double, N>(op, x, y, op->v64.geom, s);
-  if (vk == VK_DD) return apply_split_t<double, dd, N>(op, x, y, op->v64.geom, s);
-  return apply_split_t<float, float, N>(op, x, y, op->v32.geom, s);
+  const int v = op->variant[vk];
+  if (vk == VK_F64) return apply_split_t<double, double, N>(op, v, x, y, op->v64.geom, s);
+  if (vk == VK_DD) return apply_split_t<double, dd, N>(op, v, x, y, op->v64.geom, s);
+  return apply_split_t<float, float, N>(op, v, x, y, op->v32.geom, s);
 }
 
 template <int N>

@@ -1,0 +1,75 @@
+// mf_solver.h -- CG state and the asynchronous solver engine shared by mf_cg_solve (one
+// request, host waits on the stream) and the server (many requests, host polls events).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "mf_internal.h"
+
+namespace mf {
+
+// Device-resident CG scalars.
+struct CgState {
+  double rr;    // <r, r> (assembled)
+  double pq;    // <p, A p>
+  double alpha, beta;
+  double bnorm; // ||b|| of this CG
+  double tol2;  // (rtol * ||b||)^2
+  int it;       // iterations done
+  int flag;     // 0 running, 1 converged, 2 breakdown, 3 maxit
+  int maxit;
+  int pad;
+};
+
+struct RedScratch;
+
+// Workspace layout of a solve (all device pointers inside the caller's workspace).
+struct SolveWs {
+  CgState* st;
+  RedScratch *sc1, *sc2, *sc3;
+  double* hist;
+  double* scal;          // [0] inner <r,r>, [1] outer ||b||^2, [2] outer ||r||^2
+  void *r, *p, *q;       // CG vectors of the (inner) element type
+  void *r64, *q64, *b64; // mixed: FP64 outer residual, A x, masked b
+  void* d32;             // mixed: inner solution
+};
+
+// Host copy of the scalars each phase reports (pinned memory when used asynchronously).
+struct HostMirror {
+  CgState st;
+  double bn2, rn2;
+  double pad[6];
+};
+
+enum { PH_INNER = 1, PH_OUTER = 2, PH_DONE = 3 };
+
+struct SolverEngine {
+  const mf_operator* op = nullptr;
+  int mixed = 0, elem_in = 8;
+  cudaStream_t s = nullptr;
+  SolveWs w{};
+  const void* b = nullptr;
+  void* x = nullptr;
+  void* x_in = nullptr;
+  double rtol = 0.0, inner_rtol = 1e-4;
+  int maxit = 0, chunk = 20, max_outer = 60;
+  HostMirror* hm = nullptr;
+  int phase = 0, total_it = 0, outer = 0;
+  double bn = 0.0, rel = 0.0;
+  mf_status status = MF_OK;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  bool record = false, cancel = false;
+  int hist_off = 0;
+};
+
+size_t solve_ws_layout(const mf_operator* op, int mixed, char* base, SolveWs* w);
+mf_status engine_init(SolverEngine* e, const mf_operator* op, int mixed, const void* b, void* x, double rtol, int maxit,
+                      void* ws, cudaStream_t s, HostMirror* hm);
+// Enqueue the first phase (ends with a D2H copy into e->hm).
+mf_status engine_start(SolverEngine* e);
+// Called once the last enqueued D2H copy has landed: decides and enqueues the next phase, or
+// marks the engine done (e->phase == PH_DONE, result in e->status).
+mf_status engine_advance(SolverEngine* e);
+void engine_release(SolverEngine* e);
+
+} // namespace mf

@@ -6,6 +6,7 @@
 """
 import numpy as np
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 from numpy.polynomial import legendre as npleg
 
 
@@ -74,3 +75,12 @@ def probe_dense(op):
         e[g] = 1.0
         A[:, g] = op.apply(e)
     return A
+
+
+def solve_direct(op, b):
+    """Dirichlet solve (P A P) u = P b with the brute-force assembled matrix (sparse LU)."""
+    A = assemble_csr(op, dirichlet=True)
+    free = ~op.boundary_mask()
+    u = np.zeros(op.n_unique)
+    u[free] = spla.spsolve(A[free][:, free].tocsc(), b[free])
+    return u

@@ -223,3 +223,23 @@ def test_full_size_helmholtz_sweep_sampled(oracle, k, N, prec):
     o = oracle_op(oracle, N, N, N, k, "cart", 1.0, 0)
     check_sampled(o, xu, y, 1e-12, seed=k, nsample=60)
     d.close()
+
+
+@pytest.mark.parametrize("k,geom,prec", [(2, "cart", mf.MF_FP64), (4, "curved", mf.MF_FP64), (5, "curved", mf.MF_FP32),
+                                         (8, "shear", mf.MF_FP64), (3, "curved", mf.MF_FP64_DFMA)])
+def test_launch_variants_agree_bitwise_and_autotune(k, geom, prec):
+    """Both launch configurations run the same per-thread arithmetic: bitwise equal output.
+    The autotuner picks one of them and leaves the result unchanged."""
+    d = DevOp(5, 6, 3, k, geom, mf.MF_HELMHOLTZ, 1.0, prec, 0)
+    xn = d.native_from_unique(inputs.random_unique(5, 6, 3, k, 13))
+    mf.mf_operator_set_variant(d.op, 0)
+    y0 = d.apply(xn)
+    mf.mf_operator_set_variant(d.op, 1)
+    y1 = d.apply(xn)
+    torch.cuda.synchronize()
+    assert torch.equal(y0, y1)
+    scratch = torch.empty_like(xn)
+    v = mf.mf_operator_autotune(d.op, xn.data_ptr(), scratch.data_ptr(), 2)
+    assert v in (0, 1)
+    assert torch.equal(d.apply(xn), y0)
+    d.close()

@@ -6,19 +6,8 @@ import math
 
 import numpy as np
 import pytest
-import scipy.sparse as sp
-import scipy.sparse.linalg as spla
 
-from tests._fem_ref import assemble_csr
-
-
-def solve_direct(op, b):
-    A = assemble_csr(op, dirichlet=True)
-    free = ~op.boundary_mask()
-    u = np.zeros(op.n_unique)
-    Af = A[free][:, free].tocsc()
-    u[free] = spla.spsolve(Af, b[free])
-    return u
+from tests._fem_ref import solve_direct
 
 
 @pytest.mark.parametrize("k,geom,Ns", [
