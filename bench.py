@@ -270,18 +270,19 @@ def solve_run(args):
     x = torch.zeros_like(b)
     autotune(mf, torch, op, b, s)
     l2 = torch.zeros(1, dtype=torch.float64, device="cuda")
-    for mixed in (1, 0):
+    runs = [(1, t) for t in args.inner_rtol] + [(0, 0.0)]
+    for mixed, itol in runs:
         cws = torch.empty(mf.mf_cg_workspace_bytes(op, mixed), dtype=torch.uint8, device="cuda")
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         ev[0].record(stream)
         st = mf.mf_cg_solve(op, b.data_ptr(), x.data_ptr(), 1e-10, 400000, mixed, cws.data_ptr(), cws.numel(), s,
-                            allow_not_converged=True)
+                            allow_not_converged=True, inner_rtol=itol)
         ev[1].record(stream)
         ev[1].synchronize()
         t = ev[0].elapsed_time(ev[1]) / 1e3
         mf.mf_error_manufactured(op, 2.0, x.data_ptr(), l2.data_ptr(), sc.data_ptr(), sc.numel(), s)
         stream.synchronize()
-        out["mixed" if mixed else "fp64"] = {
+        out[f"mixed_inner{itol:g}" if mixed else "fp64"] = {
             "status": st["code"], "iterations": st["iterations"], "outer": st["outer_iterations"],
             "rel_residual": st["rel_residual"], "seconds": t,
             "solved_gdofs_cellwise": info["n_cellwise"] / t / 1e9, "solved_gdofs_unique": info["n_unique"] / t / 1e9,
@@ -289,7 +290,9 @@ def solve_run(args):
         del cws
         torch.cuda.empty_cache()
     out["n_cellwise"], out["n_unique"] = info["n_cellwise"], info["n_unique"]
-    out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    best = min((v["seconds"], kk) for kk, v in out.items() if kk.startswith("mixed_inner"))
+    out["best_mixed"] = best[1]
+    out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / best[0]
     print(json.dumps(out), flush=True)
     mf.mf_operator_destroy(op)
     mf.mf_mesh_destroy(mesh)
@@ -364,6 +367,7 @@ def main():
                     help="serving run: NREQ solve requests with Poisson arrivals (prints its own JSON line)")
     ap.add_argument("--rate", type=float, default=0.0, help="serving arrival rate (requests/s); 0 = measure capacity")
     ap.add_argument("--solve-n", type=int, default=96, help="cells per axis of the --solve mesh")
+    ap.add_argument("--inner-rtol", type=float, nargs="+", default=[1e-3], help="inner FP32 CG tolerances to run")
     args = ap.parse_args()
     if args.profile_apply:
         profile_apply(args)

@@ -203,6 +203,17 @@ typedef struct {
 size_t mf_cg_workspace_bytes(const mf_operator* op, int mixed);
 mf_status mf_cg_solve(const mf_operator* op, const void* b_dev, void* x_dev, double rtol, int maxit, int mixed,
                       mf_solve_stats* stats, void* workspace_dev, size_t bytes, void* stream);
+/* mf_cg_solve with options (0 fields keep the defaults): inner_rtol of the FP32 CG in
+ * defect correction (default 1e-3), CG iterations per graph launch (default 20), cap on
+ * defect-correction steps (default 60). */
+typedef struct {
+  double inner_rtol;
+  int32_t chunk_iterations;
+  int32_t max_outer;
+} mf_solve_options;
+mf_status mf_cg_solve_ex(const mf_operator* op, const void* b_dev, void* x_dev, double rtol, int maxit, int mixed,
+                         const mf_solve_options* opts, mf_solve_stats* stats, void* workspace_dev, size_t bytes,
+                         void* stream);
 /* Records up to `cap` relative residual norms (one per iteration, FP64) of the next
  * mf_cg_solve on this thread into hist_host; pass NULL to stop recording. */
 mf_status mf_cg_record_history(double* hist_host, int cap);
@@ -225,7 +236,7 @@ typedef struct {
   int32_t queue_capacity;   /* pending requests before MF_ERR_BUSY (default 100000) */
   int32_t chunk_iterations; /* CG iterations per graph launch (default 20) */
   int32_t autotune;         /* 1: autotune the apply of each new operator class */
-  double inner_rtol;        /* mixed: inner FP32 CG tolerance (default 1e-4) */
+  double inner_rtol;        /* mixed: inner FP32 CG tolerance (default 1e-3) */
 } mf_server_config;
 
 typedef struct {

@@ -45,6 +45,10 @@ class mf_solve_stats(C.Structure):
                 ("seconds", C.c_double), ("status", C.c_int32), ("check_every", C.c_int32)]
 
 
+class mf_solve_options(C.Structure):
+    _fields_ = [("inner_rtol", C.c_double), ("chunk_iterations", C.c_int32), ("max_outer", C.c_int32)]
+
+
 class mf_server_config(C.Structure):
     _fields_ = [("max_slots", C.c_int32), ("queue_capacity", C.c_int32), ("chunk_iterations", C.c_int32),
                 ("autotune", C.c_int32), ("inner_rtol", C.c_double)]
@@ -114,6 +118,8 @@ def lib() -> C.CDLL:
     L.mf_cg_workspace_bytes.restype = sz
     L.mf_cg_solve.argtypes = [vp, vp, vp, d, i32, i32, C.POINTER(mf_solve_stats), vp, sz, vp]
     L.mf_cg_record_history.argtypes = [vp, i32]
+    L.mf_cg_solve_ex.argtypes = [vp, vp, vp, d, i32, i32, C.POINTER(mf_solve_options), C.POINTER(mf_solve_stats),
+                                 vp, sz, vp]
     L.mf_server_create.argtypes = [C.POINTER(mf_server_config), vp, sz, C.POINTER(vp)]
     L.mf_batch_submit.argtypes = [vp, C.POINTER(mf_request), C.POINTER(C.c_uint64)]
     L.mf_batch_poll.argtypes = [vp, C.c_uint64, C.POINTER(mf_result)]
@@ -255,10 +261,12 @@ def mf_cg_workspace_bytes(op, mixed: int = 0) -> int:
 
 
 def mf_cg_solve(op, b_ptr: int, x_ptr: int, rtol: float, maxit: int, mixed: int, workspace_ptr: int,
-                nbytes: int, stream: int = 0, allow_not_converged: bool = False) -> dict:
+                nbytes: int, stream: int = 0, allow_not_converged: bool = False, inner_rtol: float = 0.0,
+                chunk_iterations: int = 0, max_outer: int = 0) -> dict:
     st = mf_solve_stats()
-    code = lib().mf_cg_solve(op, b_ptr, x_ptr, rtol, maxit, mixed, C.byref(st), workspace_ptr, nbytes,
-                             stream or None)
+    opts = mf_solve_options(inner_rtol, chunk_iterations, max_outer)
+    code = lib().mf_cg_solve_ex(op, b_ptr, x_ptr, rtol, maxit, mixed, C.byref(opts), C.byref(st), workspace_ptr,
+                                nbytes, stream or None)
     if not (code == MF_OK or (allow_not_converged and code == MF_ERR_NOT_CONVERGED)):
         _check(code)
     out = {f: getattr(st, f) for f, _ in mf_solve_stats._fields_}
@@ -272,7 +280,7 @@ def mf_cg_record_history(hist_ptr: int | None, cap: int) -> None:
 
 # ---------------------------------------------------------------- serving
 def mf_server_create(arena_ptr: int, arena_bytes: int, max_slots: int = 32, queue_capacity: int = 0,
-                     chunk_iterations: int = 20, autotune: int = 0, inner_rtol: float = 1e-4):
+                     chunk_iterations: int = 20, autotune: int = 0, inner_rtol: float = 1e-3):
     cfg = mf_server_config(max_slots, queue_capacity, chunk_iterations, autotune, inner_rtol)
     h = C.c_void_p()
     _check(lib().mf_server_create(C.byref(cfg), arena_ptr, arena_bytes, C.byref(h)))

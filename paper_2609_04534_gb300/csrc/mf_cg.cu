@@ -13,6 +13,7 @@
 #include <cstring>
 #include <vector>
 
+#include "mf_dd.cuh"
 #include "mf_internal.h"
 #include "mf_solver.h"
 
@@ -58,6 +59,38 @@ __device__ __forceinline__ double node_weight(const GridInfo& g, long long e, in
   // 1 / multiplicity = 2^-sh, selected (a double division costs tens of FP64-pipe slots)
   return sh == 0 ? 1.0 : (sh == 1 ? 0.5 : (sh == 2 ? 0.25 : 0.125));
 }
+
+// Per-thread accumulation of w a b (w = 1/multiplicity, a power of two).  Double operands
+// accumulate in FP64.  Float operands never touch the FP64 pipe (GB300 issues 64x fewer FP64
+// than FP32 instructions): the product is split exactly (TwoProd, a b = p + e), scaled
+// exactly by w, and summed in double-float (TwoSum on the leading part); the thread's value
+// enters the FP64 block reduction once.
+struct AccD {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double w, double a, double b) { s = fma(w, a * b, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+struct AccF {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add(double wd, float a, float b) {
+    const float w = (float)wd;
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);
+    const float pw = p * w, ew = e * w;
+    const float s = hi + pw;
+    const float v = s - hi;
+    const float t = (hi - (s - v)) + (pw - v);
+    hi = s;
+    lo += t + ew;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+template <typename T>
+struct AccOf;
+template <>
+struct AccOf<double> { using type = AccD; };
+template <>
+struct AccOf<float> { using type = AccF; };
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -114,10 +147,10 @@ static int red_blocks(long long n) {
 template <typename T, int N>
 __global__ void __launch_bounds__(RED_THREADS) dot_kernel(const T* __restrict__ a, const T* __restrict__ b, long long n,
                                                           GridInfo g, int split, RedScratch* sc, double* out) {
-  double s = 0.0;
+  typename AccOf<T>::type acc;
   for (long long e = blockIdx.x * (long long)RED_THREADS + threadIdx.x; e < n; e += (long long)gridDim.x * RED_THREADS)
-    s += node_weight<N>(g, e, split) * ((double)a[e] * (double)b[e]);
-  s = block_sum(s);
+    acc.add(node_weight<N>(g, e, split), a[e], b[e]);
+  const double s = block_sum(acc.value());
   double tot;
   if (last_block_total(sc, s, &tot)) *out = tot;
 }
@@ -126,10 +159,10 @@ __global__ void __launch_bounds__(RED_THREADS) dot_kernel(const T* __restrict__ 
 template <typename T, int N>
 __global__ void __launch_bounds__(RED_THREADS) cg_pq_kernel(const T* __restrict__ p, const T* __restrict__ q, long long n,
                                                             GridInfo g, RedScratch* sc, CgState* st) {
-  double s = 0.0;
+  typename AccOf<T>::type acc;
   for (long long e = blockIdx.x * (long long)RED_THREADS + threadIdx.x; e < n; e += (long long)gridDim.x * RED_THREADS)
-    s += node_weight<N>(g, e, 0) * ((double)p[e] * (double)q[e]);
-  s = block_sum(s);
+    acc.add(node_weight<N>(g, e, 0), p[e], q[e]);
+  const double s = block_sum(acc.value());
   double tot;
   if (last_block_total(sc, s, &tot)) {
     if (st->flag == 0) {
@@ -147,19 +180,19 @@ template <typename T, int N>
 __global__ void __launch_bounds__(RED_THREADS) cg_xr_kernel(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
                                                             const T* __restrict__ q, long long n, GridInfo g,
                                                             RedScratch* sc, CgState* st, double* hist) {
-  const double al = st->alpha;
+  const T al = (T)st->alpha; // float vectors: FP32 updates (the inner CG of defect correction)
   const bool run = st->flag == 0;
-  double s = 0.0;
+  typename AccOf<T>::type acc;
   for (long long e = blockIdx.x * (long long)RED_THREADS + threadIdx.x; e < n; e += (long long)gridDim.x * RED_THREADS) {
     T rv = r[e];
     if (run) {
-      x[e] = (T)((double)x[e] + al * (double)p[e]);
-      rv = (T)((double)rv - al * (double)q[e]);
+      x[e] = fma(al, p[e], x[e]);
+      rv = fma(-al, q[e], rv);
       r[e] = rv;
     }
-    s += node_weight<N>(g, e, 0) * ((double)rv * (double)rv);
+    acc.add(node_weight<N>(g, e, 0), rv, rv);
   }
-  s = block_sum(s);
+  const double s = block_sum(acc.value());
   double tot;
   if (last_block_total(sc, s, &tot)) {
     if (st->flag == 0) {
@@ -180,10 +213,10 @@ __global__ void __launch_bounds__(RED_THREADS) cg_xr_kernel(T* __restrict__ x, T
 template <typename T>
 __global__ void cg_p_kernel(const T* __restrict__ r, T* __restrict__ p, long long n, const CgState* st, int was_running) {
   (void)was_running;
-  const double be = st->beta;
+  const T be = (T)st->beta;
   if (st->flag != 0 && st->flag != 1) return;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    p[e] = (T)((double)r[e] + be * (double)p[e]);
+    p[e] = fma(be, p[e], r[e]);
 }
 
 // Small element-wise kernels of the drivers.
@@ -560,7 +593,16 @@ size_t mf_cg_workspace_bytes(const mf_operator* op, int mixed) {
 
 mf_status mf_cg_solve(const mf_operator* op, const void* b_dev, void* x_dev, double rtol, int maxit, int mixed,
                       mf_solve_stats* stats, void* workspace_dev, size_t bytes, void* stream) {
+  return mf_cg_solve_ex(op, b_dev, x_dev, rtol, maxit, mixed, nullptr, stats, workspace_dev, bytes, stream);
+}
+
+mf_status mf_cg_solve_ex(const mf_operator* op, const void* b_dev, void* x_dev, double rtol, int maxit, int mixed,
+                         const mf_solve_options* opts, mf_solve_stats* stats, void* workspace_dev, size_t bytes,
+                         void* stream) {
   if (!op || !b_dev || !x_dev) return set_error(MF_ERR_ARG, "mf_cg_solve: NULL argument");
+  if (opts && ((opts->inner_rtol != 0.0 && !(opts->inner_rtol > 0.0 && opts->inner_rtol < 1.0)) ||
+               opts->chunk_iterations < 0 || opts->max_outer < 0))
+    return set_error(MF_ERR_ARG, "mf_cg_solve_ex: bad options");
   if (!op->ready) return set_error(MF_ERR_ARG, "mf_cg_solve: operator not set up");
   if (maxit < 0 || !(rtol >= 0.0)) return set_error(MF_ERR_ARG, "mf_cg_solve: bad rtol/maxit");
   if (mixed && op->precision != MF_MIXED) return set_error(MF_ERR_ARG, "mf_cg_solve: mixed needs an MF_MIXED operator");
@@ -587,6 +629,11 @@ mf_status mf_cg_solve(const mf_operator* op, const void* b_dev, void* x_dev, dou
   std::memset(&hm, 0, sizeof(hm));
   SolverEngine e;
   engine_init(&e, op, mixed ? 1 : 0, b_dev, x_dev, rtol, maxit, workspace_dev, s, &hm);
+  if (opts) {
+    if (opts->inner_rtol > 0.0) e.inner_rtol = opts->inner_rtol;
+    if (opts->chunk_iterations > 0) e.chunk = opts->chunk_iterations;
+    if (opts->max_outer > 0) e.max_outer = opts->max_outer;
+  }
   e.record = g_hist_host != nullptr;
   mf_status st = engine_start(&e);
   // every advance either finishes or moves the iteration count forward by a chunk; bound the

@@ -50,7 +50,7 @@ struct SolverEngine {
   const void* b = nullptr;
   void* x = nullptr;
   void* x_in = nullptr;
-  double rtol = 0.0, inner_rtol = 1e-4;
+  double rtol = 0.0, inner_rtol = 1e-3;
   int maxit = 0, chunk = 20, max_outer = 60;
   HostMirror* hm = nullptr;
   int phase = 0, total_it = 0, outer = 0;
