@@ -169,7 +169,9 @@ mf_status mf_operator_create(const mf_mesh* mesh, int degree, int kind, double m
   if (op->path == PATH_CURVED) {
     const size_t comps = (size_t)geom_comps(op);
     op->v64.geom_bytes = (precision == MF_FP32) ? 0 : comps * npts * 8;
-    op->v32.geom_bytes = (precision == MF_FP64) ? 0 : comps * npts * 4;
+    // the FP32 view computes its metric per point from small sin/cos tables
+    const size_t tab = sizeof(float) * 2 * (size_t)(g.nx + g.ny + g.nz) * op->n;
+    op->v32.geom_bytes = (precision == MF_FP64 || precision == MF_FP64_DFMA) ? 0 : tab;
   }
   *out = op;
   return MF_OK;
@@ -192,7 +194,7 @@ mf_status mf_operator_info(const mf_operator* op, mf_info* info) {
   info->workspace_bytes = align256(op->v64.geom_bytes) + align256(op->v32.geom_bytes) + 256;
   const double e = info->elem_bytes;
   double per_dof = 2.0 * e;
-  if (op->path == PATH_CURVED) per_dof += geom_comps(op) * e;
+  if (op->path == PATH_CURVED && op->precision != MF_FP32) per_dof += geom_comps(op) * e; // FP32: no stream
   info->algorithmic_bytes_per_apply = per_dof * (double)op->n_cellwise;
   return MF_OK;
 }

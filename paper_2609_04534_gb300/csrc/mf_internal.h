@@ -50,6 +50,10 @@ struct ApplyArgs {
   T mdet;                     // affine: mass_coeff * |det J|
   T gx, gy, gz, cmass;        // Cartesian: det/h_d^2 and mass_coeff * det
   Tab<T, N> tab;
+  // FP32 curved: the metric is computed per point from per-direction tables of
+  // sin(pi xh), cos(pi xh) at the Gauss points of every cell layer ([(nx+ny+nz)*N][2]).
+  const float* gtab;
+  float amp, cm, h[3];
 };
 
 // Host-side double tables (any n <= MAXN).

@@ -259,7 +259,35 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T
     for (int q = 0; q < N; ++q) {
       const int l = pa + N * pb + N2 * q;
       T g0, g1, g2, g3, g4, g5, m = T(0);
-      if (CURVED) {
+      if constexpr (CURVED && sizeof(T) == 4) {
+        // x = xh + amp s(xh) (1,1,1): J = (I + u v^T) D with u = amp (1,1,1), v = grad s,
+        // D = diag(h).  Sherman-Morrison: J^-1 = D^-1 (I - u v^T / beta), beta = 1 + v.u, and
+        // J^-1 J^-T = D^-1 (I - (u v^T + v u^T)/beta + |v|^2 u u^T / beta^2) D^-1.
+        int ccx, ccy, ccz;
+        cell_of(a.g, t, lane0 + c, ccx, ccy, ccz);
+        ccx = min(ccx, a.g.nx - 1);
+        ccy = min(ccy, a.g.ny - 1);
+        ccz = min(ccz, a.g.nz - 1);
+        const float* tx = a.gtab + 2 * (ccx * N + pa);
+        const float* ty = a.gtab + 2 * ((a.g.nx + ccy) * N + pb);
+        const float* tz = a.gtab + 2 * ((a.g.nx + a.g.ny + ccz) * N + q);
+        const float sx = tx[0], cxv = tx[1], sy = ty[0], cyv = ty[1], sz = tz[0], czv = tz[1];
+        const float pi = 3.14159265358979f;
+        const float v1 = pi * cxv * sy * sz, v2 = pi * sx * cyv * sz, v3 = pi * sx * sy * czv;
+        const float beta = fmaf(a.amp, v1 + v2 + v3, 1.0f);
+        const float ib = 1.0f / beta;
+        const float au = a.amp * ib;
+        const float c2 = au * au * (v1 * v1 + v2 * v2 + v3 * v3);
+        const float wd = a.tab.W[pa] * a.tab.W[pb] * a.tab.W[q] * (a.h[0] * a.h[1] * a.h[2]) * fabsf(beta);
+        const float i0 = 1.0f / a.h[0], i1 = 1.0f / a.h[1], i2 = 1.0f / a.h[2];
+        g0 = wd * i0 * i0 * (1.0f - 2.0f * au * v1 + c2);
+        g1 = wd * i0 * i1 * (c2 - au * (v1 + v2));
+        g2 = wd * i0 * i2 * (c2 - au * (v1 + v3));
+        g3 = wd * i1 * i1 * (1.0f - 2.0f * au * v2 + c2);
+        g4 = wd * i1 * i2 * (c2 - au * (v2 + v3));
+        g5 = wd * i2 * i2 * (1.0f - 2.0f * au * v3 + c2);
+        if (HELM) m = wd * a.cm;
+      } else if (CURVED) {
         const T* gp = a.geom + gbase + (long long)l * BL;
         g0 = gp[0];
         g1 = gp[(long long)1 * N3 * BL];
@@ -341,54 +369,76 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T
 // along x, then the x-sums along y, then along z.  One thread per global node; each copy
 // is read and written by exactly one thread, so no atomics and no races.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ int copies_1d(long long I, int ncell, int k, int* cell, int* loc) {
-  const long long c = I / k;
+__device__ __forceinline__ int copies_1d(int I, int ncell, int k, int* cell, int* loc) {
+  const int c = I / k;
   if (I - c * k == 0) {
     if (c == 0) { cell[0] = 0; loc[0] = 0; return 1; }
     if (c == ncell) { cell[0] = ncell - 1; loc[0] = k; return 1; }
-    cell[0] = (int)c - 1; loc[0] = k;
-    cell[1] = (int)c; loc[1] = 0;
+    cell[0] = c - 1; loc[0] = k;
+    cell[1] = c; loc[1] = 0;
     return 2;
   }
-  cell[0] = (int)c; loc[0] = (int)(I - c * k);
+  cell[0] = c; loc[0] = I - c * k;
   return 1;
 }
 
+// One thread per global node (I, J, L); unique-node counts stay below 2^31 (checked by the
+// launcher), so the index arithmetic is 32-bit.
 template <typename T, int N>
 __global__ void dss_kernel(T* __restrict__ y, GridInfo g) {
   constexpr int K = N - 1, N2 = N * N, N3 = N2 * N;
-  const long long NX = (long long)g.nx * K + 1, NY = (long long)g.ny * K + 1, NZ = (long long)g.nz * K + 1;
-  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (gid >= NX * NY * NZ) return;
-  const long long I = gid % NX, J = (gid / NX) % NY, L = gid / (NX * NY);
+  const int NX = g.nx * K + 1, NY = g.ny * K + 1, NZ = g.nz * K + 1;
+  const unsigned gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned nxy = (unsigned)NX * (unsigned)NY;
+  if (gid >= nxy * (unsigned)NZ) return;
+  const int L = (int)(gid / nxy);
+  const unsigned rem = gid - (unsigned)L * nxy;
+  const int J = (int)(rem / (unsigned)NX);
+  const int I = (int)(rem - (unsigned)J * (unsigned)NX);
+  // quick exit: a node inside one cell (not on a cell face) and off the Dirichlet boundary
+  const bool onI = (I % K) == 0, onJ = (J % K) == 0, onL = (L % K) == 0;
+  const bool bnd = g.bc && (I == 0 || I == NX - 1 || J == 0 || J == NY - 1 || L == 0 || L == NZ - 1);
+  if (!onI && !onJ && !onL) return;
   int cx[2], ix[2], cy[2], iy[2], cz[2], iz[2];
   const int mx = copies_1d(I, g.nx, K, cx, ix);
   const int my = copies_1d(J, g.ny, K, cy, iy);
   const int mz = copies_1d(L, g.nz, K, cz, iz);
-  const bool bnd = g.bc && (I == 0 || I == NX - 1 || J == 0 || J == NY - 1 || L == 0 || L == NZ - 1);
   if (mx * my * mz == 1 && !bnd) return;
   long long addr[8];
-  T s = T(0);
-  T sz[2];
-  for (int zz = 0; zz < mz; ++zz) {
-    T sy[2];
-    for (int yy = 0; yy < my; ++yy) {
-      T sx = T(0);
-      for (int xx = 0; xx < mx; ++xx) {
-        const long long ad = native_index(g, N3, cx[xx], cy[yy], cz[zz], ix[xx] + N * iy[yy] + N2 * iz[zz]);
-        addr[xx + 2 * (yy + 2 * zz)] = ad;
-        const T v = y[ad];
-        sx = (xx == 0) ? v : sx + v;
+  T v[8];
+#pragma unroll
+  for (int zz = 0; zz < 2; ++zz)
+#pragma unroll
+    for (int yy = 0; yy < 2; ++yy)
+#pragma unroll
+      for (int xx = 0; xx < 2; ++xx) {
+        const int m = xx + 2 * (yy + 2 * zz);
+        if (xx < mx && yy < my && zz < mz) {
+          addr[m] = native_index(g, N3, cx[xx], cy[yy], cz[zz], ix[xx] + N * iy[yy] + N2 * iz[zz]);
+          v[m] = y[addr[m]]; // all loads issued before the sums
+        }
       }
-      sy[yy] = sx;
+  // canonical order: pairwise along x, then y, then z
+  T sz[2];
+#pragma unroll
+  for (int zz = 0; zz < 2; ++zz) {
+    T sy[2];
+#pragma unroll
+    for (int yy = 0; yy < 2; ++yy) {
+      const int m = 2 * (yy + 2 * zz);
+      sy[yy] = (mx == 2) ? v[m] + v[m + 1] : v[m];
     }
     sz[zz] = (my == 2) ? sy[0] + sy[1] : sy[0];
   }
-  s = (mz == 2) ? sz[0] + sz[1] : sz[0];
+  T s = (mz == 2) ? sz[0] + sz[1] : sz[0];
   if (bnd) s = T(0);
-  for (int zz = 0; zz < mz; ++zz)
-    for (int yy = 0; yy < my; ++yy)
-      for (int xx = 0; xx < mx; ++xx) y[addr[xx + 2 * (yy + 2 * zz)]] = s;
+#pragma unroll
+  for (int zz = 0; zz < 2; ++zz)
+#pragma unroll
+    for (int yy = 0; yy < 2; ++yy)
+#pragma unroll
+      for (int xx = 0; xx < 2; ++xx)
+        if (xx < mx && yy < my && zz < mz) y[addr[xx + 2 * (yy + 2 * zz)]] = s;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -396,6 +446,25 @@ __global__ void dss_kernel(T* __restrict__ y, GridInfo g) {
 // G = w |det J| J^-1 J^-T (xx,xy,xz,yy,yz,zz) and, for Helmholtz, m = w |det J| c_m, computed
 // in FP64 from the analytic Jacobian and stored in T, layout [tile][comp][l][lane].
 // ---------------------------------------------------------------------------------------
+struct GeomArgsQ {
+  double qx[MAXN];
+};
+
+// FP32 curved view: sin(pi xh) and cos(pi xh) at the Gauss points of every cell layer, per
+// direction ([(nx+ny+nz) * N][2] floats), computed in FP64 once at set-up.
+template <int N>
+__global__ void geom_table_kernel(float* tab, GridInfo g, GeomArgsQ q) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (g.nx + g.ny + g.nz) * N) return;
+  const int r = e / N, qq = e - r * N;
+  const int nd = r < g.nx ? g.nx : (r < g.nx + g.ny ? g.ny : g.nz);
+  const int c = r < g.nx ? r : (r < g.nx + g.ny ? r - g.nx : r - g.nx - g.ny);
+  double sp, cp;
+  sincospi((c + q.qx[qq]) / nd, &sp, &cp);
+  tab[2 * e] = (float)sp;
+  tab[2 * e + 1] = (float)cp;
+}
+
 template <typename T>
 __device__ __forceinline__ T geom_value(double v) { return (T)v; }
 template <>
@@ -403,6 +472,7 @@ __device__ __forceinline__ dd geom_value<dd>(double v) {
   const float h = __double2float_rn(v);
   return dd(h, __double2float_rn(v - (double)h));
 }
+
 
 struct GeomArgs {
   GridInfo g;
@@ -508,6 +578,12 @@ static void fill_args(const mf_operator* op, ApplyArgs<S, T, N>& a) {
   a.gy = host_from_double<T>(op->gy);
   a.gz = host_from_double<T>(op->gz);
   a.cmass = host_from_double<T>(op->cmass);
+  a.gtab = static_cast<const float*>(op->v32.geom);
+  a.amp = (float)op->mesh.amp;
+  a.cm = (float)(op->kind == MF_HELMHOLTZ ? op->mass : 0.0);
+  a.h[0] = 1.0f / op->g.nx;
+  a.h[1] = 1.0f / op->g.ny;
+  a.h[2] = 1.0f / op->g.nz;
   const HostTables& h = op->tab;
   for (int q = 0; q < N; ++q) {
     a.tab.W[q] = host_from_double<T>(h.qw[q]);
@@ -566,6 +642,7 @@ mf_status apply_split_n(const mf_operator* op, int vk, const void* x, void* y, c
 template <int N>
 mf_status dss_n(const mf_operator* op, int elem, void* y, cudaStream_t s) {
   const long long total = op->n_unique;
+  if (total >= (1LL << 31)) return set_error(MF_ERR_UNSUPPORTED, "duplicate summation: %lld nodes >= 2^31", total);
   const int thr = 256;
   const long long blocks = (total + thr - 1) / thr;
   if (elem == 8) dss_kernel<double, N><<<(unsigned)blocks, thr, 0, s>>>(static_cast<double*>(y), op->g);
@@ -586,7 +663,12 @@ mf_status geometry_n(const mf_operator* op, int vk, void* geom, cudaStream_t s) 
   const long long blocks = (total + thr - 1) / thr;
   if (vk == VK_F64) geometry_kernel<double, N><<<(unsigned)blocks, thr, 0, s>>>(static_cast<double*>(geom), a);
   else if (vk == VK_DD) geometry_kernel<dd, N><<<(unsigned)blocks, thr, 0, s>>>(static_cast<dd*>(geom), a);
-  else geometry_kernel<float, N><<<(unsigned)blocks, thr, 0, s>>>(static_cast<float*>(geom), a);
+  else {
+    GeomArgsQ q;
+    for (int i = 0; i < N; ++i) q.qx[i] = op->tab.qx[i];
+    const int nt = (op->g.nx + op->g.ny + op->g.nz) * N;
+    geom_table_kernel<N><<<(nt + 127) / 128, 128, 0, s>>>(static_cast<float*>(geom), op->g, q);
+  }
   return cuda_check(cudaGetLastError(), "geometry launch");
 }
 

@@ -69,7 +69,8 @@ def test_operator_argument_validation_and_info(L):
     op = mf.mf_operator_create(mc, 4, mf.MF_HELMHOLTZ, 1.0, mf.MF_MIXED, mf.MF_BC_DIRICHLET0)
     info = mf.mf_operator_info(op)
     assert info["path"] == 2
-    assert info["geom_bytes"] == 7 * info["n_native"] * (8 + 4)
+    # FP64 view streams 7 values per point; the FP32 view keeps sin/cos tables per cell layer
+    assert info["geom_bytes"] == 7 * info["n_native"] * 8 + 4 * 2 * (5 + 6 + 3) * 5
     assert info["algorithmic_bytes_per_apply"] == (16 + 7 * 8) * info["n_cellwise"]
     # not set up yet: apply must refuse without touching the GPU
     with pytest.raises(mf.MfError) as e:
