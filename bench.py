@@ -104,6 +104,25 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate_ranks(dist, device, t_local: float, units_local: float):
+    """Replicas: every rank runs the same workload on its own GPU.  The job time is the max
+    over ranks (after a barrier); the job throughput is the units all ranks processed / that
+    time.  Works with any process group (NCCL on GPUs, gloo on CPU)."""
+    import torch
+
+    if dist is None:
+        return t_local, units_local / t_local
+    world = dist.get_world_size()
+    tt = torch.tensor([t_local, units_local], dtype=torch.float64, device=device)
+    tmax = tt[:1].clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    units = tt[1:].clone()
+    dist.all_reduce(units, op=dist.ReduceOp.SUM)
+    dist.barrier()
+    del world
+    return float(tmax.item()), float(units.item()) / float(tmax.item())
+
+
 def make_op(mf, torch, N, k, geom, kind, prec, bc, stream):
     mesh = mf.mf_mesh_create(N, N, N, geom, None, 0.1)
     op = mf.mf_operator_create(mesh, k, kind, 1.0, prec, bc)
@@ -427,14 +446,10 @@ def main():
         ev[1].synchronize()
     torch.cuda.synchronize()
     t_steps = ev[0].elapsed_time(ev[1]) / 1e3
-    if dist:
-        tt = torch.tensor([t_steps], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_steps = float(tt.item())
-        dist.barrier()
     its = st["iterations"]
+    t_steps, rate = aggregate_ranks(dist, "cuda", t_steps, float(ncw) * its)
     t_it = t_steps / max(its, 1)
-    value = world * ncw / t_it / 1e9
+    value = rate / 1e9
 
     # apply alone on the same operator, plus per-kernel times of the dominant kernel
     t_apply = time_apply(mf, torch, op, b, y, stream, 20, 3)
