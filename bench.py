@@ -258,10 +258,11 @@ def profile_apply(args):
     with torch.cuda.stream(stream):
         x = random_native(mf, torch, op, info, N, k, 1, dt, s)
         y = torch.empty_like(x)
-    t = time_apply(mf, torch, op, x, y, stream, args.reps, 1)
-    print(json.dumps({"case": args.profile_apply, "n_cellwise": info["n_cellwise"], "ms": t * 1e3,
-                      "gdofs": info["n_cellwise"] / t / 1e9,
-                      "alg_bytes": info["algorithmic_bytes_per_apply"]}), flush=True)
+    for v in ([args.variant] if args.variant >= 0 else [0, 1, 2]):
+        mf.mf_operator_set_variant(op, v)
+        t = time_apply(mf, torch, op, x, y, stream, args.reps, 1)
+        print(json.dumps({"case": args.profile_apply, "variant": v, "n_cellwise": info["n_cellwise"],
+                          "ms": round(t * 1e3, 4), "gdofs": round(info["n_cellwise"] / t / 1e9, 3)}), flush=True)
     mf.mf_operator_destroy(op)
     mf.mf_mesh_destroy(mesh)
 
@@ -382,6 +383,7 @@ def main():
     ap.add_argument("--profile-apply", default=None, metavar="N,k,geom,prec,kind",
                     help="only run a few applies of one case (for ncu), e.g. 32,4,curved,fp64,laplace")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--variant", type=int, default=-1, help="--profile-apply: launch variant (-1: all)")
     ap.add_argument("--serve", type=int, default=0, metavar="NREQ",
                     help="serving run: NREQ solve requests with Poisson arrivals (prints its own JSON line)")
     ap.add_argument("--rate", type=float, default=0.0, help="serving arrival rate (requests/s); 0 = measure capacity")

@@ -107,14 +107,15 @@ mf_status mf_operator_info(const mf_operator* op, mf_info* info);
 mf_status mf_operator_setup(mf_operator* op, void* workspace_dev, size_t bytes, void* stream);
 
 /* Autotuner: times each launch configuration of the apply kernel (variant 0: n^2 x CB
- * threads per CTA, two CTAs per SM; variant 1: half the cells per CTA, three CTAs per SM)
+ * threads per CTA, registers capped for two CTAs per SM; variant 1: half the cells per CTA,
+ * capped for three; variant 2: half the cells per CTA, no register cap)
  * with `reps` applies of x_dev into y_dev (both native vectors of this operator; y is
  * overwritten) and keeps the fastest.  The choice is cached per (device, degree, path,
  * kind, precision) for the life of the process, so later operators of the same class reuse
  * it without timing.  Synchronises `stream`.  Results do not depend on the variant (each
  * thread runs the same arithmetic), only speed does. */
 mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, int reps, void* stream);
-/* Forces a launch variant (0 or 1) for every precision view; returns MF_ERR_ARG otherwise. */
+/* Forces a launch variant (0, 1 or 2) for every precision view; returns MF_ERR_ARG otherwise. */
 mf_status mf_operator_set_variant(mf_operator* op, int variant);
 /* Variant in use for the operator's main precision view (-1 for a NULL operator). */
 int mf_operator_get_variant(const mf_operator* op);

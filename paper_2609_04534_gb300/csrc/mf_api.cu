@@ -320,7 +320,7 @@ mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, 
   if ((st = cuda_check(cudaEventCreate(&e1), "event"))) { cudaEventDestroy(e0); return st; }
   float best = 1e30f;
   int best_v = 0;
-  for (int v = 0; v < 2 && st == MF_OK; ++v) {
+  for (int v = 0; v < 3 && st == MF_OK; ++v) {
     op->variant[vk] = v;
     st = launch_apply_split(op, vk, x_dev, y_dev, s); // warm-up
     if (st) break;
@@ -343,7 +343,7 @@ mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, 
 }
 
 mf_status mf_operator_set_variant(mf_operator* op, int variant) {
-  if (!op || variant < 0 || variant > 1) return set_error(MF_ERR_ARG, "mf_operator_set_variant: bad argument");
+  if (!op || variant < 0 || variant > 2) return set_error(MF_ERR_ARG, "mf_operator_set_variant: bad argument");
   op->variant[VK_F64] = op->variant[VK_DD] = op->variant[VK_F32] = variant;
   return MF_OK;
 }

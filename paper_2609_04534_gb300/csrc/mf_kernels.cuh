@@ -13,12 +13,16 @@ namespace mf {
 // pencil (a 1D line of n values) of one cell in every sweep, so a CTA has n^2 * CB threads.
 // Launch configurations of the apply kernels, chosen per operator by the autotuner
 // (mf_operator_autotune): variant 0 = CB0 cells per CTA with registers capped for 2 resident
-// CTAs per SM; variant 1 = CB0/2 cells per CTA, capped for 3 resident CTAs per SM.
+// CTAs per SM; variant 1 = CB0/2 cells per CTA, capped for 3 resident CTAs per SM;
+// variant 2 = CB0/2 cells per CTA with no register cap (high degrees spill under a cap).
+// (Staging the streamed geometry into shared memory with cp.async was measured and lost:
+// the 2-CTA configuration already hides its load latency.)
+constexpr int MF_NUM_VARIANTS = 3;
 template <typename T, int N, int V>
 struct Cfg {
   static constexpr int CB0 = (N <= 4) ? 32 : (N <= 6) ? 16 : (N <= 8) ? 8 : (sizeof(T) == 4 ? 8 : 4);
   static constexpr int CB = V == 0 ? CB0 : ((CB0 / 2) >= 4 ? (CB0 / 2) : 4);
-  static constexpr int MINB = V == 0 ? 2 : 3;
+  static constexpr int MINB = V == 0 ? 2 : (V == 1 ? 3 : 1);
   static constexpr int NT = N * N * CB;
 };
 
@@ -178,9 +182,11 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_cartesian(ApplyArgs<S,
 template <typename S, typename T, int N, int CB, int MINB, bool CURVED, bool HELM>
 __global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T, N> a) {
   constexpr int N2 = N * N, N3 = N2 * N, NT = N2 * CB, GPT = BL / CB;
+  constexpr int NC = HELM ? 7 : 6;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* buf0 = reinterpret_cast<T*>(smem_raw);
   T* buf1 = buf0 + N3 * CB;
+  T* buf2 = buf1 + N3 * CB;
   const long long t = blockIdx.x / GPT;
   const int lane0 = (blockIdx.x % GPT) * CB;
   load_tile<S, T, N, CB, NT>(a, t, lane0, buf0);
@@ -214,7 +220,8 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T
     }
   }
   __syncthreads();
-  // z-sweep, pencil (i=pa, j=pb): values U and z-derivative stay in registers
+  // z-sweep, pencil (i=pa, j=pb): values U and the z-derivative stay in registers, U also goes
+  // to buf1 for the x- and y-derivatives of the other pencils
   T U[N], d3[N];
   {
     T in[N];
@@ -226,6 +233,7 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T
 #pragma unroll
       for (int k = 0; k < N; ++k) s = fma(Sm[q * N + k], in[k], s);
       U[q] = finish(s);
+      buf1[(pa + N * pb + N2 * q) * CB + c] = U[q];
     }
 #pragma unroll
     for (int q = 0; q < N; ++q) {
@@ -236,122 +244,109 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T
     }
   }
   __syncthreads();
-#pragma unroll
-  for (int q = 0; q < N; ++q) buf0[(pa + N * pb + N2 * q) * CB + c] = U[q];
-  __syncthreads();
-  T d1[N], d2[N];
+  // Per Gauss point (pa, pb, q): reference gradient (x and y parts from buf1), metric, and the
+  // fluxes v = G grad u; v1 -> buf0, v2 -> buf2, v3 stays in registers (Helmholtz: m u too).
+  const long long gbase = (t * NC * (long long)N3) * BL + lane0 + c;
 #pragma unroll
   for (int q = 0; q < N; ++q) {
+    const int l = pa + N * pb + N2 * q;
     T s1 = T(0), s2 = T(0);
 #pragma unroll
     for (int r = 0; r < N; ++r) {
-      s1 = fma(Dc[pa * N + r], buf0[(r + N * pb + N2 * q) * CB + c], s1);
-      s2 = fma(Dc[pb * N + r], buf0[(pa + N * r + N2 * q) * CB + c], s2);
+      s1 = fma(Dc[pa * N + r], buf1[(r + N * pb + N2 * q) * CB + c], s1);
+      s2 = fma(Dc[pb * N + r], buf1[(pa + N * r + N2 * q) * CB + c], s2);
     }
-    d1[q] = finish(s1);
-    d2[q] = finish(s2);
+    const T d1 = finish(s1), d2 = finish(s2);
+    T g0, g1, g2, g3, g4, g5, m = T(0);
+    if constexpr (CURVED && sizeof(T) == 4) {
+      // x = xh + amp s(xh) (1,1,1): J = (I + u v^T) D with u = amp (1,1,1), v = grad s,
+      // D = diag(h).  Sherman-Morrison: J^-1 = D^-1 (I - u v^T / beta), beta = 1 + v.u, and
+      // J^-1 J^-T = D^-1 (I - (u v^T + v u^T)/beta + |v|^2 u u^T / beta^2) D^-1.
+      int ccx, ccy, ccz;
+      cell_of(a.g, t, lane0 + c, ccx, ccy, ccz);
+      ccx = min(ccx, a.g.nx - 1);
+      ccy = min(ccy, a.g.ny - 1);
+      ccz = min(ccz, a.g.nz - 1);
+      const float* tx = a.gtab + 2 * (ccx * N + pa);
+      const float* ty = a.gtab + 2 * ((a.g.nx + ccy) * N + pb);
+      const float* tz = a.gtab + 2 * ((a.g.nx + a.g.ny + ccz) * N + q);
+      const float sx = tx[0], cxv = tx[1], sy = ty[0], cyv = ty[1], sz = tz[0], czv = tz[1];
+      const float pi = 3.14159265358979f;
+      const float v1 = pi * cxv * sy * sz, v2 = pi * sx * cyv * sz, v3 = pi * sx * sy * czv;
+      const float beta = fmaf(a.amp, v1 + v2 + v3, 1.0f);
+      const float ib = 1.0f / beta;
+      const float au = a.amp * ib;
+      const float c2 = au * au * (v1 * v1 + v2 * v2 + v3 * v3);
+      const float wd = a.tab.W[pa] * a.tab.W[pb] * a.tab.W[q] * (a.h[0] * a.h[1] * a.h[2]) * fabsf(beta);
+      const float i0 = 1.0f / a.h[0], i1 = 1.0f / a.h[1], i2 = 1.0f / a.h[2];
+      g0 = wd * i0 * i0 * (1.0f - 2.0f * au * v1 + c2);
+      g1 = wd * i0 * i1 * (c2 - au * (v1 + v2));
+      g2 = wd * i0 * i2 * (c2 - au * (v1 + v3));
+      g3 = wd * i1 * i1 * (1.0f - 2.0f * au * v2 + c2);
+      g4 = wd * i1 * i2 * (c2 - au * (v2 + v3));
+      g5 = wd * i2 * i2 * (1.0f - 2.0f * au * v3 + c2);
+      if (HELM) m = wd * a.cm;
+    } else if (CURVED) {
+      const T* gp = a.geom + gbase + (long long)l * BL;
+      g0 = gp[0];
+      g1 = gp[(long long)1 * N3 * BL];
+      g2 = gp[(long long)2 * N3 * BL];
+      g3 = gp[(long long)3 * N3 * BL];
+      g4 = gp[(long long)4 * N3 * BL];
+      g5 = gp[(long long)5 * N3 * BL];
+      if (HELM) m = gp[(long long)6 * N3 * BL];
+    } else {
+      const T w = a.tab.W[pa] * a.tab.W[pb] * a.tab.W[q];
+      g0 = w * a.G[0]; g1 = w * a.G[1]; g2 = w * a.G[2];
+      g3 = w * a.G[3]; g4 = w * a.G[4]; g5 = w * a.G[5];
+      if (HELM) m = w * a.mdet;
+    }
+    buf0[l * CB + c] = finish(fma(g0, d1, fma(g1, d2, g2 * d3[q])));
+    buf2[l * CB + c] = finish(fma(g1, d1, fma(g3, d2, g4 * d3[q])));
+    d3[q] = finish(fma(g2, d1, fma(g4, d2, g5 * d3[q])));
+    if (HELM) U[q] = m * U[q];
   }
   __syncthreads();
-  // quadrature points (pa, pb, q): v = G grad u
+  // t = Dc^T_x v1 + Dc^T_y v2 + Dc^T_z v3 (+ m u) at points (pa, pb, q), then S^T along z
   {
-    const long long gbase = (t * (HELM ? 7 : 6) * (long long)N3) * BL + lane0 + c;
+    T tq[N];
 #pragma unroll
     for (int q = 0; q < N; ++q) {
-      const int l = pa + N * pb + N2 * q;
-      T g0, g1, g2, g3, g4, g5, m = T(0);
-      if constexpr (CURVED && sizeof(T) == 4) {
-        // x = xh + amp s(xh) (1,1,1): J = (I + u v^T) D with u = amp (1,1,1), v = grad s,
-        // D = diag(h).  Sherman-Morrison: J^-1 = D^-1 (I - u v^T / beta), beta = 1 + v.u, and
-        // J^-1 J^-T = D^-1 (I - (u v^T + v u^T)/beta + |v|^2 u u^T / beta^2) D^-1.
-        int ccx, ccy, ccz;
-        cell_of(a.g, t, lane0 + c, ccx, ccy, ccz);
-        ccx = min(ccx, a.g.nx - 1);
-        ccy = min(ccy, a.g.ny - 1);
-        ccz = min(ccz, a.g.nz - 1);
-        const float* tx = a.gtab + 2 * (ccx * N + pa);
-        const float* ty = a.gtab + 2 * ((a.g.nx + ccy) * N + pb);
-        const float* tz = a.gtab + 2 * ((a.g.nx + a.g.ny + ccz) * N + q);
-        const float sx = tx[0], cxv = tx[1], sy = ty[0], cyv = ty[1], sz = tz[0], czv = tz[1];
-        const float pi = 3.14159265358979f;
-        const float v1 = pi * cxv * sy * sz, v2 = pi * sx * cyv * sz, v3 = pi * sx * sy * czv;
-        const float beta = fmaf(a.amp, v1 + v2 + v3, 1.0f);
-        const float ib = 1.0f / beta;
-        const float au = a.amp * ib;
-        const float c2 = au * au * (v1 * v1 + v2 * v2 + v3 * v3);
-        const float wd = a.tab.W[pa] * a.tab.W[pb] * a.tab.W[q] * (a.h[0] * a.h[1] * a.h[2]) * fabsf(beta);
-        const float i0 = 1.0f / a.h[0], i1 = 1.0f / a.h[1], i2 = 1.0f / a.h[2];
-        g0 = wd * i0 * i0 * (1.0f - 2.0f * au * v1 + c2);
-        g1 = wd * i0 * i1 * (c2 - au * (v1 + v2));
-        g2 = wd * i0 * i2 * (c2 - au * (v1 + v3));
-        g3 = wd * i1 * i1 * (1.0f - 2.0f * au * v2 + c2);
-        g4 = wd * i1 * i2 * (c2 - au * (v2 + v3));
-        g5 = wd * i2 * i2 * (1.0f - 2.0f * au * v3 + c2);
-        if (HELM) m = wd * a.cm;
-      } else if (CURVED) {
-        const T* gp = a.geom + gbase + (long long)l * BL;
-        g0 = gp[0];
-        g1 = gp[(long long)1 * N3 * BL];
-        g2 = gp[(long long)2 * N3 * BL];
-        g3 = gp[(long long)3 * N3 * BL];
-        g4 = gp[(long long)4 * N3 * BL];
-        g5 = gp[(long long)5 * N3 * BL];
-        if (HELM) m = gp[(long long)6 * N3 * BL];
-      } else {
-        const T w = a.tab.W[pa] * a.tab.W[pb] * a.tab.W[q];
-        g0 = w * a.G[0]; g1 = w * a.G[1]; g2 = w * a.G[2];
-        g3 = w * a.G[3]; g4 = w * a.G[4]; g5 = w * a.G[5];
-        if (HELM) m = w * a.mdet;
+      T s = HELM ? U[q] : T(0);
+#pragma unroll
+      for (int r = 0; r < N; ++r) {
+        s = fma(Dc[r * N + pa], buf0[(r + N * pb + N2 * q) * CB + c], s);
+        s = fma(Dc[r * N + pb], buf2[(pa + N * r + N2 * q) * CB + c], s);
+        s = fma(Dc[r * N + q], d3[r], s);
       }
-      const T v1 = finish(fma(g0, d1[q], fma(g1, d2[q], g2 * d3[q])));
-      const T v2 = finish(fma(g1, d1[q], fma(g3, d2[q], g4 * d3[q])));
-      const T v3 = finish(fma(g2, d1[q], fma(g4, d2[q], g5 * d3[q])));
-      buf0[l * CB + c] = v1;
-      buf1[l * CB + c] = v2;
-      d3[q] = v3;
-      U[q] = HELM ? m * U[q] : T(0);
+      tq[q] = finish(s);
     }
-  }
-  __syncthreads();
-  // t = Dc^T_x v1 + Dc^T_y v2 + Dc^T_z v3 (+ m u) at points (pa, pb, q)
-  T tq[N];
 #pragma unroll
-  for (int q = 0; q < N; ++q) {
-    T s = U[q];
+    for (int k = 0; k < N; ++k) {
+      T s = T(0);
 #pragma unroll
-    for (int r = 0; r < N; ++r) {
-      s = fma(Dc[r * N + pa], buf0[(r + N * pb + N2 * q) * CB + c], s);
-      s = fma(Dc[r * N + pb], buf1[(pa + N * r + N2 * q) * CB + c], s);
-      s = fma(Dc[r * N + q], d3[r], s);
+      for (int q = 0; q < N; ++q) s = fma(Sm[q * N + k], tq[q], s);
+      buf1[(pa + N * pb + N2 * k) * CB + c] = finish(s);
     }
-    tq[q] = finish(s);
-  }
-  __syncthreads();
-  // S^T along z, pencil (i=pa, j=pb)
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    T s = T(0);
-#pragma unroll
-    for (int q = 0; q < N; ++q) s = fma(Sm[q * N + k], tq[q], s);
-    buf0[(pa + N * pb + N2 * k) * CB + c] = finish(s);
   }
   __syncthreads();
   { // S^T along y, pencil (i=pa, k=pb), in place
     T in[N];
 #pragma unroll
-    for (int q = 0; q < N; ++q) in[q] = buf0[(pa + N * q + N2 * pb) * CB + c];
+    for (int q = 0; q < N; ++q) in[q] = buf1[(pa + N * q + N2 * pb) * CB + c];
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       T s = T(0);
 #pragma unroll
       for (int q = 0; q < N; ++q) s = fma(Sm[q * N + j], in[q], s);
-      buf0[(pa + N * j + N2 * pb) * CB + c] = finish(s);
+      buf1[(pa + N * j + N2 * pb) * CB + c] = finish(s);
     }
   }
   __syncthreads();
   { // S^T along x, pencil (j=pa, k=pb) -> global
     T in[N], o[N];
 #pragma unroll
-    for (int q = 0; q < N; ++q) in[q] = buf0[(q + N * pa + N2 * pb) * CB + c];
+    for (int q = 0; q < N; ++q) in[q] = buf1[(q + N * pa + N2 * pb) * CB + c];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       T s = T(0);
@@ -369,76 +364,54 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T
 // along x, then the x-sums along y, then along z.  One thread per global node; each copy
 // is read and written by exactly one thread, so no atomics and no races.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ int copies_1d(int I, int ncell, int k, int* cell, int* loc) {
-  const int c = I / k;
+__device__ __forceinline__ int copies_1d(long long I, int ncell, int k, int* cell, int* loc) {
+  const long long c = I / k;
   if (I - c * k == 0) {
     if (c == 0) { cell[0] = 0; loc[0] = 0; return 1; }
     if (c == ncell) { cell[0] = ncell - 1; loc[0] = k; return 1; }
-    cell[0] = c - 1; loc[0] = k;
-    cell[1] = c; loc[1] = 0;
+    cell[0] = (int)c - 1; loc[0] = k;
+    cell[1] = (int)c; loc[1] = 0;
     return 2;
   }
-  cell[0] = c; loc[0] = I - c * k;
+  cell[0] = (int)c; loc[0] = (int)(I - c * k);
   return 1;
 }
 
-// One thread per global node (I, J, L); unique-node counts stay below 2^31 (checked by the
-// launcher), so the index arithmetic is 32-bit.
 template <typename T, int N>
 __global__ void dss_kernel(T* __restrict__ y, GridInfo g) {
   constexpr int K = N - 1, N2 = N * N, N3 = N2 * N;
-  const int NX = g.nx * K + 1, NY = g.ny * K + 1, NZ = g.nz * K + 1;
-  const unsigned gid = blockIdx.x * blockDim.x + threadIdx.x;
-  const unsigned nxy = (unsigned)NX * (unsigned)NY;
-  if (gid >= nxy * (unsigned)NZ) return;
-  const int L = (int)(gid / nxy);
-  const unsigned rem = gid - (unsigned)L * nxy;
-  const int J = (int)(rem / (unsigned)NX);
-  const int I = (int)(rem - (unsigned)J * (unsigned)NX);
-  // quick exit: a node inside one cell (not on a cell face) and off the Dirichlet boundary
-  const bool onI = (I % K) == 0, onJ = (J % K) == 0, onL = (L % K) == 0;
-  const bool bnd = g.bc && (I == 0 || I == NX - 1 || J == 0 || J == NY - 1 || L == 0 || L == NZ - 1);
-  if (!onI && !onJ && !onL) return;
+  const long long NX = (long long)g.nx * K + 1, NY = (long long)g.ny * K + 1, NZ = (long long)g.nz * K + 1;
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (gid >= NX * NY * NZ) return;
+  const long long I = gid % NX, J = (gid / NX) % NY, L = gid / (NX * NY);
   int cx[2], ix[2], cy[2], iy[2], cz[2], iz[2];
   const int mx = copies_1d(I, g.nx, K, cx, ix);
   const int my = copies_1d(J, g.ny, K, cy, iy);
   const int mz = copies_1d(L, g.nz, K, cz, iz);
+  const bool bnd = g.bc && (I == 0 || I == NX - 1 || J == 0 || J == NY - 1 || L == 0 || L == NZ - 1);
   if (mx * my * mz == 1 && !bnd) return;
   long long addr[8];
-  T v[8];
-#pragma unroll
-  for (int zz = 0; zz < 2; ++zz)
-#pragma unroll
-    for (int yy = 0; yy < 2; ++yy)
-#pragma unroll
-      for (int xx = 0; xx < 2; ++xx) {
-        const int m = xx + 2 * (yy + 2 * zz);
-        if (xx < mx && yy < my && zz < mz) {
-          addr[m] = native_index(g, N3, cx[xx], cy[yy], cz[zz], ix[xx] + N * iy[yy] + N2 * iz[zz]);
-          v[m] = y[addr[m]]; // all loads issued before the sums
-        }
-      }
-  // canonical order: pairwise along x, then y, then z
+  T s = T(0);
   T sz[2];
-#pragma unroll
-  for (int zz = 0; zz < 2; ++zz) {
+  for (int zz = 0; zz < mz; ++zz) {
     T sy[2];
-#pragma unroll
-    for (int yy = 0; yy < 2; ++yy) {
-      const int m = 2 * (yy + 2 * zz);
-      sy[yy] = (mx == 2) ? v[m] + v[m + 1] : v[m];
+    for (int yy = 0; yy < my; ++yy) {
+      T sx = T(0);
+      for (int xx = 0; xx < mx; ++xx) {
+        const long long ad = native_index(g, N3, cx[xx], cy[yy], cz[zz], ix[xx] + N * iy[yy] + N2 * iz[zz]);
+        addr[xx + 2 * (yy + 2 * zz)] = ad;
+        const T v = y[ad];
+        sx = (xx == 0) ? v : sx + v;
+      }
+      sy[yy] = sx;
     }
     sz[zz] = (my == 2) ? sy[0] + sy[1] : sy[0];
   }
-  T s = (mz == 2) ? sz[0] + sz[1] : sz[0];
+  s = (mz == 2) ? sz[0] + sz[1] : sz[0];
   if (bnd) s = T(0);
-#pragma unroll
-  for (int zz = 0; zz < 2; ++zz)
-#pragma unroll
-    for (int yy = 0; yy < 2; ++yy)
-#pragma unroll
-      for (int xx = 0; xx < 2; ++xx)
-        if (xx < mx && yy < my && zz < mz) y[addr[xx + 2 * (yy + 2 * zz)]] = s;
+  for (int zz = 0; zz < mz; ++zz)
+    for (int yy = 0; yy < my; ++yy)
+      for (int xx = 0; xx < mx; ++xx) y[addr[xx + 2 * (yy + 2 * zz)]] = s;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -604,10 +577,10 @@ static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, co
   a.x = static_cast<const S*>(x);
   a.y = static_cast<S*>(y);
   a.geom = static_cast<const T*>(geom);
-  const size_t smem = 2 * sizeof(T) * N * N * N * C::CB;
+  const bool helm = op->kind == MF_HELMHOLTZ;
+  const size_t smem = (op->path == PATH_CARTESIAN ? 2 : 3) * sizeof(T) * N * N * N * C::CB;
   const long long blocks = op->g.ntiles * (BL / C::CB);
   if (blocks <= 0) return MF_OK;
-  const bool helm = op->kind == MF_HELMHOLTZ;
   void (*k)(ApplyArgs<S, T, N>) = nullptr;
   if (op->path == PATH_CARTESIAN)
     k = helm ? apply_cartesian<S, T, N, C::CB, C::MINB, true> : apply_cartesian<S, T, N, C::CB, C::MINB, false>;
@@ -615,6 +588,7 @@ static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, co
     k = helm ? apply_general<S, T, N, C::CB, C::MINB, false, true> : apply_general<S, T, N, C::CB, C::MINB, false, false>;
   else
     k = helm ? apply_general<S, T, N, C::CB, C::MINB, true, true> : apply_general<S, T, N, C::CB, C::MINB, true, false>;
+  if (smem > 227 * 1024) return set_error(MF_ERR_UNSUPPORTED, "apply variant needs %zu bytes of shared memory", smem);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(apply)");
@@ -626,7 +600,9 @@ static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, co
 template <typename S, typename T, int N>
 static mf_status apply_split_t(const mf_operator* op, int variant, const void* x, void* y, const void* geom,
                                cudaStream_t s) {
-  return variant == 1 ? apply_split_v<S, T, N, 1>(op, x, y, geom, s) : apply_split_v<S, T, N, 0>(op, x, y, geom, s);
+  if (variant == 1) return apply_split_v<S, T, N, 1>(op, x, y, geom, s);
+  if (variant == 2) return apply_split_v<S, T, N, 2>(op, x, y, geom, s);
+  return apply_split_v<S, T, N, 0>(op, x, y, geom, s);
 }
 
 // vk: VK_F64 (double storage, native FP64 compute), VK_DD (double storage, double-float
@@ -642,7 +618,6 @@ mf_status apply_split_n(const mf_operator* op, int vk, const void* x, void* y, c
 template <int N>
 mf_status dss_n(const mf_operator* op, int elem, void* y, cudaStream_t s) {
   const long long total = op->n_unique;
-  if (total >= (1LL << 31)) return set_error(MF_ERR_UNSUPPORTED, "duplicate summation: %lld nodes >= 2^31", total);
   const int thr = 256;
   const long long blocks = (total + thr - 1) / thr;
   if (elem == 8) dss_kernel<double, N><<<(unsigned)blocks, thr, 0, s>>>(static_cast<double*>(y), op->g);
