@@ -206,15 +206,38 @@ mf_status mf_cg_solve(const mf_operator* op, const void* b_dev, void* x_dev, dou
                       mf_solve_stats* stats, void* workspace_dev, size_t bytes, void* stream);
 /* mf_cg_solve with options (0 fields keep the defaults): inner_rtol of the FP32 CG in
  * defect correction (default 1e-3), CG iterations per graph launch (default 20), cap on
- * defect-correction steps (default 60). */
+ * defect-correction steps (default 60), and the form of the CG iteration:
+ *   MF_CG_SPLIT_DUAL (default) -- the Krylov loop on split data of Sec. 4: the apply leaves
+ *     A p split (no duplicate summation) and forms <p, A p> -- the pairing of the consistent p
+ *     with the split product over all copies (Lemma 1) -- as the sum over quadrature points
+ *     of grad u . G grad u; the duplicate summation is folded into the update of x and r;
+ *     then p = r + beta p.  Three kernels per iteration.
+ *   MF_CG_ASSEMBLED -- apply, duplicate summation, then the vector kernels on assembled
+ *     vectors (five kernels per iteration).
+ *   MF_CG_SPLIT_DUAL_FUSED -- MF_CG_SPLIT_DUAL with p = r + beta p formed by the apply at
+ *     load (two kernels per iteration).
+ * All compute the same iterates up to rounding (only <p, A p> is summed differently). */
+enum { MF_CG_DEFAULT = 0, MF_CG_SPLIT_DUAL = 1, MF_CG_ASSEMBLED = 2, MF_CG_SPLIT_DUAL_FUSED = 3 };
 typedef struct {
   double inner_rtol;
   int32_t chunk_iterations;
   int32_t max_outer;
+  int32_t cg_form; /* MF_CG_* */
+  int32_t reserved;
 } mf_solve_options;
 mf_status mf_cg_solve_ex(const mf_operator* op, const void* b_dev, void* x_dev, double rtol, int maxit, int mixed,
                          const mf_solve_options* opts, mf_solve_stats* stats, void* workspace_dev, size_t bytes,
                          void* stream);
+/* Kernel timing of the CG iteration (a measurement helper; the paper has no counterpart):
+ * runs `iterations` FP64 (FP32 for an MF_FP32 operator) CG iterations from x = 0 on b, of the
+ * form cg_form (MF_CG_*), launching every kernel directly (no graph) with CUDA events around
+ * each kernel group on `stream`, and writes the mean durations in milliseconds:
+ * ms_out[0] the apply kernel (the fused apply of the split-dual form), ms_out[1] the duplicate
+ * summation (assembled form; 0 for split-dual), ms_out[2] the vector kernels, ms_out[3] the
+ * whole iteration.  1 <= iterations <= 1000.  Same workspace as mf_cg_solve (mixed = 0).
+ * Synchronous. */
+mf_status mf_cg_profile(const mf_operator* op, const void* b_dev, void* x_dev, int iterations, int cg_form,
+                        void* workspace_dev, size_t bytes, void* stream, double* ms_out);
 /* Records up to `cap` relative residual norms (one per iteration, FP64) of the next
  * mf_cg_solve on this thread into hist_host; pass NULL to stop recording. */
 mf_status mf_cg_record_history(double* hist_host, int cap);

@@ -21,6 +21,7 @@ MF_AFFINE, MF_CURVED_SIN = 0, 1
 MF_LAPLACE, MF_HELMHOLTZ = 0, 1
 MF_FP64, MF_FP32, MF_MIXED, MF_FP64_DFMA = 0, 1, 2, 3
 MF_BC_NONE, MF_BC_DIRICHLET0 = 0, 1
+MF_CG_DEFAULT, MF_CG_SPLIT_DUAL, MF_CG_ASSEMBLED, MF_CG_SPLIT_DUAL_FUSED = 0, 1, 2, 3
 
 _STATUS = {0: "MF_OK", -1: "MF_ERR_ARG", -2: "MF_ERR_OOM", -3: "MF_ERR_CUDA", -4: "MF_ERR_NOT_CONVERGED",
            -5: "MF_ERR_BREAKDOWN", -6: "MF_ERR_TIMEOUT", -7: "MF_ERR_BUSY", -8: "MF_ERR_UNSUPPORTED",
@@ -46,7 +47,8 @@ class mf_solve_stats(C.Structure):
 
 
 class mf_solve_options(C.Structure):
-    _fields_ = [("inner_rtol", C.c_double), ("chunk_iterations", C.c_int32), ("max_outer", C.c_int32)]
+    _fields_ = [("inner_rtol", C.c_double), ("chunk_iterations", C.c_int32), ("max_outer", C.c_int32),
+                ("cg_form", C.c_int32), ("reserved", C.c_int32)]
 
 
 class mf_server_config(C.Structure):
@@ -120,6 +122,7 @@ def lib() -> C.CDLL:
     L.mf_cg_record_history.argtypes = [vp, i32]
     L.mf_cg_solve_ex.argtypes = [vp, vp, vp, d, i32, i32, C.POINTER(mf_solve_options), C.POINTER(mf_solve_stats),
                                  vp, sz, vp]
+    L.mf_cg_profile.argtypes = [vp, vp, vp, i32, i32, vp, sz, vp, C.POINTER(C.c_double)]
     L.mf_server_create.argtypes = [C.POINTER(mf_server_config), vp, sz, C.POINTER(vp)]
     L.mf_batch_submit.argtypes = [vp, C.POINTER(mf_request), C.POINTER(C.c_uint64)]
     L.mf_batch_poll.argtypes = [vp, C.c_uint64, C.POINTER(mf_result)]
@@ -262,9 +265,9 @@ def mf_cg_workspace_bytes(op, mixed: int = 0) -> int:
 
 def mf_cg_solve(op, b_ptr: int, x_ptr: int, rtol: float, maxit: int, mixed: int, workspace_ptr: int,
                 nbytes: int, stream: int = 0, allow_not_converged: bool = False, inner_rtol: float = 0.0,
-                chunk_iterations: int = 0, max_outer: int = 0) -> dict:
+                chunk_iterations: int = 0, max_outer: int = 0, cg_form: int = 0) -> dict:
     st = mf_solve_stats()
-    opts = mf_solve_options(inner_rtol, chunk_iterations, max_outer)
+    opts = mf_solve_options(inner_rtol, chunk_iterations, max_outer, cg_form, 0)
     code = lib().mf_cg_solve_ex(op, b_ptr, x_ptr, rtol, maxit, mixed, C.byref(opts), C.byref(st), workspace_ptr,
                                 nbytes, stream or None)
     if not (code == MF_OK or (allow_not_converged and code == MF_ERR_NOT_CONVERGED)):
@@ -272,6 +275,14 @@ def mf_cg_solve(op, b_ptr: int, x_ptr: int, rtol: float, maxit: int, mixed: int,
     out = {f: getattr(st, f) for f, _ in mf_solve_stats._fields_}
     out["code"] = code
     return out
+
+
+def mf_cg_profile(op, b_ptr: int, x_ptr: int, iterations: int, cg_form: int, workspace_ptr: int, nbytes: int,
+                  stream: int = 0) -> dict:
+    """Mean kernel durations (ms) of `iterations` directly launched CG iterations."""
+    ms = (C.c_double * 4)()
+    _check(lib().mf_cg_profile(op, b_ptr, x_ptr, iterations, cg_form, workspace_ptr, nbytes, stream or None, ms))
+    return {"apply_ms": ms[0], "dss_ms": ms[1], "vector_ms": ms[2], "iteration_ms": ms[3]}
 
 
 def mf_cg_record_history(hist_ptr: int | None, cap: int) -> None:

@@ -15,6 +15,7 @@
 
 #include "mf_dd.cuh"
 #include "mf_internal.h"
+#include "mf_reduce.cuh"
 #include "mf_solver.h"
 
 namespace mf {
@@ -37,7 +38,7 @@ size_t reduce_scratch_bytes() { return sizeof(RedScratch); }
 // Weight of native element e in an assembled inner product: 0 for padding, otherwise
 // 1 / (number of cells sharing the node).  split = 1: 1 for every real copy.
 template <int N>
-__device__ __forceinline__ double node_weight(const GridInfo& g, long long e, int split) {
+__device__ __forceinline__ float node_weight(const GridInfo& g, long long e, int split) {
   constexpr int N2 = N * N, N3 = N2 * N;
   // tile indices fit in 32 bits (n_native < 2^31 * 32): keep the divisions 32-bit
   const int lane = (int)(e & (BL - 1));
@@ -50,47 +51,15 @@ __device__ __forceinline__ double node_weight(const GridInfo& g, long long e, in
   const int ty = r / g.ntx;
   const int tx = r - ty * g.ntx;
   const int cx = tx * TX + (lane & 3), cy = ty * TY + ((lane >> 2) & 3), cz = tz * TZ + (lane >> 4);
-  if (cx >= g.nx || cy >= g.ny || cz >= g.nz) return 0.0;
-  if (split) return 1.0;
+  if (cx >= g.nx || cy >= g.ny || cz >= g.nz) return 0.0f;
+  if (split) return 1.0f;
   const int i = l % N, j = (l / N) % N, k = l / N2;
   const int sh = (((i == 0 && cx > 0) || (i == N - 1 && cx < g.nx - 1)) ? 1 : 0) +
                  (((j == 0 && cy > 0) || (j == N - 1 && cy < g.ny - 1)) ? 1 : 0) +
                  (((k == 0 && cz > 0) || (k == N - 1 && cz < g.nz - 1)) ? 1 : 0);
-  // 1 / multiplicity = 2^-sh, selected (a double division costs tens of FP64-pipe slots)
-  return sh == 0 ? 1.0 : (sh == 1 ? 0.5 : (sh == 2 ? 0.25 : 0.125));
+  // 1 / multiplicity = 2^-sh, selected (a division would cost far more)
+  return sh == 0 ? 1.0f : (sh == 1 ? 0.5f : (sh == 2 ? 0.25f : 0.125f));
 }
-
-// Per-thread accumulation of w a b (w = 1/multiplicity, a power of two).  Double operands
-// accumulate in FP64.  Float operands never touch the FP64 pipe (GB300 issues 64x fewer FP64
-// than FP32 instructions): the product is split exactly (TwoProd, a b = p + e), scaled
-// exactly by w, and summed in double-float (TwoSum on the leading part); the thread's value
-// enters the FP64 block reduction once.
-struct AccD {
-  double s = 0.0;
-  __device__ __forceinline__ void add(double w, double a, double b) { s = fma(w, a * b, s); }
-  __device__ __forceinline__ double value() const { return s; }
-};
-struct AccF {
-  float hi = 0.0f, lo = 0.0f;
-  __device__ __forceinline__ void add(double wd, float a, float b) {
-    const float w = (float)wd;
-    const float p = a * b;
-    const float e = fmaf(a, b, -p);
-    const float pw = p * w, ew = e * w;
-    const float s = hi + pw;
-    const float v = s - hi;
-    const float t = (hi - (s - v)) + (pw - v);
-    hi = s;
-    lo += t + ew;
-  }
-  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-};
-template <typename T>
-struct AccOf;
-template <>
-struct AccOf<double> { using type = AccD; };
-template <>
-struct AccOf<float> { using type = AccF; };
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -213,10 +182,124 @@ __global__ void __launch_bounds__(RED_THREADS) cg_xr_kernel(T* __restrict__ x, T
 template <typename T>
 __global__ void cg_p_kernel(const T* __restrict__ r, T* __restrict__ p, long long n, const CgState* st, int was_running) {
   (void)was_running;
-  const T be = (T)st->beta;
+  const T be = scalar_from_double<T>(st->beta);
   if (st->flag != 0 && st->flag != 1) return;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    p[e] = fma(be, p[e], r[e]);
+    p[e] = finish(fma(be, p[e], r[e]));
+}
+
+// Split-dual CG update (Sec. 4: the Krylov loop on split data).  q~ = A_K p is the split
+// product written by the apply; its assembled value q = G G^T q~ is formed here, per copy, as
+// the sum of the copies of the node in the canonical order of the duplicate summation (pairs
+// along x, then the pair sums along y, then along z -- the same expression in every copy, so
+// q is consistent bitwise and equal to what the separate duplicate summation writes).  Then
+// x += alpha p, r -= alpha q, and <r, r> (copies weighted by 1/multiplicity) gives
+// beta = <r,r>_new / <r,r> and the convergence test.
+//
+// Work unit: one x-pencil (tile t, local j, k) of the 32 cells of a tile; a warp takes a unit,
+// lane = cell, so each of its accesses is one contiguous 32-element row.  Every load of the
+// unit (the pencil's x, p, r, q~, and the q~ of the neighbour copies along y / z and of the
+// x-neighbours at both pencil ends) is issued before any sum, so a thread keeps up to 7n + 8
+// loads in flight.
+template <typename T, int N>
+__global__ void __launch_bounds__(RED_THREADS) cg_update_kernel(T* __restrict__ x, T* __restrict__ r,
+                                                                const T* __restrict__ p, const T* __restrict__ q,
+                                                                GridInfo g, RedScratch* sc, CgState* st, double* hist) {
+  constexpr int N2 = N * N, N3 = N2 * N, K = N - 1;
+  if (st->flag != 0) return; // uniform: converged or stopped, nothing changes
+  const T al = scalar_from_double<T>(st->alpha);
+  const long long tile_el = (long long)N3 * BL;                 // elements of one tile
+  const long long ty_step = (long long)g.ntx * tile_el;         // one tile row along y
+  const long long tz_step = (long long)g.ntx * g.nty * tile_el; // one tile layer along z
+  const int lane = threadIdx.x & 31;
+  const int lx = lane & 3, ly = (lane >> 2) & 3, lz = lane >> 4;
+  // element distance to the neighbour copy across each face of the cell
+  const long long dxm = lx > 0 ? (long long)K * BL - 1 : (long long)K * BL - tile_el + (TX - 1);
+  const long long dxp = lx < TX - 1 ? -(long long)K * BL + 1 : tile_el - (long long)K * BL - (TX - 1);
+  const long long dym = ly > 0 ? (long long)K * N * BL - TX : (long long)K * N * BL - ty_step + TX * (TY - 1);
+  const long long dyp = ly < TY - 1 ? -(long long)K * N * BL + TX : ty_step - (long long)K * N * BL - TX * (TY - 1);
+  const long long dzm = lz > 0 ? (long long)K * N2 * BL - TX * TY : (long long)K * N2 * BL - tz_step + TX * TY * (TZ - 1);
+  const long long dzp =
+      lz < TZ - 1 ? -(long long)K * N2 * BL + TX * TY : tz_step - (long long)K * N2 * BL - TX * TY * (TZ - 1);
+  const long long units = g.ntiles * N2;
+  const long long warps = (long long)gridDim.x * (RED_THREADS / 32);
+  typename AccOf<T>::type acc;
+  for (long long u = blockIdx.x * (long long)(RED_THREADS / 32) + (threadIdx.x >> 5); u < units; u += warps) {
+    const long long t = u / N2;
+    const int jk = (int)(u - t * N2);
+    const int j = jk % N, k = jk / N;
+    const int txy = g.ntx * g.nty;
+    const int tz = (int)(t / txy);
+    const int rm = (int)(t - (long long)tz * txy);
+    const int ty = rm / g.ntx, tx = rm - ty * g.ntx;
+    const int cx = tx * TX + lx, cy = ty * TY + ly, cz = tz * TZ + lz;
+    if (cx >= g.nx || cy >= g.ny || cz >= g.nz) continue; // padding lane: nothing to update
+    const bool hxm = cx > 0, hxp = cx < g.nx - 1;
+    const bool ym = j == 0 && cy > 0, yp = j == K && cy < g.ny - 1;
+    const bool zm = k == 0 && cz > 0, zp = k == K && cz < g.nz - 1;
+    const int my = (ym || yp) ? 2 : 1, mz = (zm || zp) ? 2 : 1;
+    // copy offsets along y and z: index 0 = low copy, 1 = high copy (0 = this copy)
+    const long long oy[2] = {ym ? dym : 0, yp ? dyp : 0};
+    const long long oz[2] = {zm ? dzm : 0, zp ? dzp : 0};
+    const long long e0 = t * tile_el + (long long)(N * j + N2 * k) * BL + lane;
+    T Q[2][2][N], XM[2][2], XP[2][2];
+#pragma unroll
+    for (int zz = 0; zz < 2; ++zz)
+#pragma unroll
+      for (int yy = 0; yy < 2; ++yy)
+        if (zz < mz && yy < my) {
+          const long long o = e0 + oz[zz] + oy[yy];
+#pragma unroll
+          for (int i = 0; i < N; ++i) Q[zz][yy][i] = q[o + (long long)i * BL];
+          if (hxm) XM[zz][yy] = q[o + dxm];
+          if (hxp) XP[zz][yy] = q[o + (long long)K * BL + dxp];
+        }
+    T xv[N], pv[N], rv[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      xv[i] = x[e0 + (long long)i * BL];
+      pv[i] = p[e0 + (long long)i * BL];
+      rv[i] = r[e0 + (long long)i * BL];
+    }
+    const int shyz = (my - 1) + (mz - 1);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const bool xl = i == 0 && hxm, xh = i == K && hxp;
+      T sz[2];
+#pragma unroll
+      for (int zz = 0; zz < 2; ++zz)
+        if (zz < mz) {
+          T sy[2];
+#pragma unroll
+          for (int yy = 0; yy < 2; ++yy)
+            if (yy < my) {
+              T v = Q[zz][yy][i];
+              if (xl) v = XM[zz][yy] + v;
+              else if (xh) v = v + XP[zz][yy];
+              sy[yy] = v;
+            }
+          sz[zz] = my == 2 ? sy[0] + sy[1] : sy[0];
+        }
+      const T qv = mz == 2 ? sz[0] + sz[1] : sz[0];
+      const long long e = e0 + (long long)i * BL;
+      x[e] = finish(fma(al, pv[i], xv[i]));
+      const T rn = finish(fma(-al, qv, rv[i]));
+      r[e] = rn;
+      const int sh = shyz + ((xl || xh) ? 1 : 0);
+      acc.add(sh == 0 ? 1.0f : (sh == 1 ? 0.5f : (sh == 2 ? 0.25f : 0.125f)), rn, rn);
+    }
+  }
+  const double s = block_sum(acc.value());
+  double tot;
+  if (last_block_total(sc, s, &tot)) {
+    st->beta = tot / st->rr;
+    st->rr = tot;
+    st->it += 1;
+    if (hist && st->it < HIST_CAP) hist[st->it] = sqrt(tot) / st->bnorm;
+    if (tot <= st->tol2) st->flag = 1;
+    else if (!isfinite(tot)) st->flag = 2;
+    else if (st->it >= st->maxit) st->flag = 3;
+  }
 }
 
 // Small element-wise kernels of the drivers.
@@ -242,6 +325,44 @@ __global__ void axpy64_kernel(double* __restrict__ x, const float* __restrict__ 
   const double sc = sqrt(*rn2);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) x[e] += sc * (double)d[e];
 }
+// FP64 solver with double-float vectors: r = b 2^-s as double-float, where 2^s is the power of
+// two of max|b| (so every value of the iteration stays well inside the float exponent range,
+// for right-hand sides anywhere in the double range); the solution is converted back with
+// x = 2^s x~ at the end.  max|b| is an integer max over the bit patterns of |b| (order-free,
+// so deterministic); *amax must be zero before the launch.
+__global__ void absmax_bits_kernel(const double* __restrict__ b, unsigned long long* amax, long long n) {
+  unsigned long long m = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    m = max(m, (unsigned long long)__double_as_longlong(b[e]) & 0x7fffffffffffffffull);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(amax, m);
+}
+// 2^s from the bits of max|b|: s = its unbiased exponent; 1 for zero, subnormal or non-finite
+__device__ __forceinline__ double pow2_of_bits(unsigned long long bits) {
+  const int e = (int)((bits >> 52) & 0x7ff);
+  if (e == 0 || e == 0x7ff) return 1.0;
+  return __longlong_as_double((long long)e << 52); // 2^(e - 1023)
+}
+__device__ __forceinline__ double inv_pow2_of_bits(unsigned long long bits) {
+  const int e = (int)((bits >> 52) & 0x7ff);
+  if (e == 0 || e == 0x7ff) return 1.0;
+  const int f = 2046 - e; // biased exponent of 2^(1023 - e); 0 means 2^-1023, a subnormal
+  return f > 0 ? __longlong_as_double((long long)f << 52) : __longlong_as_double(1ll << 51);
+}
+__global__ void to_dd_scaled_kernel(const double* __restrict__ b, dd* __restrict__ r, const unsigned long long* amax,
+                                    long long n) {
+  const double isc = inv_pow2_of_bits(*amax);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    r[e] = dd_from_double(b[e] * isc);
+}
+__global__ void from_dd_scaled_kernel(const dd* __restrict__ x, double* __restrict__ o, const unsigned long long* amax,
+                                      long long n) {
+  const double sc = pow2_of_bits(*amax);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    o[e] = dd_to_double(x[e]) * sc;
+}
+
 // Dirichlet mask P b (zero constrained copies) -- used on the right-hand side
 template <typename T, int N>
 __global__ void mask_kernel(const T* __restrict__ b, T* __restrict__ o, long long n, GridInfo g) {
@@ -279,6 +400,8 @@ static mf_status dot_n(const mf_operator* op, int elem, const void* a, const voi
   const int bl = red_blocks(n);
   if (elem == 8)
     dot_kernel<double, N><<<bl, RED_THREADS, 0, s>>>((const double*)a, (const double*)b, n, op->g, split, sc, out);
+  else if (elem == ELEM_DD)
+    dot_kernel<dd, N><<<bl, RED_THREADS, 0, s>>>((const dd*)a, (const dd*)b, n, op->g, split, sc, out);
   else
     dot_kernel<float, N><<<bl, RED_THREADS, 0, s>>>((const float*)a, (const float*)b, n, op->g, split, sc, out);
   return cuda_check(cudaGetLastError(), "dot launch");
@@ -338,6 +461,52 @@ static mf_status launch_cg_vec(const mf_operator* op, int elem, void* x, void* r
   MF_SWITCH_N(op->n, cg_vec_e, op, elem, x, r, p, q, sc1, sc2, st, hist, s);
 }
 
+// One split-dual CG iteration: fused apply (p = r + beta p, q~ = A_K p, alpha) and the fused
+// update (q = G G^T q~, x, r, beta).
+template <int N>
+static mf_status cg_update_e(const mf_operator* op, int elem, void* x, void* r, void* p, void* q, const SolveWs& w,
+                             CgState* st, double* hist, cudaStream_t s) {
+  // one warp per x-pencil unit, at most RED_MAX_BLOCKS CTAs (warps loop over further units)
+  long long bl = (op->g.ntiles * (long long)N * N + RED_THREADS / 32 - 1) / (RED_THREADS / 32);
+  if (bl > RED_MAX_BLOCKS) bl = RED_MAX_BLOCKS;
+  if (bl < 1) bl = 1;
+  if (elem == 8)
+    cg_update_kernel<double, N><<<(unsigned)bl, RED_THREADS, 0, s>>>((double*)x, (double*)r, (const double*)p,
+                                                                      (const double*)q, op->g, w.sc2, st, hist);
+  else if (elem == ELEM_DD)
+    cg_update_kernel<dd, N><<<(unsigned)bl, RED_THREADS, 0, s>>>((dd*)x, (dd*)r, (const dd*)p, (const dd*)q, op->g,
+                                                                  w.sc2, st, hist);
+  else
+    cg_update_kernel<float, N><<<(unsigned)bl, RED_THREADS, 0, s>>>((float*)x, (float*)r, (const float*)p,
+                                                                     (const float*)q, op->g, w.sc2, st, hist);
+  return cuda_check(cudaGetLastError(), "cg update launch");
+}
+static mf_status launch_cg_update(const mf_operator* op, int elem, void* x, void* r, void* p, void* q, const SolveWs& w,
+                                  CgState* st, double* hist, cudaStream_t s) {
+  MF_SWITCH_N(op->n, cg_update_e, op, elem, x, r, p, q, w, st, hist, s);
+}
+template <int N>
+static mf_status cg_p_e(const mf_operator* op, int elem, const void* r, void* p, CgState* st, cudaStream_t s) {
+  const long long n = op->n_native;
+  if (elem == 8) cg_p_kernel<double><<<ew_blocks(n), 256, 0, s>>>((const double*)r, (double*)p, n, st, 1);
+  else if (elem == ELEM_DD) cg_p_kernel<dd><<<ew_blocks(n), 256, 0, s>>>((const dd*)r, (dd*)p, n, st, 1);
+  else cg_p_kernel<float><<<ew_blocks(n), 256, 0, s>>>((const float*)r, (float*)p, n, st, 1);
+  return cuda_check(cudaGetLastError(), "cg p launch");
+}
+static mf_status launch_cg_p(const mf_operator* op, int elem, const void* r, void* p, CgState* st, cudaStream_t s) {
+  MF_SWITCH_N(op->n, cg_p_e, op, elem, r, p, st, s);
+}
+// One split-dual iteration: apply with <p, A_K p> (alpha), update (q = G G^T q~, x, r, beta),
+// then p = r + beta p -- or, with fused_p, the apply forms p = r + beta p itself at load.
+static mf_status launch_cg_split(const mf_operator* op, int elem, void* x, void* r, void* p, void* q, const SolveWs& w,
+                                 CgState* st, double* hist, int fused_p, cudaStream_t s) {
+  const int vk = elem == ELEM_DD ? VK_DDS : view_of_elem(op, elem);
+  mf_status rc = launch_apply_cg(op, vk, p, r, q, st, w.apart, w.acount, fused_p, s);
+  if (rc) return rc;
+  if ((rc = launch_cg_update(op, elem, x, r, p, q, w, st, hist, s))) return rc;
+  return fused_p ? MF_OK : launch_cg_p(op, elem, r, p, st, s);
+}
+
 // apply + duplicate summation with a given element type (selects the FP64 or FP32 view)
 static mf_status apply_elem(const mf_operator* op, int elem, const void* x, void* y, cudaStream_t s) {
   mf_status st = launch_apply_split(op, view_of_elem(op, elem), x, y, s);
@@ -362,10 +531,13 @@ size_t solve_ws_layout(const mf_operator* op, int mixed, char* base, SolveWs* w)
   t.sc3 = (RedScratch*)take(sizeof(RedScratch));
   t.hist = (double*)take(sizeof(double) * HIST_CAP);
   t.scal = (double*)take(sizeof(double) * 16);
+  t.acount = (unsigned*)take(256);
+  t.apart = (double*)take(sizeof(double) * (size_t)apply_max_blocks(op));
   t.r = take(n * elem);
   t.p = take(n * elem);
   t.q = take(n * elem);
-  t.r64 = t.q64 = t.b64 = t.d32 = nullptr;
+  t.r64 = t.q64 = t.b64 = t.d32 = t.xdd = nullptr;
+  if (!mixed && elem == 8 && fp64_view(op) == VK_DD) t.xdd = take(n * 8); // double-float iterate
   if (mixed) {
     t.r64 = take(n * 8);
     t.q64 = take(n * 8);
@@ -400,18 +572,31 @@ __global__ void init_state_kernel(CgState* st, const double* rr0, double rtol, i
 static mf_status eng_inner_start(SolverEngine* e, const void* rhs, void* x_in, double rtol, int maxit) {
   const long long n = e->op->n_native;
   cudaStream_t s = e->s;
-  const int el = e->elem_in;
-  if (el == 8) {
+  const int el = e->vt;
+  mf_status st;
+  // p = r; with the direction update fused into the apply: p = 0 and beta = 0, so the first
+  // apply forms p = r + 0 p = r
+  if (el == ELEM_DD) {
+    // double-float vectors (8 bytes like a double; zero is all-zero bits in both): r = b 2^-s
+    unsigned long long* amax = reinterpret_cast<unsigned long long*>(e->w.scal + 3);
+    if ((st = cuda_check(cudaMemsetAsync(amax, 0, sizeof(*amax), s), "max clear"))) return st;
+    absmax_bits_kernel<<<ew_blocks(n), 256, 0, s>>>((const double*)rhs, amax, n);
+    zero_kernel<double><<<ew_blocks(n), 256, 0, s>>>((double*)x_in, n);
+    to_dd_scaled_kernel<<<ew_blocks(n), 256, 0, s>>>((const double*)rhs, (dd*)e->w.r, amax, n);
+    if (e->form == MF_CG_SPLIT_DUAL_FUSED) zero_kernel<double><<<ew_blocks(n), 256, 0, s>>>((double*)e->w.p, n);
+    else copy_kernel<double><<<ew_blocks(n), 256, 0, s>>>((const double*)e->w.r, (double*)e->w.p, n);
+  } else if (el == 8) {
     zero_kernel<double><<<ew_blocks(n), 256, 0, s>>>((double*)x_in, n);
     copy_kernel<double><<<ew_blocks(n), 256, 0, s>>>((const double*)rhs, (double*)e->w.r, n);
-    copy_kernel<double><<<ew_blocks(n), 256, 0, s>>>((const double*)rhs, (double*)e->w.p, n);
+    if (e->form == MF_CG_SPLIT_DUAL_FUSED) zero_kernel<double><<<ew_blocks(n), 256, 0, s>>>((double*)e->w.p, n);
+    else copy_kernel<double><<<ew_blocks(n), 256, 0, s>>>((const double*)rhs, (double*)e->w.p, n);
   } else {
     zero_kernel<float><<<ew_blocks(n), 256, 0, s>>>((float*)x_in, n);
     copy_kernel<float><<<ew_blocks(n), 256, 0, s>>>((const float*)rhs, (float*)e->w.r, n);
-    copy_kernel<float><<<ew_blocks(n), 256, 0, s>>>((const float*)rhs, (float*)e->w.p, n);
+    if (e->form == MF_CG_SPLIT_DUAL_FUSED) zero_kernel<float><<<ew_blocks(n), 256, 0, s>>>((float*)e->w.p, n);
+    else copy_kernel<float><<<ew_blocks(n), 256, 0, s>>>((const float*)rhs, (float*)e->w.p, n);
   }
-  mf_status st = cuda_check(cudaGetLastError(), "cg init");
-  if (st) return st;
+  if ((st = cuda_check(cudaGetLastError(), "cg init"))) return st;
   if ((st = dot_launch(e->op, el, e->w.r, e->w.r, 0, e->w.scal, e->w.sc3, s))) return st;
   init_state_kernel<<<1, 1, 0, s>>>(e->w.st, e->w.scal, rtol, maxit);
   if ((st = cuda_check(cudaGetLastError(), "init state"))) return st;
@@ -426,9 +611,15 @@ static mf_status eng_chunk(SolverEngine* e) {
     if ((st = cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture begin"))) return st;
     mf_status cst = MF_OK;
     for (int c = 0; c < e->chunk && cst == MF_OK; ++c) {
-      cst = apply_elem(e->op, e->elem_in, e->w.p, e->w.q, s);
-      if (cst == MF_OK)
-        cst = launch_cg_vec(e->op, e->elem_in, e->x_in, e->w.r, e->w.p, e->w.q, e->w.sc1, e->w.sc2, e->w.st, e->w.hist, s);
+      if (e->form != MF_CG_ASSEMBLED) {
+        cst = launch_cg_split(e->op, e->vt, e->x_in, e->w.r, e->w.p, e->w.q, e->w, e->w.st, e->w.hist,
+                              e->form == MF_CG_SPLIT_DUAL_FUSED, s);
+      } else {
+        cst = apply_elem(e->op, e->elem_in, e->w.p, e->w.q, s);
+        if (cst == MF_OK)
+          cst = launch_cg_vec(e->op, e->elem_in, e->x_in, e->w.r, e->w.p, e->w.q, e->w.sc1, e->w.sc2, e->w.st,
+                              e->w.hist, s);
+      }
     }
     cudaError_t ce = cudaStreamEndCapture(s, &e->graph);
     if (cst) {
@@ -492,9 +683,19 @@ mf_status engine_start(SolverEngine* e) {
   // itself after every launch); the workspace may hold anything
   for (RedScratch* sc : {e->w.sc1, e->w.sc2, e->w.sc3})
     if ((st = cuda_check(cudaMemsetAsync(sc, 0, sizeof(unsigned) * 64, e->s), "counter clear"))) return st;
+  if ((st = cuda_check(cudaMemsetAsync(e->w.acount, 0, sizeof(unsigned), e->s), "counter clear"))) return st;
+  // The FP64 solver of a double-float operator keeps its split-dual iteration's vectors in
+  // double-float as well: every vector operation then runs on the FP32 pipe (GB300's FP64 pipe
+  // could not keep up with HBM even for the vector updates).  b is scaled by a power of two
+  // near 1/||b|| on entry and x converted back on exit.
+  e->vt = e->elem_in;
+  if (!e->mixed && e->elem_in == 8 && fp64_view(e->op) == VK_DD && e->form != MF_CG_ASSEMBLED && e->w.xdd) {
+    e->vt = ELEM_DD;
+    e->x_in = e->w.xdd;
+  }
   if (!e->mixed) {
     if ((st = launch_mask(e->op, e->elem_in, e->b, e->w.q, e->s))) return st;
-    return eng_inner_start(e, e->w.q, e->x, e->rtol, e->maxit);
+    return eng_inner_start(e, e->w.q, e->x_in, e->rtol, e->maxit);
   }
   if ((st = launch_mask(e->op, 8, e->b, e->w.b64, e->s))) return st;
   zero_kernel<double><<<ew_blocks(n), 256, 0, e->s>>>((double*)e->x, n);
@@ -527,6 +728,11 @@ mf_status engine_advance(SolverEngine* e) {
     eng_record_history(e, h.it);
     e->total_it += h.it;
     if (!e->mixed) {
+      if (e->vt == ELEM_DD) { // x = 2^s x~
+        from_dd_scaled_kernel<<<ew_blocks(n), 256, 0, e->s>>>(
+            (const dd*)e->w.xdd, (double*)e->x, reinterpret_cast<const unsigned long long*>(e->w.scal + 3), n);
+        if ((st = cuda_check(cudaGetLastError(), "solution conversion"))) return st;
+      }
       e->rel = (h.bnorm > 0) ? std::sqrt(h.rr) / h.bnorm : 0.0;
       if (e->cancel) return eng_finish(e, MF_ERR_BUSY);
       if (h.flag == 2)
@@ -601,7 +807,8 @@ mf_status mf_cg_solve_ex(const mf_operator* op, const void* b_dev, void* x_dev, 
                          void* stream) {
   if (!op || !b_dev || !x_dev) return set_error(MF_ERR_ARG, "mf_cg_solve: NULL argument");
   if (opts && ((opts->inner_rtol != 0.0 && !(opts->inner_rtol > 0.0 && opts->inner_rtol < 1.0)) ||
-               opts->chunk_iterations < 0 || opts->max_outer < 0))
+               opts->chunk_iterations < 0 || opts->max_outer < 0 || opts->cg_form < 0 ||
+               opts->cg_form > MF_CG_SPLIT_DUAL_FUSED))
     return set_error(MF_ERR_ARG, "mf_cg_solve_ex: bad options");
   if (!op->ready) return set_error(MF_ERR_ARG, "mf_cg_solve: operator not set up");
   if (maxit < 0 || !(rtol >= 0.0)) return set_error(MF_ERR_ARG, "mf_cg_solve: bad rtol/maxit");
@@ -633,6 +840,7 @@ mf_status mf_cg_solve_ex(const mf_operator* op, const void* b_dev, void* x_dev, 
     if (opts->inner_rtol > 0.0) e.inner_rtol = opts->inner_rtol;
     if (opts->chunk_iterations > 0) e.chunk = opts->chunk_iterations;
     if (opts->max_outer > 0) e.max_outer = opts->max_outer;
+    if (opts->cg_form != MF_CG_DEFAULT) e.form = opts->cg_form;
   }
   e.record = g_hist_host != nullptr;
   mf_status st = engine_start(&e);
@@ -662,6 +870,67 @@ mf_status mf_cg_solve_ex(const mf_operator* op, const void* b_dev, void* x_dev, 
   if (stats) *stats = out;
   if (st == MF_ERR_NOT_CONVERGED) set_error(st, "mf_cg_solve: not converged after %d iterations", out.iterations);
   return st;
+}
+
+mf_status mf_cg_profile(const mf_operator* op, const void* b_dev, void* x_dev, int iterations, int cg_form,
+                        void* workspace_dev, size_t bytes, void* stream, double* ms_out) {
+  if (!op || !b_dev || !x_dev || !ms_out) return set_error(MF_ERR_ARG, "mf_cg_profile: NULL argument");
+  if (!op->ready) return set_error(MF_ERR_ARG, "mf_cg_profile: operator not set up");
+  if (iterations < 1 || iterations > 1000 || cg_form < 0 || cg_form > MF_CG_SPLIT_DUAL_FUSED)
+    return set_error(MF_ERR_ARG, "mf_cg_profile: iterations must be in [1, 1000], cg_form an MF_CG_* value");
+  const size_t need = mf_cg_workspace_bytes(op, 0);
+  if (!workspace_dev || bytes < need) return set_error(MF_ERR_OOM, "mf_cg_profile: workspace %zu < %zu", bytes, need);
+  if (reinterpret_cast<uintptr_t>(workspace_dev) & 255) return set_error(MF_ERR_ARG, "mf_cg_profile: workspace alignment");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  HostMirror hm;
+  std::memset(&hm, 0, sizeof(hm));
+  SolverEngine e;
+  engine_init(&e, op, 0, b_dev, x_dev, 0.0, iterations, workspace_dev, s, &hm);
+  if (cg_form != MF_CG_DEFAULT) e.form = cg_form;
+  mf_status st = engine_start(&e);
+  if (st) return st;
+  std::vector<cudaEvent_t> ev(4 * (size_t)iterations, nullptr);
+  for (auto& x : ev)
+    if ((st = cuda_check(cudaEventCreate(&x), "mf_cg_profile event"))) break;
+  const int el = e.vt;
+  for (int it = 0; it < iterations && st == MF_OK; ++it) {
+    cudaEvent_t* E = &ev[4 * (size_t)it];
+    cudaEventRecord(E[0], s);
+    if (e.form != MF_CG_ASSEMBLED) {
+      const int fp = e.form == MF_CG_SPLIT_DUAL_FUSED;
+      const int vk = el == ELEM_DD ? VK_DDS : view_of_elem(op, el);
+      st = launch_apply_cg(op, vk, e.w.p, e.w.r, e.w.q, e.w.st, e.w.apart, e.w.acount, fp, s);
+      cudaEventRecord(E[1], s);
+      cudaEventRecord(E[2], s);
+      if (st == MF_OK) st = launch_cg_update(op, el, e.x_in, e.w.r, e.w.p, e.w.q, e.w, e.w.st, nullptr, s);
+      if (st == MF_OK && !fp) st = launch_cg_p(op, el, e.w.r, e.w.p, e.w.st, s);
+    } else {
+      st = launch_apply_split(op, view_of_elem(op, el), e.w.p, e.w.q, s);
+      cudaEventRecord(E[1], s);
+      if (st == MF_OK) st = launch_dss(op, el, e.w.q, s);
+      cudaEventRecord(E[2], s);
+      if (st == MF_OK)
+        st = launch_cg_vec(op, el, e.x_in, e.w.r, e.w.p, e.w.q, e.w.sc1, e.w.sc2, e.w.st, nullptr, s);
+    }
+    cudaEventRecord(E[3], s);
+  }
+  if (st == MF_OK) st = cuda_check(cudaStreamSynchronize(s), "mf_cg_profile sync");
+  double acc[4] = {0, 0, 0, 0};
+  for (int it = 0; it < iterations && st == MF_OK; ++it) {
+    cudaEvent_t* E = &ev[4 * (size_t)it];
+    float a = 0, b = 0, c = 0, d = 0;
+    cudaEventElapsedTime(&a, E[0], E[1]);
+    cudaEventElapsedTime(&b, E[1], E[2]);
+    cudaEventElapsedTime(&c, E[2], E[3]);
+    cudaEventElapsedTime(&d, E[0], E[3]);
+    acc[0] += a; acc[1] += b; acc[2] += c; acc[3] += d;
+  }
+  for (auto& x : ev)
+    if (x) cudaEventDestroy(x);
+  if (st) return st;
+  for (int i = 0; i < 4; ++i) ms_out[i] = acc[i] / iterations;
+  if (e.form != MF_CG_ASSEMBLED) ms_out[1] = 0.0;
+  return MF_OK;
 }
 
 } // extern "C"

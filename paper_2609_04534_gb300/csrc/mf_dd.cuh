@@ -52,6 +52,8 @@ __device__ __forceinline__ dd operator*(dd a, dd b) {
   return finish(dd(p, e));
 }
 
+__host__ __device__ __forceinline__ dd operator-(dd a) { return dd(-a.hi, -a.lo); }
+
 __device__ __forceinline__ dd operator+(dd a, dd b) {
   const float s = a.hi + b.hi;
   const float v = s - a.hi;
@@ -92,6 +94,12 @@ __device__ __forceinline__ double f2d_bits(float f) {
 
 // dd -> double: exact sum of the two parts (one FP64 add).
 __device__ __forceinline__ double dd_to_double(dd a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
+
+// A double scalar (a CG coefficient) in a vector element type.
+template <typename S>
+__device__ __forceinline__ S scalar_from_double(double v) { return (S)v; }
+template <>
+__device__ __forceinline__ dd scalar_from_double<dd>(double v) { return dd_from_double(v); }
 
 // storage <-> compute conversions used by the kernels
 template <typename C, typename S>

@@ -38,7 +38,40 @@ struct Tab {
 };
 
 // Precision views of an operator: storage type of the vectors / compute type of the apply.
-enum ViewKind { VK_F64 = 0, VK_DD = 1, VK_F32 = 2 };
+// VK_DDS is VK_DD with double-float storage (the FP64 solver's internal vectors); it shares
+// VK_DD's geometry and launch variant.
+enum ViewKind { VK_F64 = 0, VK_DD = 1, VK_F32 = 2, VK_DDS = 3 };
+// Element types of vectors: 8 double, 4 float, ELEM_DD double-float (8 bytes).
+constexpr int ELEM_DD = 9;
+
+// Device-resident CG scalars.
+struct CgState {
+  double rr;    // <r, r> (assembled)
+  double pq;    // <p, A p>
+  double alpha, beta;
+  double bnorm; // ||b|| of this CG
+  double tol2;  // (rtol * ||b||)^2
+  int it;       // iterations done
+  int flag;     // 0 running, 1 converged, 2 breakdown, 3 maxit
+  int maxit;
+  int pad;
+};
+
+// CG step carried by an apply launch (the split-dual iteration of Sec. 4): with st set, the
+// apply writes the split product y = A_K p per cell (no duplicate summation) and reduces
+// <p, y> over all copies -- the pairing of a consistent with a split vector, Lemma 1 -- to
+// alpha = <r, r> / <p, y> in its last CTA (partials: one double per CTA).  The input is
+// p = x; with update_p the apply instead reads r and the previous direction p and forms
+// p = r + beta p at load (written back in place).
+template <typename S>
+struct CgFuse {
+  S* p;
+  const S* r;
+  CgState* st;
+  double* partials;
+  unsigned* counter;
+  int update_p;
+};
 
 template <typename S, typename T, int N>
 struct ApplyArgs {
@@ -54,6 +87,7 @@ struct ApplyArgs {
   // sin(pi xh), cos(pi xh) at the Gauss points of every cell layer ([(nx+ny+nz)*N][2]).
   const float* gtab;
   float amp, cm, h[3];
+  CgFuse<S> cg; // cg.st == nullptr: plain apply
 };
 
 // Host-side double tables (any n <= MAXN).
@@ -104,12 +138,20 @@ mf_status cuda_check(cudaError_t e, const char* what);
 // elem: 8 or 4.  All return MF_OK or an error status.
 // apply / geometry take a ViewKind; dss / layout / reductions take the element size.
 mf_status launch_apply_split(const mf_operator* op, int vk, const void* x, void* y, cudaStream_t s);
+// CG step apply (see CgFuse): p and r in the element type of the view vk
+mf_status launch_apply_cg(const mf_operator* op, int vk, void* p, const void* r, void* y, CgState* st, double* partials,
+                          unsigned* counter, int update_p, cudaStream_t s);
+// upper bound of the CTA count of any apply launch of op (size of CgFuse::partials)
+long long apply_max_blocks(const mf_operator* op);
 mf_status launch_dss(const mf_operator* op, int elem, void* y, cudaStream_t s);
 mf_status launch_geometry(const mf_operator* op, int vk, void* geom, cudaStream_t s);
 mf_status launch_layout(const mf_operator* op, int elem, int mode, const void* in, void* out, cudaStream_t s);
 
 template <int N>
 mf_status apply_split_n(const mf_operator* op, int vk, const void* x, void* y, cudaStream_t s);
+template <int N>
+mf_status apply_cg_n(const mf_operator* op, int vk, void* p, const void* r, void* y, CgState* st, double* partials,
+                     unsigned* counter, int update_p, cudaStream_t s);
 template <int N>
 mf_status dss_n(const mf_operator* op, int elem, void* y, cudaStream_t s);
 template <int N>

@@ -6,6 +6,7 @@
 #pragma once
 #include "mf_dd.cuh"
 #include "mf_internal.h"
+#include "mf_reduce.cuh"
 
 namespace mf {
 
@@ -24,6 +25,7 @@ struct Cfg {
   static constexpr int CB = V == 0 ? CB0 : ((CB0 / 2) >= 4 ? (CB0 / 2) : 4);
   static constexpr int MINB = V == 0 ? 2 : (V == 1 ? 3 : 1);
   static constexpr int NT = N * N * CB;
+  static_assert(CB >= 4 && BL % CB == 0, "a CTA holds at least 4 cells of a tile (apply_max_blocks)");
 };
 
 __device__ __forceinline__ void cell_of(const GridInfo& g, long long t64, int lane, int& cx, int& cy, int& cz) {
@@ -50,32 +52,68 @@ __device__ __forceinline__ bool on_cube_boundary(const GridInfo& g, int cx, int 
          (cy == g.ny - 1 && j == N - 1) || (cz == 0 && k == 0) || (cz == g.nz - 1 && k == N - 1);
 }
 
+// Accumulators of the fused CG pairing in store_xpencil: PairAcc sums p y of the stored
+// values (Cartesian path); NoAcc when the kernel forms the pairing at the quadrature points.
+template <typename S>
+struct PairAcc {
+  static constexpr bool active = true;
+  typename AccOf<S>::type acc;
+  __device__ __forceinline__ void add(S p, S y) { acc.add(p, y); }
+  __device__ __forceinline__ double value() const { return acc.value(); }
+};
+struct NoAcc {
+  static constexpr bool active = false;
+  template <typename S>
+  __device__ __forceinline__ void add(S, S) {}
+};
+
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(float v) { return (double)v; }
+__device__ __forceinline__ double to_double(dd v) { return dd_to_double(v); }
+
 // Load the CB cells [lane0, lane0+CB) of tile t into smem as buf[l*CB + c] (cell fastest),
-// zeroing padding cells and, for Dirichlet, the constrained nodes (the P of P A P).
+// zeroing padding cells and, for Dirichlet, the constrained nodes (the P of P A P).  In a
+// CG step with update_p the loaded vector is the new direction p = r + beta p, written back.
 template <typename S, typename T, int N, int CB, int NT>
 __device__ __forceinline__ void load_tile(const ApplyArgs<S, T, N>& a, long long t, int lane0, T* buf) {
   constexpr int N2 = N * N, N3 = N2 * N;
   const long long base = t * (long long)N3 * BL + lane0;
+  const bool fuse = a.cg.st != nullptr && a.cg.update_p;
+  const S beta = fuse ? scalar_from_double<S>(a.cg.st->beta) : S(0);
+  S* __restrict__ pg = a.cg.p;
+  const S* __restrict__ rg = a.cg.r;
+#pragma unroll
   for (int idx = threadIdx.x; idx < N3 * CB; idx += NT) {
     const int l = idx / CB, c = idx - l * CB;
+    const long long e = base + (long long)l * BL + c;
     int cx, cy, cz;
     cell_of(a.g, t, lane0 + c, cx, cy, cz);
     T v = T(0);
     if (cx < a.g.nx && cy < a.g.ny && cz < a.g.nz) {
-      v = to_compute<T, S>(a.x[base + (long long)l * BL + c]);
+      S xv;
+      if (fuse) {
+        xv = finish(fma(beta, pg[e], rg[e]));
+        pg[e] = xv;
+      } else {
+        xv = a.x[e];
+      }
+      v = to_compute<T, S>(xv);
       if (a.g.bc) {
         const int i = l % N, j = (l / N) % N, k = l / N2;
         if (on_cube_boundary<N>(a.g, cx, cy, cz, i, j, k)) v = T(0);
       }
+    } else if (fuse) {
+      pg[e] = S(0);
     }
     buf[idx] = v;
   }
 }
 
-// Store one x-pencil (j, k) of cell c to global y, zeroing padding / constrained nodes.
-template <typename S, typename T, int N, int CB>
+// Store one x-pencil (j, k) of cell c to global y, zeroing padding / constrained nodes.  In a
+// fused CG step each stored value is also paired with p (acc += p y over real copies).
+template <typename S, typename T, int N, int CB, typename Acc>
 __device__ __forceinline__ void store_xpencil(const ApplyArgs<S, T, N>& a, long long t, int lane0, int c, int j, int k,
-                                              const T* out) {
+                                              const T* out, Acc& acc, const S* pv) {
   constexpr int N2 = N * N, N3 = N2 * N;
   int cx, cy, cz;
   cell_of(a.g, t, lane0 + c, cx, cy, cz);
@@ -85,7 +123,29 @@ __device__ __forceinline__ void store_xpencil(const ApplyArgs<S, T, N>& a, long 
   for (int i = 0; i < N; ++i) {
     S v = valid ? to_storage<S, T>(out[i]) : S(0);
     if (valid && a.g.bc && on_cube_boundary<N>(a.g, cx, cy, cz, i, j, k)) v = S(0);
-    a.y[base + (long long)(i + N * j + N2 * k) * BL] = v;
+    const long long e = base + (long long)(i + N * j + N2 * k) * BL;
+    a.y[e] = v;
+    if constexpr (Acc::active) {
+      if (a.cg.st != nullptr && valid) acc.add(pv[i], v);
+    }
+  }
+}
+
+// End of a fused CG step: CTA sum of <p, y>, then the last CTA forms alpha = <r,r> / <p, y>
+// (breakdown when <p, y> is not positive and finite).  park: blockDim.x doubles of free smem.
+template <typename S, typename T, int N>
+__device__ __forceinline__ void apply_cg_finish(const ApplyArgs<S, T, N>& a, double v, double* park) {
+  const double part = block_park_sum(v, park);
+  double tot;
+  if (grid_total_last(part, a.cg.partials, a.cg.counter, park, &tot)) {
+    CgState* st = a.cg.st;
+    st->pq = tot;
+    if (!(tot > 0.0) || !isfinite(tot)) {
+      st->flag = 2;
+      st->alpha = 0.0;
+    } else {
+      st->alpha = st->rr / tot;
+    }
   }
 }
 
@@ -101,6 +161,7 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_cartesian(ApplyArgs<S,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* buf0 = reinterpret_cast<T*>(smem_raw);
   T* buf1 = buf0 + N3 * CB;
+  if (a.cg.st != nullptr && a.cg.st->flag != 0) return; // fused CG step after convergence: no work
   const long long t = blockIdx.x / GPT;
   const int lane0 = (blockIdx.x % GPT) * CB;
   load_tile<S, T, N, CB, NT>(a, t, lane0, buf0);
@@ -165,12 +226,22 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_cartesian(ApplyArgs<S,
     for (int q = 0; q < N; ++q) buf0[(pa + N * pb + N2 * q) * CB + c] = o[q];
   }
   __syncthreads();
-  { // write out as x-pencils (j=pa, k=pb) so the Dirichlet mask indexes match
+  PairAcc<S> acc;
+  { // write out as x-pencils (j=pa, k=pb) so the Dirichlet mask indexes match; a fused CG step
+    // pairs each stored value with p (this CTA wrote p during the load, before the barriers)
+    S pv[N];
+    if (a.cg.st != nullptr) {
+      const S* __restrict__ pg = (a.cg.update_p ? a.cg.p : a.x) + t * (long long)N3 * BL + lane0 + c;
+#pragma unroll
+      for (int i = 0; i < N; ++i) pv[i] = pg[(long long)(i + N * pa + N2 * pb) * BL];
+    }
     T o[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) o[i] = buf0[(i + N * pa + N2 * pb) * CB + c];
-    store_xpencil<S, T, N, CB>(a, t, lane0, c, pa, pb, o);
+    store_xpencil<S, T, N, CB>(a, t, lane0, c, pa, pb, o, acc, pv);
   }
+  // buf1 was last read before the barrier ahead of the output phase
+  if (a.cg.st != nullptr) apply_cg_finish(a, acc.value(), reinterpret_cast<double*>(buf1));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -187,6 +258,7 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T
   T* buf0 = reinterpret_cast<T*>(smem_raw);
   T* buf1 = buf0 + N3 * CB;
   T* buf2 = buf1 + N3 * CB;
+  if (a.cg.st != nullptr && a.cg.st->flag != 0) return; // fused CG step after convergence: no work
   const long long t = blockIdx.x / GPT;
   const int lane0 = (blockIdx.x % GPT) * CB;
   load_tile<S, T, N, CB, NT>(a, t, lane0, buf0);
@@ -246,7 +318,11 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T
   __syncthreads();
   // Per Gauss point (pa, pb, q): reference gradient (x and y parts from buf1), metric, and the
   // fluxes v = G grad u; v1 -> buf0, v2 -> buf2, v3 stays in registers (Helmholtz: m u too).
+  // A fused CG step also sums grad u . v (+ m u^2): p_K^T A_K p_K of this pencil's points,
+  // equal to the pairing of p with the split product written below (Lemma 1).
   const long long gbase = (t * NC * (long long)N3) * BL + lane0 + c;
+  const bool fuse = a.cg.st != nullptr;
+  T pap = T(0);
 #pragma unroll
   for (int q = 0; q < N; ++q) {
     const int l = pa + N * pb + N2 * q;
@@ -301,9 +377,17 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T
       g3 = w * a.G[3]; g4 = w * a.G[4]; g5 = w * a.G[5];
       if (HELM) m = w * a.mdet;
     }
-    buf0[l * CB + c] = finish(fma(g0, d1, fma(g1, d2, g2 * d3[q])));
-    buf2[l * CB + c] = finish(fma(g1, d1, fma(g3, d2, g4 * d3[q])));
-    d3[q] = finish(fma(g2, d1, fma(g4, d2, g5 * d3[q])));
+    const T d3q = d3[q];
+    const T v1 = finish(fma(g0, d1, fma(g1, d2, g2 * d3q)));
+    const T v2 = finish(fma(g1, d1, fma(g3, d2, g4 * d3q)));
+    const T v3 = finish(fma(g2, d1, fma(g4, d2, g5 * d3q)));
+    buf0[l * CB + c] = v1;
+    buf2[l * CB + c] = v2;
+    d3[q] = v3;
+    if (fuse) { // <p, A_K p> as the quadrature form: sum over points of grad u . G grad u (+ m u^2)
+      pap = fma(d1, v1, fma(d2, v2, fma(d3q, v3, pap)));
+      if (HELM) pap = fma(U[q], m * U[q], pap);
+    }
     if (HELM) U[q] = m * U[q];
   }
   __syncthreads();
@@ -343,6 +427,7 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T
     }
   }
   __syncthreads();
+  NoAcc acc;
   { // S^T along x, pencil (j=pa, k=pb) -> global
     T in[N], o[N];
 #pragma unroll
@@ -354,8 +439,10 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T
       for (int q = 0; q < N; ++q) s = fma(Sm[q * N + i], in[q], s);
       o[i] = finish(s);
     }
-    store_xpencil<S, T, N, CB>(a, t, lane0, c, pa, pb, o);
+    store_xpencil<S, T, N, CB>(a, t, lane0, c, pa, pb, o, acc, static_cast<const S*>(nullptr));
   }
+  // buf0 was last read before the barrier ahead of the S^T sweep along y
+  if (fuse) apply_cg_finish(a, to_double(finish(pap)), reinterpret_cast<double*>(buf0));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -570,10 +657,12 @@ static void fill_args(const mf_operator* op, ApplyArgs<S, T, N>& a) {
 }
 
 template <typename S, typename T, int N, int V>
-static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, const void* geom, cudaStream_t s) {
+static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, const void* geom, const CgFuse<S>& cg,
+                               cudaStream_t s) {
   using C = Cfg<T, N, V>;
   ApplyArgs<S, T, N> a;
   fill_args<S, T, N>(op, a);
+  a.cg = cg;
   a.x = static_cast<const S*>(x);
   a.y = static_cast<S*>(y);
   a.geom = static_cast<const T*>(geom);
@@ -589,7 +678,9 @@ static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, co
   else
     k = helm ? apply_general<S, T, N, C::CB, C::MINB, true, true> : apply_general<S, T, N, C::CB, C::MINB, true, false>;
   if (smem > 227 * 1024) return set_error(MF_ERR_UNSUPPORTED, "apply variant needs %zu bytes of shared memory", smem);
-  if (smem > 48 * 1024) {
+  // the kernels also hold a few bytes of static shared memory (the fused CG epilogue), and
+  // static + dynamic above 48 KB needs the opt-in
+  if (smem + 256 > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(apply)");
   }
@@ -599,20 +690,38 @@ static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, co
 
 template <typename S, typename T, int N>
 static mf_status apply_split_t(const mf_operator* op, int variant, const void* x, void* y, const void* geom,
-                               cudaStream_t s) {
-  if (variant == 1) return apply_split_v<S, T, N, 1>(op, x, y, geom, s);
-  if (variant == 2) return apply_split_v<S, T, N, 2>(op, x, y, geom, s);
-  return apply_split_v<S, T, N, 0>(op, x, y, geom, s);
+                               const CgFuse<S>& cg, cudaStream_t s) {
+  if (variant == 1) return apply_split_v<S, T, N, 1>(op, x, y, geom, cg, s);
+  if (variant == 2) return apply_split_v<S, T, N, 2>(op, x, y, geom, cg, s);
+  return apply_split_v<S, T, N, 0>(op, x, y, geom, cg, s);
 }
 
 // vk: VK_F64 (double storage, native FP64 compute), VK_DD (double storage, double-float
 // compute), VK_F32 (float storage and compute).
 template <int N>
 mf_status apply_split_n(const mf_operator* op, int vk, const void* x, void* y, cudaStream_t s) {
-  const int v = op->variant[vk];
-  if (vk == VK_F64) return apply_split_t<double, double, N>(op, v, x, y, op->v64.geom, s);
-  if (vk == VK_DD) return apply_split_t<double, dd, N>(op, v, x, y, op->v64.geom, s);
-  return apply_split_t<float, float, N>(op, v, x, y, op->v32.geom, s);
+  const int v = op->variant[vk == VK_DDS ? VK_DD : vk];
+  if (vk == VK_F64) return apply_split_t<double, double, N>(op, v, x, y, op->v64.geom, CgFuse<double>{}, s);
+  if (vk == VK_DD) return apply_split_t<double, dd, N>(op, v, x, y, op->v64.geom, CgFuse<double>{}, s);
+  if (vk == VK_DDS) return apply_split_t<dd, dd, N>(op, v, x, y, op->v64.geom, CgFuse<dd>{}, s);
+  return apply_split_t<float, float, N>(op, v, x, y, op->v32.geom, CgFuse<float>{}, s);
+}
+
+template <int N>
+mf_status apply_cg_n(const mf_operator* op, int vk, void* p, const void* r, void* y, CgState* st, double* partials,
+                     unsigned* counter, int update_p, cudaStream_t s) {
+  const int v = op->variant[vk == VK_DDS ? VK_DD : vk];
+  if (vk == VK_F32) {
+    const CgFuse<float> cg{static_cast<float*>(p), static_cast<const float*>(r), st, partials, counter, update_p};
+    return apply_split_t<float, float, N>(op, v, update_p ? nullptr : p, y, op->v32.geom, cg, s);
+  }
+  if (vk == VK_DDS) {
+    const CgFuse<dd> cg{static_cast<dd*>(p), static_cast<const dd*>(r), st, partials, counter, update_p};
+    return apply_split_t<dd, dd, N>(op, v, update_p ? nullptr : p, y, op->v64.geom, cg, s);
+  }
+  const CgFuse<double> cg{static_cast<double*>(p), static_cast<const double*>(r), st, partials, counter, update_p};
+  if (vk == VK_F64) return apply_split_t<double, double, N>(op, v, update_p ? nullptr : p, y, op->v64.geom, cg, s);
+  return apply_split_t<double, dd, N>(op, v, update_p ? nullptr : p, y, op->v64.geom, cg, s);
 }
 
 template <int N>
@@ -665,6 +774,8 @@ mf_status layout_n(const mf_operator* op, int elem, int mode, const void* in, vo
 #define MF_INSTANTIATE_DEGREE(NN)                                                                        \
   namespace mf {                                                                                        \
   template mf_status apply_split_n<NN>(const mf_operator*, int, const void*, void*, cudaStream_t);      \
+  template mf_status apply_cg_n<NN>(const mf_operator*, int, void*, const void*, void*, CgState*, double*, \
+                                    unsigned*, int, cudaStream_t);                                      \
   template mf_status dss_n<NN>(const mf_operator*, int, void*, cudaStream_t);                           \
   template mf_status geometry_n<NN>(const mf_operator*, int, void*, cudaStream_t);                      \
   template mf_status layout_n<NN>(const mf_operator*, int, int, const void*, void*, cudaStream_t);      \

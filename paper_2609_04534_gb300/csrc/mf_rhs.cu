@@ -331,6 +331,10 @@ mf_status tables(const mf_operator* op, const RhsArgs<T, N>& a, dd* tab, cudaStr
   return cuda_check(cudaGetLastError(), "manufactured tables launch");
 }
 
+// static shared memory of the RHS / error kernels (the 1024-double reduction park and a
+// flag): static + dynamic above 48 KB needs the opt-in
+constexpr size_t STATIC_SMEM_ALLOWANCE = 1024 * sizeof(double) + 256;
+
 template <typename T, int N>
 mf_status rhs_t(const mf_operator* op, double freq, void* b, char* scratch, cudaStream_t s) {
   RhsArgs<T, N> a;
@@ -340,7 +344,7 @@ mf_status rhs_t(const mf_operator* op, double freq, void* b, char* scratch, cuda
   if ((st = tables<T, N>(op, a, tab, s))) return st;
   a.b = static_cast<T*>(b);
   const size_t smem = sizeof(dd) * N * N * N * RCfg<N>::CB;
-  if (smem > 48 * 1024) {
+  if (smem + STATIC_SMEM_ALLOWANCE > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(rhs_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(e, "rhs attribute");
   }
@@ -363,7 +367,7 @@ mf_status err_t(const mf_operator* op, double freq, const void* u, double* out, 
   if (blocks > 65536) return set_error(MF_ERR_UNSUPPORTED, "manufactured error: mesh too large (%lld CTAs)", blocks);
   if ((st = cuda_check(cudaMemsetAsync(&a.red->counter, 0, sizeof(unsigned), s), "err memset"))) return st;
   const size_t smem = sizeof(dd) * N * N * N * RCfg<N>::CB;
-  if (smem > 48 * 1024) {
+  if (smem + STATIC_SMEM_ALLOWANCE > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(err_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(e, "err attribute");
   }

@@ -7,19 +7,6 @@
 
 namespace mf {
 
-// Device-resident CG scalars.
-struct CgState {
-  double rr;    // <r, r> (assembled)
-  double pq;    // <p, A p>
-  double alpha, beta;
-  double bnorm; // ||b|| of this CG
-  double tol2;  // (rtol * ||b||)^2
-  int it;       // iterations done
-  int flag;     // 0 running, 1 converged, 2 breakdown, 3 maxit
-  int maxit;
-  int pad;
-};
-
 struct RedScratch;
 
 // Workspace layout of a solve (all device pointers inside the caller's workspace).
@@ -28,9 +15,12 @@ struct SolveWs {
   RedScratch *sc1, *sc2, *sc3;
   double* hist;
   double* scal;          // [0] inner <r,r>, [1] outer ||b||^2, [2] outer ||r||^2
+  double* apart;         // split-dual iteration: per-CTA partials of <p, A p> in the apply
+  unsigned* acount;      //   and their arrival counter
   void *r, *p, *q;       // CG vectors of the (inner) element type
   void *r64, *q64, *b64; // mixed: FP64 outer residual, A x, masked b
   void* d32;             // mixed: inner solution
+  void* xdd;             // FP64 solver with double-float vectors: the iterate
 };
 
 // Host copy of the scalars each phase reports (pinned memory when used asynchronously).
@@ -52,6 +42,8 @@ struct SolverEngine {
   void* x_in = nullptr;
   double rtol = 0.0, inner_rtol = 1e-3;
   int maxit = 0, chunk = 20, max_outer = 60;
+  int form = MF_CG_SPLIT_DUAL; // MF_CG_SPLIT_DUAL, MF_CG_ASSEMBLED or MF_CG_SPLIT_DUAL_FUSED
+  int vt = 8;                  // element type of the CG vectors (8, 4 or ELEM_DD), set at start
   HostMirror* hm = nullptr;
   int phase = 0, total_it = 0, outer = 0;
   double bn = 0.0, rel = 0.0;

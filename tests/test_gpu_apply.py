@@ -142,6 +142,23 @@ def test_dot_products(oracle, prec):
     d.close()
 
 
+@pytest.mark.parametrize("scale", [1e-200, 1e-25, 1.0, 1e25, 1e200])
+def test_dot_keeps_the_double_range(scale):
+    """The FP64 dot accumulates on the FP32 pipe for operands within [2^-60, 2^60] and in FP64
+    outside; over the whole double range (both paths in one dot: half of b sits 30 decades
+    lower) it stays within 1e-13 of the exactly rounded sum."""
+    import math
+    dims, k = (5, 4, 3), 2
+    d = DevOp(*dims, k, "cart", mf.MF_LAPLACE, 1.0, mf.MF_FP64, 0)
+    a = inputs.random_unique(*dims, k, 31) * scale
+    b = inputs.random_unique(*dims, k, 32)
+    b[::2] *= 1e-30
+    got = d.dot(d.native_from_unique(a), d.native_from_unique(b))
+    ref = math.fsum(a * b)
+    assert abs(got - ref) <= 1e-13 * np.abs(a * b).sum(), (got, ref)
+    d.close()
+
+
 @pytest.mark.parametrize("k", [3, 4])
 @pytest.mark.parametrize("prec", [mf.MF_FP64, mf.MF_FP32, mf.MF_FP64_DFMA])
 def test_full_size_curved_64cubed_sampled(oracle, k, prec):

@@ -12,7 +12,7 @@ from tests._gpu import DevOp, oracle_op, rel_max
 pytestmark = pytest.mark.gpu
 
 
-def solve(d, b, rtol, maxit, mixed, hist_cap=0):
+def solve(d, b, rtol, maxit, mixed, hist_cap=0, cg_form=0):
     x = torch.zeros(d.n_native, dtype=d.dtype, device="cuda")
     ws = torch.empty(mf.mf_cg_workspace_bytes(d.op, mixed), dtype=torch.uint8, device="cuda")
     hist = np.zeros(max(hist_cap, 1))
@@ -20,16 +20,17 @@ def solve(d, b, rtol, maxit, mixed, hist_cap=0):
         mf.mf_cg_record_history(hist.ctypes.data, hist_cap)
     try:
         st = mf.mf_cg_solve(d.op, b.data_ptr(), x.data_ptr(), rtol, maxit, mixed, ws.data_ptr(), ws.numel(),
-                            allow_not_converged=True)
+                            allow_not_converged=True, cg_form=cg_form)
     finally:
         mf.mf_cg_record_history(None, 0)
     return x, st, hist
 
 
-def test_config1_50_cg_iterations(oracle):
+@pytest.mark.parametrize("cg_form", [mf.MF_CG_SPLIT_DUAL, mf.MF_CG_ASSEMBLED])
+def test_config1_50_cg_iterations(oracle, cg_form):
     """Q2 Laplace 8^3, Dirichlet, b = A x_true with x_true the seed-0 random vector masked at
     the boundary; 50 CG iterations from 0.  Per-iteration relative residuals and x_50 agree
-    with the oracle within 1e-10."""
+    with the oracle within 1e-10, for both forms of the iteration."""
     N, k = 8, 2
     d = DevOp(N, N, N, k, "cart", mf.MF_LAPLACE, 1.0, mf.MF_FP64, 1)
     o = oracle_op(oracle, N, N, N, k, "cart", 0.0, 1)
@@ -38,7 +39,7 @@ def test_config1_50_cg_iterations(oracle):
     b_ref = o.apply(xt)
     x_ref, h_ref = o.cg(b_ref, maxit=50, rtol=0.0)
     b = d.apply(d.native_from_unique(xt))
-    x, st, h = solve(d, b, 0.0, 50, 0, hist_cap=64)
+    x, st, h = solve(d, b, 0.0, 50, 0, hist_cap=64, cg_form=cg_form)
     assert st["iterations"] == 50
     np.testing.assert_allclose(h[:51], h_ref, rtol=1e-10, atol=0)
     assert rel_max(d.unique_from_native(x), x_ref) <= 1e-10
@@ -96,4 +97,74 @@ def test_breakdown_is_reported():
     with pytest.raises(mf.MfError) as e:
         solve(d, b, 1e-10, 10, 0)
     assert e.value.code == mf.MF_ERR_BREAKDOWN
+    d.close()
+
+
+def consistent(d, x):
+    """All copies of every node bitwise equal (and padding zero): x == G G^T-free round trip."""
+    u = torch.empty(d.n_unique, dtype=d.dtype, device="cuda")
+    mf.mf_gather_unique(d.op, x.data_ptr(), u.data_ptr())
+    xs = torch.empty_like(x)
+    mf.mf_scatter_unique(d.op, u.data_ptr(), xs.data_ptr())
+    torch.cuda.synchronize()
+    return bool(torch.equal(xs, x))
+
+
+@pytest.mark.parametrize("dims,k,geom,kind,prec,bc", [
+    ((7, 6, 5), 3, "curved", mf.MF_LAPLACE, mf.MF_FP64, 1),
+    ((9, 5, 3), 2, "shear", mf.MF_HELMHOLTZ, mf.MF_FP64, 0),
+    ((5, 9, 4), 4, "cart", mf.MF_LAPLACE, mf.MF_FP64, 1),
+    ((6, 7, 5), 5, "curved", mf.MF_HELMHOLTZ, mf.MF_FP64_DFMA, 0),
+    ((4, 4, 2), 1, "cart", mf.MF_HELMHOLTZ, mf.MF_FP64, 0),
+    ((5, 3, 7), 8, "stretch", mf.MF_LAPLACE, mf.MF_FP64, 1),
+    ((7, 6, 5), 3, "curved", mf.MF_LAPLACE, mf.MF_FP32, 1),
+    ((9, 5, 3), 6, "cart", mf.MF_HELMHOLTZ, mf.MF_FP32, 0),
+])
+def test_split_dual_matches_assembled_iteration(oracle, dims, k, geom, kind, prec, bc):
+    """The split-dual iteration (fused apply with <p, A_K p> over all copies, duplicate
+    summation folded into the update of r) against the assembled iteration (apply, duplicate
+    summation, vector kernels), on ragged meshes whose cells cross tile boundaries in every
+    direction: the residual histories agree to rounding, the iterates stay consistent
+    bitwise, and the split-dual solution satisfies the oracle's equations."""
+    nx, ny, nz = dims
+    d = DevOp(nx, ny, nz, k, geom, kind, 1.0, prec, bc)
+    bu = inputs.random_unique(nx, ny, nz, k, 11)
+    b = d.native_from_unique(bu)
+    its = 25
+    xa, sta, ha = solve(d, b, 0.0, its, 0, hist_cap=its + 2, cg_form=mf.MF_CG_ASSEMBLED)
+    assert sta["iterations"] == its and consistent(d, xa)
+    tol = 1e-3 if prec == mf.MF_FP32 else 1e-9
+    for form in (mf.MF_CG_SPLIT_DUAL, mf.MF_CG_SPLIT_DUAL_FUSED):
+        xs, sts, hs = solve(d, b, 0.0, its, 0, hist_cap=its + 2, cg_form=form)
+        assert sts["iterations"] == its
+        np.testing.assert_allclose(hs[:its + 1], ha[:its + 1], rtol=tol, atol=0)
+        assert consistent(d, xs)
+        assert rel_max(d.unique_from_native(xs), d.unique_from_native(xa)) <= tol
+    if prec != mf.MF_FP32:
+        o = oracle_op(oracle, nx, ny, nz, k, geom, 1.0 if kind == mf.MF_HELMHOLTZ else 0.0, bc)
+        x1, st1, _ = solve(d, b, 1e-11, 20000, 0)
+        assert st1["code"] == mf.MF_OK
+        bm = np.where(o.boundary_mask(), 0.0, bu) if bc else bu
+        res = np.linalg.norm(bm - o.apply(d.unique_from_native(x1))) / np.linalg.norm(bm)
+        assert res <= 2e-11, res
+    d.close()
+
+
+@pytest.mark.parametrize("scale", [1e-200, 3e-30, 7e25, 1e200])
+def test_fp64_cg_across_the_double_range(scale):
+    """The FP64 solver's double-float iteration scales b by a power of two near 1/||b|| (so its
+    float exponents stay in range) and scales x back: right-hand sides anywhere in the double
+    range give the same relative residual history and the correspondingly scaled solution."""
+    N, k = 5, 3
+    d = DevOp(N, N, N, k, "curved", mf.MF_LAPLACE, 1.0, mf.MF_FP64, 1)
+    bu = inputs.random_unique(N, N, N, k, 13)
+    x0, st0, h0 = solve(d, d.native_from_unique(bu), 1e-10, 5000, 0, hist_cap=4000)
+    x1, st1, h1 = solve(d, d.native_from_unique(bu * scale), 1e-10, 5000, 0, hist_cap=4000)
+    assert st0["code"] == st1["code"] == mf.MF_OK
+    assert abs(st0["iterations"] - st1["iterations"]) <= 2
+    m = min(st0["iterations"], st1["iterations"]) + 1
+    np.testing.assert_allclose(h1[:m], h0[:m], rtol=1e-8, atol=0)
+    u0, u1 = d.unique_from_native(x0), d.unique_from_native(x1)
+    assert np.isfinite(u1).all()
+    assert rel_max(u1 / scale, u0) <= 1e-8
     d.close()

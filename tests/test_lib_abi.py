@@ -81,6 +81,14 @@ def test_operator_argument_validation_and_info(L):
         mf.mf_operator_setup(op, 256, 1024)
     assert e.value.code == mf.MF_ERR_OOM
     assert mf.mf_cg_workspace_bytes(op, 1) > mf.mf_cg_workspace_bytes(op, 0) > 0
+    # solver entry points refuse before touching the GPU: bad CG form, operator not set up
+    with pytest.raises(mf.MfError) as e:
+        mf.mf_cg_solve(op, 16, 32, 1e-10, 10, 0, 256, 1 << 30, cg_form=7)
+    assert e.value.code == mf.MF_ERR_ARG
+    for its, form in [(10, 0), (0, 1), (1001, 1), (5, 4)]:
+        with pytest.raises(mf.MfError) as e:
+            mf.mf_cg_profile(op, 16, 32, its, form, 256, 1 << 30)
+        assert e.value.code == mf.MF_ERR_ARG
     mf.mf_operator_destroy(op)
     mf.mf_mesh_destroy(mc)
     mf.mf_mesh_destroy(m)
