@@ -88,6 +88,9 @@ struct ApplyArgs {
   const float* gtab;
   float amp, cm, h[3];
   CgFuse<S> cg; // cg.st == nullptr: plain apply
+  // L2 prefetch distance in tiles (about one wave of resident CTAs ahead; 0 = off): the first
+  // CTA of tile t prefetches the input and geometry of tile t + pf_tiles
+  int pf_tiles;
 };
 
 // Host-side double tables (any n <= MAXN).

@@ -4,6 +4,8 @@
 //
 // Included once per degree by mf_apply_k<k>.cu so the eight degrees compile in parallel.
 #pragma once
+#include <mutex>
+
 #include "mf_dd.cuh"
 #include "mf_internal.h"
 #include "mf_reduce.cuh"
@@ -70,6 +72,35 @@ struct NoAcc {
 __device__ __forceinline__ double to_double(double v) { return v; }
 __device__ __forceinline__ double to_double(float v) { return (double)v; }
 __device__ __forceinline__ double to_double(dd v) { return dd_to_double(v); }
+
+// Bulk prefetch of [p, p + bytes) into L2 (16-byte aligned, size a multiple of 16), split into
+// 16 KB requests over the lanes of the calling warp.
+__device__ __forceinline__ void prefetch_l2_warp(const void* p, unsigned long long bytes) {
+  const unsigned long long chunk = 16384;
+  for (unsigned long long o = (unsigned long long)(threadIdx.x & 31) * chunk; o < bytes; o += 32 * chunk) {
+    const unsigned long long n = bytes - o < chunk ? bytes - o : chunk;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"((const char*)p + o), "r"((unsigned)n) : "memory");
+  }
+}
+
+// Warp 0 of the first CTA of tile t starts moving tile t + pf_tiles (its input vector rows
+// and, for streamed geometry, its metric) from HBM into L2, so that the CTAs of the next wave
+// find their loads in L2.  Tiles are contiguous chunks of both arrays.
+template <typename S, typename T, int N, int NC>
+__device__ __forceinline__ void prefetch_next_wave(const ApplyArgs<S, T, N>& a, long long t, int lane0) {
+  constexpr int N3 = N * N * N;
+  if (a.pf_tiles <= 0 || lane0 != 0 || threadIdx.x >= 32) return;
+  const long long tn = t + a.pf_tiles;
+  if (tn >= a.g.ntiles) return;
+  const S* xin = (a.cg.st != nullptr && a.cg.update_p) ? a.cg.p : a.x;
+  const unsigned long long xb = (unsigned long long)N3 * BL * sizeof(S);
+  prefetch_l2_warp(xin + tn * (long long)N3 * BL, xb);
+  if (a.cg.st != nullptr && a.cg.update_p) prefetch_l2_warp(a.cg.r + tn * (long long)N3 * BL, xb);
+  if (NC > 0 && a.geom != nullptr) {
+    const unsigned long long gb = (unsigned long long)NC * N3 * BL * sizeof(T);
+    prefetch_l2_warp(a.geom + tn * (long long)NC * N3 * BL, gb);
+  }
+}
 
 // Load the CB cells [lane0, lane0+CB) of tile t into smem as buf[l*CB + c] (cell fastest),
 // zeroing padding cells and, for Dirichlet, the constrained nodes (the P of P A P).  In a
@@ -164,6 +195,7 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_cartesian(ApplyArgs<S,
   if (a.cg.st != nullptr && a.cg.st->flag != 0) return; // fused CG step after convergence: no work
   const long long t = blockIdx.x / GPT;
   const int lane0 = (blockIdx.x % GPT) * CB;
+  prefetch_next_wave<S, T, N, 0>(a, t, lane0);
   load_tile<S, T, N, CB, NT>(a, t, lane0, buf0);
   __syncthreads();
   const int c = threadIdx.x % CB, p = threadIdx.x / CB, pa = p % N, pb = p / N;
@@ -261,6 +293,7 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T
   if (a.cg.st != nullptr && a.cg.st->flag != 0) return; // fused CG step after convergence: no work
   const long long t = blockIdx.x / GPT;
   const int lane0 = (blockIdx.x % GPT) * CB;
+  prefetch_next_wave<S, T, N, (CURVED && sizeof(T) != 4) ? NC : 0>(a, t, lane0);
   load_tile<S, T, N, CB, NT>(a, t, lane0, buf0);
   __syncthreads();
   const int c = threadIdx.x % CB, p = threadIdx.x / CB, pa = p % N, pb = p / N;
@@ -323,6 +356,22 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T
   const long long gbase = (t * NC * (long long)N3) * BL + lane0 + c;
   const bool fuse = a.cg.st != nullptr;
   T pap = T(0);
+  // FP32 curved: sin / cos of pi xh at this thread's x and y points and at every z point of
+  // the cell's layer, loaded before the point loop
+  float sx = 0.f, cxv = 0.f, sy = 0.f, cyv = 0.f, szq[N], czq[N];
+  if constexpr (CURVED && sizeof(T) == 4) {
+    int ccx, ccy, ccz;
+    cell_of(a.g, t, lane0 + c, ccx, ccy, ccz);
+    ccx = min(ccx, a.g.nx - 1);
+    ccy = min(ccy, a.g.ny - 1);
+    ccz = min(ccz, a.g.nz - 1);
+    const float* tx = a.gtab + 2 * (ccx * N + pa);
+    const float* ty = a.gtab + 2 * ((a.g.nx + ccy) * N + pb);
+    const float* tz = a.gtab + 2 * ((a.g.nx + a.g.ny + ccz) * N);
+    sx = tx[0]; cxv = tx[1]; sy = ty[0]; cyv = ty[1];
+#pragma unroll
+    for (int q = 0; q < N; ++q) { szq[q] = tz[2 * q]; czq[q] = tz[2 * q + 1]; }
+  }
 #pragma unroll
   for (int q = 0; q < N; ++q) {
     const int l = pa + N * pb + N2 * q;
@@ -338,15 +387,7 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T
       // x = xh + amp s(xh) (1,1,1): J = (I + u v^T) D with u = amp (1,1,1), v = grad s,
       // D = diag(h).  Sherman-Morrison: J^-1 = D^-1 (I - u v^T / beta), beta = 1 + v.u, and
       // J^-1 J^-T = D^-1 (I - (u v^T + v u^T)/beta + |v|^2 u u^T / beta^2) D^-1.
-      int ccx, ccy, ccz;
-      cell_of(a.g, t, lane0 + c, ccx, ccy, ccz);
-      ccx = min(ccx, a.g.nx - 1);
-      ccy = min(ccy, a.g.ny - 1);
-      ccz = min(ccz, a.g.nz - 1);
-      const float* tx = a.gtab + 2 * (ccx * N + pa);
-      const float* ty = a.gtab + 2 * ((a.g.nx + ccy) * N + pb);
-      const float* tz = a.gtab + 2 * ((a.g.nx + a.g.ny + ccz) * N + q);
-      const float sx = tx[0], cxv = tx[1], sy = ty[0], cyv = ty[1], sz = tz[0], czv = tz[1];
+      const float sz = szq[q], czv = czq[q];
       const float pi = 3.14159265358979f;
       const float v1 = pi * cxv * sy * sz, v2 = pi * sx * cyv * sz, v3 = pi * sx * sy * czv;
       const float beta = fmaf(a.amp, v1 + v2 + v3, 1.0f);
@@ -656,6 +697,35 @@ static void fill_args(const mf_operator* op, ApplyArgs<S, T, N>& a) {
   }
 }
 
+// L2 prefetch distance of an apply launch: MF_PREFETCH_WAVES waves of resident CTAs, in
+// tiles (gpt CTAs per tile).  Occupancy and SM count are looked up once per kernel.
+#ifndef MF_PREFETCH_WAVES
+#define MF_PREFETCH_WAVES 1
+#endif
+static int prefetch_distance_tiles(const void* kernel, int threads, size_t smem, int gpt) {
+  if (MF_PREFETCH_WAVES <= 0) return 0;
+  struct Entry {
+    const void* k;
+    size_t smem;
+    int dev, tiles;
+  };
+  static Entry cache[64];
+  static int ncache = 0;
+  static std::mutex mu;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  for (int i = 0; i < ncache; ++i)
+    if (cache[i].k == kernel && cache[i].smem == smem && cache[i].dev == dev) return cache[i].tiles;
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  cudaGetLastError(); // a failed query only turns the prefetch off
+  const int tiles = (sms > 0 && per_sm > 0) ? MF_PREFETCH_WAVES * ((sms * per_sm + gpt - 1) / gpt) : 0;
+  if (ncache < 64) cache[ncache++] = Entry{kernel, smem, dev, tiles};
+  return tiles;
+}
+
 template <typename S, typename T, int N, int V>
 static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, const void* geom, const CgFuse<S>& cg,
                                cudaStream_t s) {
@@ -684,6 +754,7 @@ static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, co
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(apply)");
   }
+  a.pf_tiles = prefetch_distance_tiles((const void*)k, C::NT, smem, BL / C::CB);
   k<<<(unsigned)blocks, C::NT, smem, s>>>(a);
   return cuda_check(cudaGetLastError(), "apply launch");
 }
