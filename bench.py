@@ -580,9 +580,10 @@ def main():
             "helmholtz_sweep_50M": sweep,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            # mask, zero x, copy r, copy p, <r,r>, state; then 3 kernels per iteration in graph
-            # chunks of 20 iterations (a partial last chunk still launches its kernels)
-            "gpu_launches": 6 + 3 * 20 * ((its + 19) // 20),
+            # mask, max|b|, zero x, scale b, copy p, <r,r>, state; then 4 kernels per iteration
+            # (apply, alpha, update, p) in graph chunks of 20 iterations (a partial last chunk
+            # still launches its kernels); the final conversion of x
+            "gpu_launches": 7 + 4 * 20 * ((its + 19) // 20) + 1,
             "clocks": clk.summary(),
             "peaks": pk,
         }

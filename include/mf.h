@@ -211,11 +211,11 @@ mf_status mf_cg_solve(const mf_operator* op, const void* b_dev, void* x_dev, dou
  *     A p split (no duplicate summation) and forms <p, A p> -- the pairing of the consistent p
  *     with the split product over all copies (Lemma 1) -- as the sum over quadrature points
  *     of grad u . G grad u; the duplicate summation is folded into the update of x and r;
- *     then p = r + beta p.  Three kernels per iteration.
+ *     then p = r + beta p.  Four kernels per iteration (apply, alpha, update, direction).
  *   MF_CG_ASSEMBLED -- apply, duplicate summation, then the vector kernels on assembled
  *     vectors (five kernels per iteration).
  *   MF_CG_SPLIT_DUAL_FUSED -- MF_CG_SPLIT_DUAL with p = r + beta p formed by the apply at
- *     load (two kernels per iteration).
+ *     load (three kernels per iteration).
  * All compute the same iterates up to rounding (only <p, A p> is summed differently). */
 enum { MF_CG_DEFAULT = 0, MF_CG_SPLIT_DUAL = 1, MF_CG_ASSEMBLED = 2, MF_CG_SPLIT_DUAL_FUSED = 3 };
 typedef struct {
@@ -232,7 +232,8 @@ mf_status mf_cg_solve_ex(const mf_operator* op, const void* b_dev, void* x_dev, 
  * runs `iterations` FP64 (FP32 for an MF_FP32 operator) CG iterations from x = 0 on b, of the
  * form cg_form (MF_CG_*), launching every kernel directly (no graph) with CUDA events around
  * each kernel group on `stream`, and writes the mean durations in milliseconds:
- * ms_out[0] the apply kernel (the fused apply of the split-dual form), ms_out[1] the duplicate
+ * ms_out[0] the apply kernel (split-dual forms: the apply and the one-CTA alpha kernel after it),
+ * ms_out[1] the duplicate
  * summation (assembled form; 0 for split-dual), ms_out[2] the vector kernels, ms_out[3] the
  * whole iteration.  1 <= iterations <= 1000.  Same workspace as mf_cg_solve (mixed = 0).
  * Synchronous. */

@@ -44,8 +44,8 @@ mf_status launch_apply_split(const mf_operator* op, int elem, const void* x, voi
   MF_DISPATCH_N(op->n, apply_split_n, op, elem, x, y, s);
 }
 mf_status launch_apply_cg(const mf_operator* op, int vk, void* p, const void* r, void* y, CgState* st, double* partials,
-                          unsigned* counter, int update_p, cudaStream_t s) {
-  MF_DISPATCH_N(op->n, apply_cg_n, op, vk, p, r, y, st, partials, counter, update_p, s);
+                          int update_p, long long* nblocks, cudaStream_t s) {
+  MF_DISPATCH_N(op->n, apply_cg_n, op, vk, p, r, y, st, partials, update_p, nblocks, s);
 }
 // every launch variant puts at least 4 cells of a 32-cell tile in one CTA
 long long apply_max_blocks(const mf_operator* op) { return op->g.ntiles * (BL / 4); }

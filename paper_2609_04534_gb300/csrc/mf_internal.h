@@ -58,18 +58,17 @@ struct CgState {
 };
 
 // CG step carried by an apply launch (the split-dual iteration of Sec. 4): with st set, the
-// apply writes the split product y = A_K p per cell (no duplicate summation) and reduces
-// <p, y> over all copies -- the pairing of a consistent with a split vector, Lemma 1 -- to
-// alpha = <r, r> / <p, y> in its last CTA (partials: one double per CTA).  The input is
-// p = x; with update_p the apply instead reads r and the previous direction p and forms
-// p = r + beta p at load (written back in place).
+// apply writes the split product y = A_K p per cell (no duplicate summation) and each CTA
+// writes its part of <p, y> over all copies -- the pairing of a consistent with a split
+// vector, Lemma 1 -- to partials[blockIdx.x]; a one-CTA kernel then folds the partials and
+// forms alpha = <r, r> / <p, y>.  The input is p = x; with update_p the apply instead reads r
+// and the previous direction p and forms p = r + beta p at load (written back in place).
 template <typename S>
 struct CgFuse {
   S* p;
   const S* r;
   CgState* st;
   double* partials;
-  unsigned* counter;
   int update_p;
 };
 
@@ -141,9 +140,10 @@ mf_status cuda_check(cudaError_t e, const char* what);
 // elem: 8 or 4.  All return MF_OK or an error status.
 // apply / geometry take a ViewKind; dss / layout / reductions take the element size.
 mf_status launch_apply_split(const mf_operator* op, int vk, const void* x, void* y, cudaStream_t s);
-// CG step apply (see CgFuse): p and r in the element type of the view vk
+// CG step apply (see CgFuse): p and r in the element type of the view vk; *nblocks = CTAs
+// launched (the number of partials written)
 mf_status launch_apply_cg(const mf_operator* op, int vk, void* p, const void* r, void* y, CgState* st, double* partials,
-                          unsigned* counter, int update_p, cudaStream_t s);
+                          int update_p, long long* nblocks, cudaStream_t s);
 // upper bound of the CTA count of any apply launch of op (size of CgFuse::partials)
 long long apply_max_blocks(const mf_operator* op);
 mf_status launch_dss(const mf_operator* op, int elem, void* y, cudaStream_t s);
@@ -154,7 +154,7 @@ template <int N>
 mf_status apply_split_n(const mf_operator* op, int vk, const void* x, void* y, cudaStream_t s);
 template <int N>
 mf_status apply_cg_n(const mf_operator* op, int vk, void* p, const void* r, void* y, CgState* st, double* partials,
-                     unsigned* counter, int update_p, cudaStream_t s);
+                     int update_p, long long* nblocks, cudaStream_t s);
 template <int N>
 mf_status dss_n(const mf_operator* op, int elem, void* y, cudaStream_t s);
 template <int N>

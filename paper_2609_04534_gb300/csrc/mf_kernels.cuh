@@ -162,22 +162,18 @@ __device__ __forceinline__ void store_xpencil(const ApplyArgs<S, T, N>& a, long 
   }
 }
 
-// End of a fused CG step: CTA sum of <p, y>, then the last CTA forms alpha = <r,r> / <p, y>
-// (breakdown when <p, y> is not positive and finite).  park: blockDim.x doubles of free smem.
-template <typename S, typename T, int N>
-__device__ __forceinline__ void apply_cg_finish(const ApplyArgs<S, T, N>& a, double v, double* park) {
-  const double part = block_park_sum(v, park);
-  double tot;
-  if (grid_total_last(part, a.cg.partials, a.cg.counter, park, &tot)) {
-    CgState* st = a.cg.st;
-    st->pq = tot;
-    if (!(tot > 0.0) || !isfinite(tot)) {
-      st->flag = 2;
-      st->alpha = 0.0;
-    } else {
-      st->alpha = st->rr / tot;
-    }
-  }
+// A CTA's part of <p, A_K p> in a CG step: every thread parks its value in red[threadIdx.x]
+// before a barrier the caller provides; after it, warp 0 folds red in a fixed order and
+// writes partials[blockIdx.x] with a plain store (the next kernel of the stream reads it, so
+// no fence is needed and no thread waits for its stores to drain).
+template <int NT>
+__device__ __forceinline__ void cta_partial_after_barrier(const double* red, double* partials) {
+  if (threadIdx.x >= 32) return;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < NT; i += 32) s += red[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -272,8 +268,12 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_cartesian(ApplyArgs<S,
     for (int i = 0; i < N; ++i) o[i] = buf0[(i + N * pa + N2 * pb) * CB + c];
     store_xpencil<S, T, N, CB>(a, t, lane0, c, pa, pb, o, acc, pv);
   }
-  // buf1 was last read before the barrier ahead of the output phase
-  if (a.cg.st != nullptr) apply_cg_finish(a, acc.value(), reinterpret_cast<double*>(buf1));
+  if (a.cg.st != nullptr) {
+    __shared__ double red[NT];
+    red[threadIdx.x] = acc.value();
+    __syncthreads();
+    cta_partial_after_barrier<NT>(red, a.cg.partials);
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -482,8 +482,12 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T
     }
     store_xpencil<S, T, N, CB>(a, t, lane0, c, pa, pb, o, acc, static_cast<const S*>(nullptr));
   }
-  // buf0 was last read before the barrier ahead of the S^T sweep along y
-  if (fuse) apply_cg_finish(a, to_double(finish(pap)), reinterpret_cast<double*>(buf0));
+  if (fuse) { // after the last barrier, so that no warp waits for warp 0's fold
+    __shared__ double red[NT];
+    red[threadIdx.x] = to_double(finish(pap));
+    __syncthreads();
+    cta_partial_after_barrier<NT>(red, a.cg.partials);
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -728,7 +732,7 @@ static int prefetch_distance_tiles(const void* kernel, int threads, size_t smem,
 
 template <typename S, typename T, int N, int V>
 static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, const void* geom, const CgFuse<S>& cg,
-                               cudaStream_t s) {
+                               long long* nblocks, cudaStream_t s) {
   using C = Cfg<T, N, V>;
   ApplyArgs<S, T, N> a;
   fill_args<S, T, N>(op, a);
@@ -739,6 +743,7 @@ static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, co
   const bool helm = op->kind == MF_HELMHOLTZ;
   const size_t smem = (op->path == PATH_CARTESIAN ? 2 : 3) * sizeof(T) * N * N * N * C::CB;
   const long long blocks = op->g.ntiles * (BL / C::CB);
+  if (nblocks) *nblocks = blocks;
   if (blocks <= 0) return MF_OK;
   void (*k)(ApplyArgs<S, T, N>) = nullptr;
   if (op->path == PATH_CARTESIAN)
@@ -748,9 +753,9 @@ static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, co
   else
     k = helm ? apply_general<S, T, N, C::CB, C::MINB, true, true> : apply_general<S, T, N, C::CB, C::MINB, true, false>;
   if (smem > 227 * 1024) return set_error(MF_ERR_UNSUPPORTED, "apply variant needs %zu bytes of shared memory", smem);
-  // the kernels also hold a few bytes of static shared memory (the fused CG epilogue), and
-  // static + dynamic above 48 KB needs the opt-in
-  if (smem + 256 > 48 * 1024) {
+  // the kernels also hold static shared memory (the CG partial's park, NT doubles, and a few
+  // bytes of the compiler's), and static + dynamic above 48 KB needs the opt-in
+  if (smem + sizeof(double) * C::NT + 1024 > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(apply)");
   }
@@ -761,10 +766,10 @@ static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, co
 
 template <typename S, typename T, int N>
 static mf_status apply_split_t(const mf_operator* op, int variant, const void* x, void* y, const void* geom,
-                               const CgFuse<S>& cg, cudaStream_t s) {
-  if (variant == 1) return apply_split_v<S, T, N, 1>(op, x, y, geom, cg, s);
-  if (variant == 2) return apply_split_v<S, T, N, 2>(op, x, y, geom, cg, s);
-  return apply_split_v<S, T, N, 0>(op, x, y, geom, cg, s);
+                               const CgFuse<S>& cg, long long* nblocks, cudaStream_t s) {
+  if (variant == 1) return apply_split_v<S, T, N, 1>(op, x, y, geom, cg, nblocks, s);
+  if (variant == 2) return apply_split_v<S, T, N, 2>(op, x, y, geom, cg, nblocks, s);
+  return apply_split_v<S, T, N, 0>(op, x, y, geom, cg, nblocks, s);
 }
 
 // vk: VK_F64 (double storage, native FP64 compute), VK_DD (double storage, double-float
@@ -772,27 +777,28 @@ static mf_status apply_split_t(const mf_operator* op, int variant, const void* x
 template <int N>
 mf_status apply_split_n(const mf_operator* op, int vk, const void* x, void* y, cudaStream_t s) {
   const int v = op->variant[vk == VK_DDS ? VK_DD : vk];
-  if (vk == VK_F64) return apply_split_t<double, double, N>(op, v, x, y, op->v64.geom, CgFuse<double>{}, s);
-  if (vk == VK_DD) return apply_split_t<double, dd, N>(op, v, x, y, op->v64.geom, CgFuse<double>{}, s);
-  if (vk == VK_DDS) return apply_split_t<dd, dd, N>(op, v, x, y, op->v64.geom, CgFuse<dd>{}, s);
-  return apply_split_t<float, float, N>(op, v, x, y, op->v32.geom, CgFuse<float>{}, s);
+  if (vk == VK_F64) return apply_split_t<double, double, N>(op, v, x, y, op->v64.geom, CgFuse<double>{}, nullptr, s);
+  if (vk == VK_DD) return apply_split_t<double, dd, N>(op, v, x, y, op->v64.geom, CgFuse<double>{}, nullptr, s);
+  if (vk == VK_DDS) return apply_split_t<dd, dd, N>(op, v, x, y, op->v64.geom, CgFuse<dd>{}, nullptr, s);
+  return apply_split_t<float, float, N>(op, v, x, y, op->v32.geom, CgFuse<float>{}, nullptr, s);
 }
 
 template <int N>
 mf_status apply_cg_n(const mf_operator* op, int vk, void* p, const void* r, void* y, CgState* st, double* partials,
-                     unsigned* counter, int update_p, cudaStream_t s) {
+                     int update_p, long long* nblocks, cudaStream_t s) {
   const int v = op->variant[vk == VK_DDS ? VK_DD : vk];
+  void* x = update_p ? nullptr : p;
   if (vk == VK_F32) {
-    const CgFuse<float> cg{static_cast<float*>(p), static_cast<const float*>(r), st, partials, counter, update_p};
-    return apply_split_t<float, float, N>(op, v, update_p ? nullptr : p, y, op->v32.geom, cg, s);
+    const CgFuse<float> cg{static_cast<float*>(p), static_cast<const float*>(r), st, partials, update_p};
+    return apply_split_t<float, float, N>(op, v, x, y, op->v32.geom, cg, nblocks, s);
   }
   if (vk == VK_DDS) {
-    const CgFuse<dd> cg{static_cast<dd*>(p), static_cast<const dd*>(r), st, partials, counter, update_p};
-    return apply_split_t<dd, dd, N>(op, v, update_p ? nullptr : p, y, op->v64.geom, cg, s);
+    const CgFuse<dd> cg{static_cast<dd*>(p), static_cast<const dd*>(r), st, partials, update_p};
+    return apply_split_t<dd, dd, N>(op, v, x, y, op->v64.geom, cg, nblocks, s);
   }
-  const CgFuse<double> cg{static_cast<double*>(p), static_cast<const double*>(r), st, partials, counter, update_p};
-  if (vk == VK_F64) return apply_split_t<double, double, N>(op, v, update_p ? nullptr : p, y, op->v64.geom, cg, s);
-  return apply_split_t<double, dd, N>(op, v, update_p ? nullptr : p, y, op->v64.geom, cg, s);
+  const CgFuse<double> cg{static_cast<double*>(p), static_cast<const double*>(r), st, partials, update_p};
+  if (vk == VK_F64) return apply_split_t<double, double, N>(op, v, x, y, op->v64.geom, cg, nblocks, s);
+  return apply_split_t<double, dd, N>(op, v, x, y, op->v64.geom, cg, nblocks, s);
 }
 
 template <int N>
@@ -846,7 +852,7 @@ mf_status layout_n(const mf_operator* op, int elem, int mode, const void* in, vo
   namespace mf {                                                                                        \
   template mf_status apply_split_n<NN>(const mf_operator*, int, const void*, void*, cudaStream_t);      \
   template mf_status apply_cg_n<NN>(const mf_operator*, int, void*, const void*, void*, CgState*, double*, \
-                                    unsigned*, int, cudaStream_t);                                      \
+                                    int, long long*, cudaStream_t);                                     \
   template mf_status dss_n<NN>(const mf_operator*, int, void*, cudaStream_t);                           \
   template mf_status geometry_n<NN>(const mf_operator*, int, void*, cudaStream_t);                      \
   template mf_status layout_n<NN>(const mf_operator*, int, int, const void*, void*, cudaStream_t);      \

@@ -111,29 +111,4 @@ __device__ __forceinline__ double block_park_sum(double v, double* park) {
   return s;
 }
 
-// Grid-wide sum of one value per CTA in block-index order.  Called by every thread of every
-// CTA (it contains barriers); part is the CTA's partial (valid in thread 0).  Returns true in
-// thread 0 of the last CTA to arrive, with *total = sum of partials[0 .. gridDim.x) folded in
-// a fixed order; that CTA also resets the counter for the next launch.
-__device__ __forceinline__ bool grid_total_last(double part, double* partials, unsigned* counter, double* park,
-                                                double* total) {
-  __shared__ unsigned last_flag;
-  if (threadIdx.x == 0) {
-    partials[blockIdx.x] = part;
-    __threadfence();
-    last_flag = (atomicAdd(counter, 1u) == gridDim.x - 1) ? 1u : 0u;
-  }
-  __syncthreads();
-  if (!last_flag) return false;
-  __threadfence();
-  double s = 0.0;
-  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) s += ((volatile double*)partials)[b];
-  s = block_park_sum(s, park);
-  if (threadIdx.x == 0) {
-    *counter = 0u;
-    *total = s;
-  }
-  return threadIdx.x == 0;
-}
-
 } // namespace mf

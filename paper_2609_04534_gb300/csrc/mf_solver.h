@@ -15,8 +15,7 @@ struct SolveWs {
   RedScratch *sc1, *sc2, *sc3;
   double* hist;
   double* scal;          // [0] inner <r,r>, [1] outer ||b||^2, [2] outer ||r||^2
-  double* apart;         // split-dual iteration: per-CTA partials of <p, A p> in the apply
-  unsigned* acount;      //   and their arrival counter
+  double* apart;         // split-dual iteration: per-CTA partials of <p, A p> from the apply
   void *r, *p, *q;       // CG vectors of the (inner) element type
   void *r64, *q64, *b64; // mixed: FP64 outer residual, A x, masked b
   void* d32;             // mixed: inner solution
