@@ -333,7 +333,8 @@ def serve_run(args):
     ks = rng.integers(2, 7, n)
     geo = rng.integers(0, 2, n)
     arena = torch.empty(int(120 * 2**30), dtype=torch.uint8, device="cuda")
-    sv = mf.mf_server_create(arena.data_ptr(), arena.numel(), max_slots=64, autotune=1)
+    sv = mf.mf_server_create(arena.data_ptr(), arena.numel(), max_slots=64, autotune=1,
+                             batching=-1 if args.no_batching else 0)
     reqs = [mf.make_request(int(N), int(N), int(N), int(k), geometry=mf.MF_CURVED_SIN if g else mf.MF_AFFINE,
                             rhs=mf.MF_RHS_MANUFACTURED, rtol=1e-10, maxit=400000, mixed=1)
             for N, k, g in zip(Ns, ks, geo)]
@@ -367,6 +368,11 @@ def serve_run(args):
            "solved_gdofs_cellwise": sum(r["n_cellwise"] for r in ok) / makespan / 1e9,
            "solved_gdofs_unique": sum(r["n_unique"] for r in ok) / makespan / 1e9,
            "max_rel_residual": max(r["rel_residual"] for r in ok) if ok else None,
+           "status_counts": {str(k): int(v) for k, v in zip(*np.unique([r["status"] for r in rs], return_counts=True))},
+           "failed": [dict(N=int(Ns[i]), k=int(ks[i]), curved=int(geo[i]), status=int(rs[i]["status"]),
+                           iterations=int(rs[i]["iterations"]), outer=int(rs[i]["outer_iterations"]),
+                           rel=float(rs[i]["rel_residual"])) for i in range(n) if rs[i]["status"] != 0][:10],
+           "batching": not args.no_batching,
            "arena_peak_gb": st["arena_peak"] / 2**30, "slots": 64}
     print(json.dumps(out), flush=True)
 
@@ -387,6 +393,7 @@ def main():
     ap.add_argument("--serve", type=int, default=0, metavar="NREQ",
                     help="serving run: NREQ solve requests with Poisson arrivals (prints its own JSON line)")
     ap.add_argument("--rate", type=float, default=0.0, help="serving arrival rate (requests/s); 0 = measure capacity")
+    ap.add_argument("--no-batching", action="store_true", help="serving: every request on its own graph chunks")
     ap.add_argument("--solve-n", type=int, default=96, help="cells per axis of the --solve mesh")
     ap.add_argument("--inner-rtol", type=float, nargs="+", default=[1e-3], help="inner FP32 CG tolerances to run")
     args = ap.parse_args()

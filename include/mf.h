@@ -247,13 +247,20 @@ mf_status mf_cg_record_history(double* hist_host, int cap);
  * Continuous-batching solve server.  Requests are queued by mf_batch_submit and admitted in
  * arrival order whenever one of max_slots slots and enough of the caller's device arena are
  * free (a request that does not fit yet does not block smaller ones behind it).  An admitted
- * request keeps its geometry, vectors and CG state resident in its arena block and runs on
- * its slot's CUDA stream as graph chunks of CG iterations, so the work of all active
- * requests overlaps on the GPU; a native scheduler thread advances each request when its
- * scalars have landed and admits new ones as slots and memory free up.  Every request solves
- * the homogeneous Dirichlet problem on the unit cube with the given operator; mixed = 1 runs
- * FP32 applies inside FP64 defect correction (else FP64 CG).  The arena is the only device
- * memory used (pinned host memory holds per-slot scalars); it must outlive the server. */
+ * request keeps its geometry, vectors and CG state resident in its arena block.  Its set-up,
+ * the outer steps of defect correction and its finish run on its slot's CUDA stream; its CG
+ * iterations run in a continuous batch: every active request of the same degree, path,
+ * operator kind, vector precision and launch variant takes part in one batched launch per
+ * kernel of the (split-dual) CG iteration -- apply, alpha, update, direction -- in chunks of
+ * chunk_iterations, and requests join and leave the batch between chunks.  Each request's
+ * arithmetic (its CTAs, reductions and their order) is exactly that of its own solo launch,
+ * so its result does not depend on what else is in the batch.  batching = -1 runs every
+ * request as separate graph chunks on its own stream instead.  A native scheduler thread
+ * advances requests when their scalars have landed and admits new ones as slots and memory
+ * free up.  Every request solves the homogeneous Dirichlet problem on the unit cube with the
+ * given operator; mixed = 1 runs FP32 applies inside FP64 defect correction (else FP64 CG).
+ * The arena is the only device memory used (pinned host memory holds per-slot scalars and
+ * batch descriptors); it must outlive the server. */
 enum { MF_RHS_MANUFACTURED = 0, MF_RHS_RANDOM = 1 };
 
 typedef struct {
@@ -262,6 +269,8 @@ typedef struct {
   int32_t chunk_iterations; /* CG iterations per graph launch (default 20) */
   int32_t autotune;         /* 1: autotune the apply of each new operator class */
   double inner_rtol;        /* mixed: inner FP32 CG tolerance (default 1e-3) */
+  int32_t batching;         /* 0 / 1: continuous batches of CG iterations (default); -1: off */
+  int32_t reserved;
 } mf_server_config;
 
 typedef struct {

@@ -53,7 +53,8 @@ class mf_solve_options(C.Structure):
 
 class mf_server_config(C.Structure):
     _fields_ = [("max_slots", C.c_int32), ("queue_capacity", C.c_int32), ("chunk_iterations", C.c_int32),
-                ("autotune", C.c_int32), ("inner_rtol", C.c_double)]
+                ("autotune", C.c_int32), ("inner_rtol", C.c_double), ("batching", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class mf_request(C.Structure):
@@ -291,8 +292,8 @@ def mf_cg_record_history(hist_ptr: int | None, cap: int) -> None:
 
 # ---------------------------------------------------------------- serving
 def mf_server_create(arena_ptr: int, arena_bytes: int, max_slots: int = 32, queue_capacity: int = 0,
-                     chunk_iterations: int = 20, autotune: int = 0, inner_rtol: float = 1e-3):
-    cfg = mf_server_config(max_slots, queue_capacity, chunk_iterations, autotune, inner_rtol)
+                     chunk_iterations: int = 20, autotune: int = 0, inner_rtol: float = 1e-3, batching: int = 0):
+    cfg = mf_server_config(max_slots, queue_capacity, chunk_iterations, autotune, inner_rtol, batching, 0)
     h = C.c_void_p()
     _check(lib().mf_server_create(C.byref(cfg), arena_ptr, arena_bytes, C.byref(h)))
     return h.value

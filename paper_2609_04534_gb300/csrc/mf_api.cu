@@ -8,6 +8,7 @@
 #include <new>
 #include <tuple>
 
+#include "mf_dd.cuh"
 #include "mf_internal.h"
 
 namespace mf {
@@ -46,6 +47,19 @@ mf_status launch_apply_split(const mf_operator* op, int elem, const void* x, voi
 mf_status launch_apply_cg(const mf_operator* op, int vk, void* p, const void* r, void* y, CgState* st, double* partials,
                           int update_p, long long* nblocks, cudaStream_t s) {
   MF_DISPATCH_N(op->n, apply_cg_n, op, vk, p, r, y, st, partials, update_p, nblocks, s);
+}
+mf_status apply_batch_fill(const BatchMember* m, int n, int vk, void* jobs_host, long long* block0_host) {
+  MF_DISPATCH_N(m[0].op->n, apply_batch_fill_n, m, n, vk, jobs_host, block0_host);
+}
+mf_status apply_batch_launch(const mf_operator* op0, int vk, const void* jobs_dev, const long long* block0_dev,
+                             int njobs, long long blocks, cudaStream_t s) {
+  MF_DISPATCH_N(op0->n, apply_batch_launch_n, op0, vk, jobs_dev, block0_dev, njobs, blocks, s);
+}
+size_t apply_job_bytes(int vk) {
+  // the description layout depends only on the element types, not on the degree
+  return vk == VK_F32 ? sizeof(ApplyJob<float, float>)
+                      : (vk == VK_DDS ? sizeof(ApplyJob<dd, dd>)
+                                      : (vk == VK_DD ? sizeof(ApplyJob<double, dd>) : sizeof(ApplyJob<double, double>)));
 }
 // every launch variant puts at least 4 cells of a 32-cell tile in one CTA
 long long apply_max_blocks(const mf_operator* op) { return op->g.ntiles * (BL / 4); }

@@ -85,19 +85,21 @@ __device__ __forceinline__ double block_sum(double v) {
 
 // Called by every thread of every block after the block partial is known.  Returns true
 // in thread 0 of the last block to finish, with *total = sum of partials in index order.
-__device__ __forceinline__ bool last_block_total(RedScratch* sc, double part, double* total) {
+// cta / ncta: the CTA's index and the CTA count of its reduction (a batched launch runs
+// several reductions, each over its own CTA range and scratch).
+__device__ __forceinline__ bool last_block_total(RedScratch* sc, double part, double* total, int cta, int ncta) {
   __shared__ bool am_last;
   if (threadIdx.x == 0) {
-    sc->partial[blockIdx.x] = part;
+    sc->partial[cta] = part;
     __threadfence();
     const unsigned prev = atomicAdd(&sc->counter, 1u);
-    am_last = (prev == gridDim.x - 1);
+    am_last = (prev == (unsigned)ncta - 1);
   }
   __syncthreads();
   if (!am_last) return false;
   __threadfence();
   double s = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += RED_THREADS) s += ((volatile double*)sc->partial)[b];
+  for (int b = threadIdx.x; b < ncta; b += RED_THREADS) s += ((volatile double*)sc->partial)[b];
   s = block_sum(s);
   if (threadIdx.x == 0) {
     sc->counter = 0; // self-cleaning for the next launch
@@ -121,7 +123,7 @@ __global__ void __launch_bounds__(RED_THREADS) dot_kernel(const T* __restrict__ 
     acc.add(node_weight<N>(g, e, split), a[e], b[e]);
   const double s = block_sum(acc.value());
   double tot;
-  if (last_block_total(sc, s, &tot)) *out = tot;
+  if (last_block_total(sc, s, &tot, blockIdx.x, gridDim.x)) *out = tot;
 }
 
 // alpha = rr / <p, q>
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(RED_THREADS) cg_pq_kernel(const T* __restrict_
     acc.add(node_weight<N>(g, e, 0), p[e], q[e]);
   const double s = block_sum(acc.value());
   double tot;
-  if (last_block_total(sc, s, &tot)) {
+  if (last_block_total(sc, s, &tot, blockIdx.x, gridDim.x)) {
     if (st->flag == 0) {
       st->pq = tot;
       if (!(tot > 0.0) || !isfinite(tot)) { st->flag = 2; st->alpha = 0.0; }
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(RED_THREADS) cg_xr_kernel(T* __restrict__ x, T
   }
   const double s = block_sum(acc.value());
   double tot;
-  if (last_block_total(sc, s, &tot)) {
+  if (last_block_total(sc, s, &tot, blockIdx.x, gridDim.x)) {
     if (st->flag == 0) {
       st->beta = tot / st->rr;
       st->rr = tot;
@@ -188,15 +190,15 @@ struct alignas(4 * sizeof(T) < 16 ? 16 : 4 * sizeof(T)) Quad {
 
 // p = r + beta p, two quads per thread and trip so that four 16-byte loads are in flight
 template <typename T>
-__global__ void cg_p_kernel(const T* __restrict__ r, T* __restrict__ p, long long n, const CgState* st, int was_running) {
-  (void)was_running;
+__device__ __forceinline__ void cg_p_body(const T* __restrict__ r, T* __restrict__ p, long long n, const CgState* st,
+                                          long long cta, long long ncta) {
   const T be = scalar_from_double<T>(st->beta);
   if (st->flag != 0 && st->flag != 1) return;
   const long long nq = n / 4;
   const Quad<T>* __restrict__ rq = reinterpret_cast<const Quad<T>*>(r);
   Quad<T>* __restrict__ pq = reinterpret_cast<Quad<T>*>(p);
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nq; i += 2 * stride) {
+  const long long stride = ncta * blockDim.x;
+  for (long long i = cta * (long long)blockDim.x + threadIdx.x; i < nq; i += 2 * stride) {
     const bool two = i + stride < nq;
     Quad<T> a = pq[i], b = rq[i], c, d;
     if (two) { c = pq[i + stride]; d = rq[i + stride]; }
@@ -209,6 +211,11 @@ __global__ void cg_p_kernel(const T* __restrict__ r, T* __restrict__ p, long lon
       pq[i + stride] = c;
     }
   }
+}
+template <typename T>
+__global__ void cg_p_kernel(const T* __restrict__ r, T* __restrict__ p, long long n, const CgState* st, int was_running) {
+  (void)was_running;
+  cg_p_body<T>(r, p, n, st, blockIdx.x, gridDim.x);
 }
 
 // Split-dual CG update (Sec. 4: the Krylov loop on split data).  q~ = A_K p is the split
@@ -225,9 +232,9 @@ __global__ void cg_p_kernel(const T* __restrict__ r, T* __restrict__ p, long lon
 // x-neighbours at both pencil ends) is issued before any sum, so a thread keeps up to 7n + 8
 // loads in flight.
 template <typename T, int N>
-__global__ void __launch_bounds__(RED_THREADS) cg_update_kernel(T* __restrict__ x, T* __restrict__ r,
-                                                                const T* __restrict__ p, const T* __restrict__ q,
-                                                                GridInfo g, RedScratch* sc, CgState* st, double* hist) {
+__device__ __forceinline__ void cg_update_body(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                                               const T* __restrict__ q, const GridInfo& g, RedScratch* sc, CgState* st,
+                                               double* hist, int cta, int ncta) {
   constexpr int N2 = N * N, N3 = N2 * N, K = N - 1;
   if (st->flag != 0) return; // uniform: converged or stopped, nothing changes
   const T al = scalar_from_double<T>(st->alpha);
@@ -245,9 +252,9 @@ __global__ void __launch_bounds__(RED_THREADS) cg_update_kernel(T* __restrict__ 
   const long long dzp =
       lz < TZ - 1 ? -(long long)K * N2 * BL + TX * TY : tz_step - (long long)K * N2 * BL - TX * TY * (TZ - 1);
   const long long units = g.ntiles * N2;
-  const long long warps = (long long)gridDim.x * (RED_THREADS / 32);
+  const long long warps = (long long)ncta * (RED_THREADS / 32);
   typename AccOf<T>::type acc;
-  for (long long u = blockIdx.x * (long long)(RED_THREADS / 32) + (threadIdx.x >> 5); u < units; u += warps) {
+  for (long long u = cta * (long long)(RED_THREADS / 32) + (threadIdx.x >> 5); u < units; u += warps) {
     const long long t = u / N2;
     const int jk = (int)(u - t * N2);
     const int j = jk % N, k = jk / N;
@@ -314,7 +321,7 @@ __global__ void __launch_bounds__(RED_THREADS) cg_update_kernel(T* __restrict__ 
   }
   const double s = block_sum(acc.value());
   double tot;
-  if (last_block_total(sc, s, &tot)) {
+  if (last_block_total(sc, s, &tot, cta, ncta)) {
     st->beta = tot / st->rr;
     st->rr = tot;
     st->it += 1;
@@ -324,11 +331,16 @@ __global__ void __launch_bounds__(RED_THREADS) cg_update_kernel(T* __restrict__ 
     else if (st->it >= st->maxit) st->flag = 3;
   }
 }
+template <typename T, int N>
+__global__ void __launch_bounds__(RED_THREADS) cg_update_kernel(T* __restrict__ x, T* __restrict__ r,
+                                                                const T* __restrict__ p, const T* __restrict__ q,
+                                                                GridInfo g, RedScratch* sc, CgState* st, double* hist) {
+  cg_update_body<T, N>(x, r, p, q, g, sc, st, hist, blockIdx.x, gridDim.x);
+}
 
 // alpha = <r, r> / <p, A p> from the apply's per-CTA partials of <p, A p>, folded in a fixed
 // order (breakdown when <p, A p> is not positive and finite).
-__global__ void __launch_bounds__(1024) alpha_kernel(const double* __restrict__ partials, long long nparts,
-                                                     CgState* st) {
+__device__ __forceinline__ void alpha_body(const double* __restrict__ partials, long long nparts, CgState* st) {
   __shared__ double park[1024];
   if (st->flag != 0) return; // uniform
   double s = 0.0;
@@ -343,6 +355,53 @@ __global__ void __launch_bounds__(1024) alpha_kernel(const double* __restrict__ 
       st->alpha = st->rr / s;
     }
   }
+}
+__global__ void __launch_bounds__(1024) alpha_kernel(const double* __restrict__ partials, long long nparts,
+                                                     CgState* st) {
+  alpha_body(partials, nparts, st);
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched CG iteration (the serving loop's continuous batch): one launch per kernel for all
+// members; member i owns CTAs [block0[i], block0[i+1]) of the update and direction launches,
+// exactly the CTA count its own launch would use, so every member computes bitwise what it
+// would compute alone.
+// ---------------------------------------------------------------------------------------
+struct VecJob {
+  void *x, *r, *p, *q;
+  GridInfo g;
+  RedScratch* sc;
+  CgState* st;
+  double* hist;
+  double* apart;
+  long long n;                  // native elements
+  long long apply_blocks;       // CTAs of its apply (partials to fold)
+  long long up0, up1, pp0, pp1; // its CTA ranges in the update and direction launches
+};
+
+__device__ __forceinline__ int find_member(const VecJob* jobs, int njobs, bool update) {
+  int lo = 0, hi = njobs - 1; // largest i whose range starts at or before blockIdx.x
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((update ? jobs[mid].up0 : jobs[mid].pp0) <= (long long)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+__global__ void __launch_bounds__(1024) alpha_batch_kernel(const VecJob* __restrict__ jobs) {
+  const VecJob& j = jobs[blockIdx.x];
+  alpha_body(j.apart, j.apply_blocks, j.st);
+}
+template <typename T, int N>
+__global__ void __launch_bounds__(RED_THREADS) cg_update_batch_kernel(const VecJob* __restrict__ jobs, int njobs) {
+  const VecJob& j = jobs[find_member(jobs, njobs, true)];
+  cg_update_body<T, N>((T*)j.x, (T*)j.r, (const T*)j.p, (const T*)j.q, j.g, j.sc, j.st, j.hist,
+                       (int)((long long)blockIdx.x - j.up0), (int)(j.up1 - j.up0));
+}
+template <typename T>
+__global__ void cg_p_batch_kernel(const VecJob* __restrict__ jobs, int njobs) {
+  const VecJob& j = jobs[find_member(jobs, njobs, false)];
+  cg_p_body<T>((const T*)j.r, (T*)j.p, j.n, j.st, (long long)blockIdx.x - j.pp0, j.pp1 - j.pp0);
 }
 
 // Small element-wise kernels of the drivers.
@@ -769,12 +828,17 @@ static mf_status eng_finish(SolverEngine* e, mf_status st) {
 }
 
 mf_status engine_advance(SolverEngine* e) {
+  e->idle = false;
   if (e->phase == PH_DONE) return MF_OK;
   mf_status st;
   const long long n = e->op->n_native;
   if (e->phase == PH_INNER) {
     const CgState& h = e->hm->st;
-    if (h.flag == 0 && !e->cancel) return eng_chunk(e);
+    if (h.flag == 0 && !e->cancel) {
+      if (!e->external) return eng_chunk(e);
+      e->idle = true; // the batch runs the iterations
+      return MF_OK;
+    }
     eng_record_history(e, h.it);
     e->total_it += h.it;
     if (!e->mixed) {
@@ -808,6 +872,123 @@ mf_status engine_advance(SolverEngine* e) {
     return eng_inner_start(e, e->w.q, e->w.d32, e->inner_rtol, e->maxit - e->total_it);
   }
   return set_error(MF_ERR_ARG, "solver engine: advance before start");
+}
+
+// ---------------------------------------------------------------- continuous batches
+BatchMember engine_batch_member(const SolverEngine* e) {
+  BatchMember m;
+  m.op = e->op;
+  m.x = e->x_in;
+  m.r = e->w.r;
+  m.p = e->w.p;
+  m.q = e->w.q;
+  m.st = e->w.st;
+  m.apart = e->w.apart;
+  m.sc = e->w.sc2;
+  m.hist = nullptr;
+  return m;
+}
+
+size_t batch_plan_bytes(int n, int vk) {
+  return a256((size_t)n * apply_job_bytes(vk)) + a256(sizeof(long long) * (size_t)(n + 1)) +
+         a256(sizeof(VecJob) * (size_t)n);
+}
+
+static int update_blocks(const mf_operator* op) {
+  long long bl = (op->g.ntiles * (long long)op->n * op->n + RED_THREADS / 32 - 1) / (RED_THREADS / 32);
+  if (bl > RED_MAX_BLOCKS) bl = RED_MAX_BLOCKS;
+  if (bl < 1) bl = 1;
+  return (int)bl;
+}
+
+mf_status batch_plan_build(BatchPlan* plan, const BatchMember* m, int n, int elem, void* dev, void* host_stage,
+                           cudaStream_t s) {
+  if (n <= 0) return set_error(MF_ERR_ARG, "batch: no members");
+  const mf_operator* op0 = m[0].op;
+  const int vk = elem == ELEM_DD ? VK_DDS : view_of_elem(op0, elem);
+  for (int i = 1; i < n; ++i) {
+    const mf_operator* o = m[i].op;
+    if (o->n != op0->n || o->path != op0->path || o->kind != op0->kind ||
+        o->variant[vk == VK_DDS ? VK_DD : vk] != op0->variant[vk == VK_DDS ? VK_DD : vk])
+      return set_error(MF_ERR_ARG, "batch: members of different classes");
+  }
+  BatchPlan p;
+  p.n = n;
+  p.elem = elem;
+  p.vk = vk;
+  p.op0 = op0;
+  p.dev = static_cast<char*>(dev);
+  p.jobs_off = 0;
+  p.block0_off = a256((size_t)n * apply_job_bytes(vk));
+  p.vec_off = p.block0_off + a256(sizeof(long long) * (size_t)(n + 1));
+  char* h = static_cast<char*>(host_stage);
+  long long* block0 = reinterpret_cast<long long*>(h + p.block0_off);
+  mf_status st = apply_batch_fill(m, n, vk, h + p.jobs_off, block0);
+  if (st) return st;
+  p.apply_blocks = block0[n];
+  VecJob* vj = reinterpret_cast<VecJob*>(h + p.vec_off);
+  long long up = 0, pp = 0;
+  for (int i = 0; i < n; ++i) {
+    const mf_operator* o = m[i].op;
+    VecJob& v = vj[i];
+    v.x = m[i].x;
+    v.r = m[i].r;
+    v.p = m[i].p;
+    v.q = m[i].q;
+    v.g = o->g;
+    v.sc = static_cast<RedScratch*>(m[i].sc);
+    v.st = m[i].st;
+    v.hist = m[i].hist;
+    v.apart = m[i].apart;
+    v.n = o->n_native;
+    v.apply_blocks = block0[i + 1] - block0[i];
+    v.up0 = up;
+    up += update_blocks(o);
+    v.up1 = up;
+    v.pp0 = pp;
+    pp += ew_blocks(o->n_native);
+    v.pp1 = pp;
+  }
+  p.up_blocks = up;
+  p.pp_blocks = pp;
+  if (up > 0x7fffffffLL || pp > 0x7fffffffLL) return set_error(MF_ERR_UNSUPPORTED, "batch too large");
+  if ((st = cuda_check(cudaMemcpyAsync(dev, host_stage, batch_plan_bytes(n, vk), cudaMemcpyHostToDevice, s),
+                       "batch descriptors H2D")))
+    return st;
+  *plan = p;
+  return MF_OK;
+}
+
+template <int N>
+static mf_status batch_vec_n(const BatchPlan& p, cudaStream_t s) {
+  const VecJob* vj = reinterpret_cast<const VecJob*>(p.dev + p.vec_off);
+  alpha_batch_kernel<<<p.n, 1024, 0, s>>>(vj);
+  if (p.elem == 8) {
+    cg_update_batch_kernel<double, N><<<(unsigned)p.up_blocks, RED_THREADS, 0, s>>>(vj, p.n);
+    cg_p_batch_kernel<double><<<(unsigned)p.pp_blocks, 256, 0, s>>>(vj, p.n);
+  } else if (p.elem == ELEM_DD) {
+    cg_update_batch_kernel<dd, N><<<(unsigned)p.up_blocks, RED_THREADS, 0, s>>>(vj, p.n);
+    cg_p_batch_kernel<dd><<<(unsigned)p.pp_blocks, 256, 0, s>>>(vj, p.n);
+  } else {
+    cg_update_batch_kernel<float, N><<<(unsigned)p.up_blocks, RED_THREADS, 0, s>>>(vj, p.n);
+    cg_p_batch_kernel<float><<<(unsigned)p.pp_blocks, 256, 0, s>>>(vj, p.n);
+  }
+  return cuda_check(cudaGetLastError(), "batched CG launch");
+}
+
+mf_status batch_iteration(const BatchPlan& p, cudaStream_t s) {
+  mf_status st = apply_batch_launch(p.op0, p.vk, p.dev + p.jobs_off, reinterpret_cast<const long long*>(p.dev + p.block0_off),
+                                    p.n, p.apply_blocks, s);
+  if (st) return st;
+  MF_SWITCH_N(p.op0->n, batch_vec_n, p, s);
+}
+
+__global__ void gather_states_kernel(const VecJob* __restrict__ jobs, int n, CgState* __restrict__ out) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = *jobs[i].st;
+}
+mf_status batch_gather_states(const BatchPlan& p, CgState* states_dev, cudaStream_t s) {
+  gather_states_kernel<<<1, 256, 0, s>>>(reinterpret_cast<const VecJob*>(p.dev + p.vec_off), p.n, states_dev);
+  return cuda_check(cudaGetLastError(), "state gather");
 }
 
 void engine_release(SolverEngine* e) {

@@ -72,8 +72,11 @@ struct CgFuse {
   int update_p;
 };
 
-template <typename S, typename T, int N>
-struct ApplyArgs {
+// Everything an apply launch needs about one operator and one vector pair except the 1D
+// tables (which depend only on the degree, so a batched launch over several requests of the
+// same degree shares them in its parameters).
+template <typename S, typename T>
+struct ApplyJob {
   const S* __restrict__ x;
   S* __restrict__ y;
   const T* __restrict__ geom; // curved: [tile][comp][l][lane], 6 (Laplace) or 7 (Helmholtz) comps
@@ -81,7 +84,6 @@ struct ApplyArgs {
   T G[6];                     // affine: w-free metric w det J J^-1 J^-T (xx,xy,xz,yy,yz,zz)
   T mdet;                     // affine: mass_coeff * |det J|
   T gx, gy, gz, cmass;        // Cartesian: det/h_d^2 and mass_coeff * det
-  Tab<T, N> tab;
   // FP32 curved: the metric is computed per point from per-direction tables of
   // sin(pi xh), cos(pi xh) at the Gauss points of every cell layer ([(nx+ny+nz)*N][2]).
   const float* gtab;
@@ -90,6 +92,32 @@ struct ApplyArgs {
   // L2 prefetch distance in tiles (about one wave of resident CTAs ahead; 0 = off): the first
   // CTA of tile t prefetches the input and geometry of tile t + pf_tiles
   int pf_tiles;
+};
+
+template <typename S, typename T, int N>
+struct ApplyArgs {
+  ApplyJob<S, T> j;
+  Tab<T, N> tab;
+};
+
+// A batched apply over several requests of one degree, path and precision: CTA b belongs to
+// job i with block0[i] <= b < block0[i + 1] and runs that job's CTA b - block0[i].
+template <typename S, typename T, int N>
+struct ApplyBatch {
+  Tab<T, N> tab;
+  const ApplyJob<S, T>* jobs;
+  const long long* block0; // njobs + 1 entries
+  int njobs;
+};
+
+// One request of a batched CG iteration (the serving loop): its operator and CG storage.
+struct BatchMember {
+  const mf_operator* op;
+  void *x, *r, *p, *q; // CG vectors in the batch's element type
+  CgState* st;
+  double* apart;       // per-CTA <p, A p> partials of its apply
+  void* sc;            // reduction scratch of its update
+  double* hist;        // residual history (may be null)
 };
 
 // Host-side double tables (any n <= MAXN).
@@ -157,6 +185,16 @@ mf_status apply_cg_n(const mf_operator* op, int vk, void* p, const void* r, void
                      int update_p, long long* nblocks, cudaStream_t s);
 template <int N>
 mf_status dss_n(const mf_operator* op, int elem, void* y, cudaStream_t s);
+template <int N>
+mf_status apply_batch_fill_n(const BatchMember* m, int n, int vk, void* jobs_host, long long* block0_host);
+template <int N>
+mf_status apply_batch_launch_n(const mf_operator* op0, int vk, const void* jobs_dev, const long long* block0_dev,
+                               int njobs, long long blocks, cudaStream_t s);
+// batched CG-step apply (mf_api.cu dispatch): all members share degree, path, kind and variant
+mf_status apply_batch_fill(const BatchMember* m, int n, int vk, void* jobs_host, long long* block0_host);
+mf_status apply_batch_launch(const mf_operator* op0, int vk, const void* jobs_dev, const long long* block0_dev,
+                             int njobs, long long blocks, cudaStream_t s);
+size_t apply_job_bytes(int vk); // size of one member's description
 template <int N>
 mf_status geometry_n(const mf_operator* op, int vk, void* geom, cudaStream_t s);
 template <int N>

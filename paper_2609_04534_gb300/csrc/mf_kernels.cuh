@@ -87,7 +87,7 @@ __device__ __forceinline__ void prefetch_l2_warp(const void* p, unsigned long lo
 // and, for streamed geometry, its metric) from HBM into L2, so that the CTAs of the next wave
 // find their loads in L2.  Tiles are contiguous chunks of both arrays.
 template <typename S, typename T, int N, int NC>
-__device__ __forceinline__ void prefetch_next_wave(const ApplyArgs<S, T, N>& a, long long t, int lane0) {
+__device__ __forceinline__ void prefetch_next_wave(const ApplyJob<S, T>& a, long long t, int lane0) {
   constexpr int N3 = N * N * N;
   if (a.pf_tiles <= 0 || lane0 != 0 || threadIdx.x >= 32) return;
   const long long tn = t + a.pf_tiles;
@@ -106,7 +106,7 @@ __device__ __forceinline__ void prefetch_next_wave(const ApplyArgs<S, T, N>& a, 
 // zeroing padding cells and, for Dirichlet, the constrained nodes (the P of P A P).  In a
 // CG step with update_p the loaded vector is the new direction p = r + beta p, written back.
 template <typename S, typename T, int N, int CB, int NT>
-__device__ __forceinline__ void load_tile(const ApplyArgs<S, T, N>& a, long long t, int lane0, T* buf) {
+__device__ __forceinline__ void load_tile(const ApplyJob<S, T>& a, long long t, int lane0, T* buf) {
   constexpr int N2 = N * N, N3 = N2 * N;
   const long long base = t * (long long)N3 * BL + lane0;
   const bool fuse = a.cg.st != nullptr && a.cg.update_p;
@@ -143,7 +143,7 @@ __device__ __forceinline__ void load_tile(const ApplyArgs<S, T, N>& a, long long
 // Store one x-pencil (j, k) of cell c to global y, zeroing padding / constrained nodes.  In a
 // fused CG step each stored value is also paired with p (acc += p y over real copies).
 template <typename S, typename T, int N, int CB, typename Acc>
-__device__ __forceinline__ void store_xpencil(const ApplyArgs<S, T, N>& a, long long t, int lane0, int c, int j, int k,
+__device__ __forceinline__ void store_xpencil(const ApplyJob<S, T>& a, long long t, int lane0, int c, int j, int k,
                                               const T* out, Acc& acc, const S* pv) {
   constexpr int N2 = N * N, N3 = N2 * N;
   int cx, cy, cz;
@@ -164,16 +164,16 @@ __device__ __forceinline__ void store_xpencil(const ApplyArgs<S, T, N>& a, long 
 
 // A CTA's part of <p, A_K p> in a CG step: every thread parks its value in red[threadIdx.x]
 // before a barrier the caller provides; after it, warp 0 folds red in a fixed order and
-// writes partials[blockIdx.x] with a plain store (the next kernel of the stream reads it, so
+// writes partials[cta] with a plain store (the next kernel of the stream reads it, so
 // no fence is needed and no thread waits for its stores to drain).
 template <int NT>
-__device__ __forceinline__ void cta_partial_after_barrier(const double* red, double* partials) {
+__device__ __forceinline__ void cta_partial_after_barrier(const double* red, double* partials, long long cta) {
   if (threadIdx.x >= 32) return;
   double s = 0.0;
   for (int i = threadIdx.x; i < NT; i += 32) s += red[i];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  if (threadIdx.x == 0) partials[cta] = s;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -182,21 +182,22 @@ __device__ __forceinline__ void cta_partial_after_barrier(const double* red, dou
 // (Kronecker factors listed z, y, x).  x-sweep: M and K (2); y-sweep: M on Mx, K on Mx, M on
 // Kx (3); z-sweep: M on the combination and K on (M(x)M)x (2).
 // ---------------------------------------------------------------------------------------
-template <typename S, typename T, int N, int CB, int MINB, bool HELM>
-__global__ void __launch_bounds__(N * N * CB, MINB) apply_cartesian(ApplyArgs<S, T, N> a) {
-  constexpr int N2 = N * N, N3 = N2 * N, NT = N2 * CB, GPT = BL / CB;
+// One CTA: cells [lane0, lane0 + CB) of tile t; cta = the CTA's index in its operator's grid
+// (where its CG partial goes).
+template <typename S, typename T, int N, int CB, bool HELM>
+__device__ __forceinline__ void cartesian_body(const ApplyJob<S, T>& a, const Tab<T, N>& tab, long long t, int lane0,
+                                               long long cta) {
+  constexpr int N2 = N * N, N3 = N2 * N, NT = N2 * CB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* buf0 = reinterpret_cast<T*>(smem_raw);
   T* buf1 = buf0 + N3 * CB;
-  if (a.cg.st != nullptr && a.cg.st->flag != 0) return; // fused CG step after convergence: no work
-  const long long t = blockIdx.x / GPT;
-  const int lane0 = (blockIdx.x % GPT) * CB;
+  if (a.cg.st != nullptr && a.cg.st->flag != 0) return; // CG step after convergence: no work
   prefetch_next_wave<S, T, N, 0>(a, t, lane0);
   load_tile<S, T, N, CB, NT>(a, t, lane0, buf0);
   __syncthreads();
   const int c = threadIdx.x % CB, p = threadIdx.x / CB, pa = p % N, pb = p / N;
-  const T* M = a.tab.M;
-  const T* K = a.tab.K;
+  const T* M = tab.M;
+  const T* K = tab.K;
   { // x: pencil (j=pa, k=pb)
     T in[N];
 #pragma unroll
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_cartesian(ApplyArgs<S,
     __shared__ double red[NT];
     red[threadIdx.x] = acc.value();
     __syncthreads();
-    cta_partial_after_barrier<NT>(red, a.cg.partials);
+    cta_partial_after_barrier<NT>(red, a.cg.partials, cta);
   }
 }
 
@@ -282,23 +283,22 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_cartesian(ApplyArgs<S,
 // derivative Dc (three sweeps), v = G grad u at every point (6 metric entries; Helmholtz adds
 // m u), then the transposes: Dc^T per direction summed, and S^T along z, y, x.
 // ---------------------------------------------------------------------------------------
-template <typename S, typename T, int N, int CB, int MINB, bool CURVED, bool HELM>
-__global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T, N> a) {
-  constexpr int N2 = N * N, N3 = N2 * N, NT = N2 * CB, GPT = BL / CB;
+template <typename S, typename T, int N, int CB, bool CURVED, bool HELM>
+__device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<T, N>& tab, long long t, int lane0,
+                                             long long cta) {
+  constexpr int N2 = N * N, N3 = N2 * N, NT = N2 * CB;
   constexpr int NC = HELM ? 7 : 6;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* buf0 = reinterpret_cast<T*>(smem_raw);
   T* buf1 = buf0 + N3 * CB;
   T* buf2 = buf1 + N3 * CB;
-  if (a.cg.st != nullptr && a.cg.st->flag != 0) return; // fused CG step after convergence: no work
-  const long long t = blockIdx.x / GPT;
-  const int lane0 = (blockIdx.x % GPT) * CB;
+  if (a.cg.st != nullptr && a.cg.st->flag != 0) return; // CG step after convergence: no work
   prefetch_next_wave<S, T, N, (CURVED && sizeof(T) != 4) ? NC : 0>(a, t, lane0);
   load_tile<S, T, N, CB, NT>(a, t, lane0, buf0);
   __syncthreads();
   const int c = threadIdx.x % CB, p = threadIdx.x / CB, pa = p % N, pb = p / N;
-  const T* Sm = a.tab.S;
-  const T* Dc = a.tab.Dc;
+  const T* Sm = tab.S;
+  const T* Dc = tab.Dc;
   { // x-sweep with S, pencil (j=pa, k=pb), in place
     T in[N];
 #pragma unroll
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T
       const float ib = 1.0f / beta;
       const float au = a.amp * ib;
       const float c2 = au * au * (v1 * v1 + v2 * v2 + v3 * v3);
-      const float wd = a.tab.W[pa] * a.tab.W[pb] * a.tab.W[q] * (a.h[0] * a.h[1] * a.h[2]) * fabsf(beta);
+      const float wd = tab.W[pa] * tab.W[pb] * tab.W[q] * (a.h[0] * a.h[1] * a.h[2]) * fabsf(beta);
       const float i0 = 1.0f / a.h[0], i1 = 1.0f / a.h[1], i2 = 1.0f / a.h[2];
       g0 = wd * i0 * i0 * (1.0f - 2.0f * au * v1 + c2);
       g1 = wd * i0 * i1 * (c2 - au * (v1 + v2));
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T
       g5 = gp[(long long)5 * N3 * BL];
       if (HELM) m = gp[(long long)6 * N3 * BL];
     } else {
-      const T w = a.tab.W[pa] * a.tab.W[pb] * a.tab.W[q];
+      const T w = tab.W[pa] * tab.W[pb] * tab.W[q];
       g0 = w * a.G[0]; g1 = w * a.G[1]; g2 = w * a.G[2];
       g3 = w * a.G[3]; g4 = w * a.G[4]; g5 = w * a.G[5];
       if (HELM) m = w * a.mdet;
@@ -486,8 +486,60 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T
     __shared__ double red[NT];
     red[threadIdx.x] = to_double(finish(pap));
     __syncthreads();
-    cta_partial_after_barrier<NT>(red, a.cg.partials);
+    cta_partial_after_barrier<NT>(red, a.cg.partials, cta);
   }
+}
+
+// Kernels: one operator per launch (CTA b = cells (b % GPT) * CB .. of tile b / GPT), or a
+// batch of operators of one degree (see ApplyBatch): the CTA finds its job by binary search
+// over the block offsets and copies the job's description into shared memory.
+template <typename S, typename T, int N, int CB, int MINB, bool HELM>
+__global__ void __launch_bounds__(N * N * CB, MINB) apply_cartesian(ApplyArgs<S, T, N> A) {
+  constexpr int GPT = BL / CB;
+  cartesian_body<S, T, N, CB, HELM>(A.j, A.tab, blockIdx.x / GPT, (blockIdx.x % GPT) * CB, blockIdx.x);
+}
+template <typename S, typename T, int N, int CB, int MINB, bool CURVED, bool HELM>
+__global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T, N> A) {
+  constexpr int GPT = BL / CB;
+  general_body<S, T, N, CB, CURVED, HELM>(A.j, A.tab, blockIdx.x / GPT, (blockIdx.x % GPT) * CB, blockIdx.x);
+}
+
+// the job of batched CTA blockIdx.x into shared memory; returns its local CTA index
+template <typename S, typename T>
+__device__ __forceinline__ long long batch_job(const ApplyJob<S, T>* jobs, const long long* block0, int njobs,
+                                               ApplyJob<S, T>& sj) {
+  __shared__ int jsel;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = njobs - 1; // largest i with block0[i] <= blockIdx.x
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (block0[mid] <= (long long)blockIdx.x) lo = mid;
+      else hi = mid - 1;
+    }
+    jsel = lo;
+  }
+  __syncthreads();
+  const int j = jsel;
+  static_assert(sizeof(ApplyJob<S, T>) % 8 == 0, "job description copied as 8-byte words");
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(jobs + j);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sj);
+  for (int i = threadIdx.x; i < (int)(sizeof(ApplyJob<S, T>) / 8); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  return (long long)blockIdx.x - block0[j];
+}
+template <typename S, typename T, int N, int CB, int MINB, bool HELM>
+__global__ void __launch_bounds__(N * N * CB, MINB) apply_cartesian_batch(ApplyBatch<S, T, N> B) {
+  constexpr int GPT = BL / CB;
+  __shared__ __align__(16) ApplyJob<S, T> sj;
+  const long long b = batch_job(B.jobs, B.block0, B.njobs, sj);
+  cartesian_body<S, T, N, CB, HELM>(sj, B.tab, b / GPT, (int)(b % GPT) * CB, b);
+}
+template <typename S, typename T, int N, int CB, int MINB, bool CURVED, bool HELM>
+__global__ void __launch_bounds__(N * N * CB, MINB) apply_general_batch(ApplyBatch<S, T, N> B) {
+  constexpr int GPT = BL / CB;
+  __shared__ __align__(16) ApplyJob<S, T> sj;
+  const long long b = batch_job(B.jobs, B.block0, B.njobs, sj);
+  general_body<S, T, N, CB, CURVED, HELM>(sj, B.tab, b / GPT, (int)(b % GPT) * CB, b);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -674,8 +726,8 @@ __global__ void layout_kernel(const T* __restrict__ in, T* __restrict__ out, Gri
 // ---------------------------------------------------------------------------------------
 // Host-side launchers for one degree.
 // ---------------------------------------------------------------------------------------
-template <typename S, typename T, int N>
-static void fill_args(const mf_operator* op, ApplyArgs<S, T, N>& a) {
+template <typename S, typename T>
+static void fill_job(const mf_operator* op, ApplyJob<S, T>& a) {
   a.g = op->g;
   for (int m = 0; m < 6; ++m) a.G[m] = host_from_double<T>(op->G[m]);
   a.mdet = host_from_double<T>(op->mdet);
@@ -689,14 +741,19 @@ static void fill_args(const mf_operator* op, ApplyArgs<S, T, N>& a) {
   a.h[0] = 1.0f / op->g.nx;
   a.h[1] = 1.0f / op->g.ny;
   a.h[2] = 1.0f / op->g.nz;
+  a.cg = CgFuse<S>{};
+  a.pf_tiles = 0;
+}
+template <typename T, int N>
+static void fill_tab(const mf_operator* op, Tab<T, N>& tab) {
   const HostTables& h = op->tab;
   for (int q = 0; q < N; ++q) {
-    a.tab.W[q] = host_from_double<T>(h.qw[q]);
+    tab.W[q] = host_from_double<T>(h.qw[q]);
     for (int i = 0; i < N; ++i) {
-      a.tab.S[q * N + i] = host_from_double<T>(h.S[q * MAXN + i]);
-      a.tab.Dc[q * N + i] = host_from_double<T>(h.Dc[q * MAXN + i]);
-      a.tab.M[q * N + i] = host_from_double<T>(h.M[q * MAXN + i]);
-      a.tab.K[q * N + i] = host_from_double<T>(h.K[q * MAXN + i]);
+      tab.S[q * N + i] = host_from_double<T>(h.S[q * MAXN + i]);
+      tab.Dc[q * N + i] = host_from_double<T>(h.Dc[q * MAXN + i]);
+      tab.M[q * N + i] = host_from_double<T>(h.M[q * MAXN + i]);
+      tab.K[q * N + i] = host_from_double<T>(h.K[q * MAXN + i]);
     }
   }
 }
@@ -735,11 +792,12 @@ static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, co
                                long long* nblocks, cudaStream_t s) {
   using C = Cfg<T, N, V>;
   ApplyArgs<S, T, N> a;
-  fill_args<S, T, N>(op, a);
-  a.cg = cg;
-  a.x = static_cast<const S*>(x);
-  a.y = static_cast<S*>(y);
-  a.geom = static_cast<const T*>(geom);
+  fill_job<S, T>(op, a.j);
+  fill_tab<T, N>(op, a.tab);
+  a.j.cg = cg;
+  a.j.x = static_cast<const S*>(x);
+  a.j.y = static_cast<S*>(y);
+  a.j.geom = static_cast<const T*>(geom);
   const bool helm = op->kind == MF_HELMHOLTZ;
   const size_t smem = (op->path == PATH_CARTESIAN ? 2 : 3) * sizeof(T) * N * N * N * C::CB;
   const long long blocks = op->g.ntiles * (BL / C::CB);
@@ -759,7 +817,7 @@ static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, co
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(apply)");
   }
-  a.pf_tiles = prefetch_distance_tiles((const void*)k, C::NT, smem, BL / C::CB);
+  a.j.pf_tiles = prefetch_distance_tiles((const void*)k, C::NT, smem, BL / C::CB);
   k<<<(unsigned)blocks, C::NT, smem, s>>>(a);
   return cuda_check(cudaGetLastError(), "apply launch");
 }
@@ -801,6 +859,94 @@ mf_status apply_cg_n(const mf_operator* op, int vk, void* p, const void* r, void
   return apply_split_t<double, dd, N>(op, v, x, y, op->v64.geom, cg, nblocks, s);
 }
 
+// ---------------------------------------------------------------------------------------
+// Batched CG-step apply over several operators of one degree, path, kind, view and launch
+// variant (the serving loop's continuous batch).  apply_batch_fill_n writes the jobs' device
+// descriptions and block offsets into host staging; apply_batch_launch_n launches one kernel
+// over all of them (tables from op0: they depend only on the degree).
+// ---------------------------------------------------------------------------------------
+template <typename S, typename T, int N, int V>
+static mf_status batch_fill_v(const BatchMember* m, int n, int vk, void* jobs_host, long long* block0_host) {
+  using C = Cfg<T, N, V>;
+  ApplyJob<S, T>* jobs = static_cast<ApplyJob<S, T>*>(jobs_host);
+  long long b = 0;
+  for (int i = 0; i < n; ++i) {
+    const mf_operator* op = m[i].op;
+    ApplyJob<S, T>& a = jobs[i];
+    fill_job<S, T>(op, a);
+    a.cg = CgFuse<S>{static_cast<S*>(m[i].p), static_cast<const S*>(m[i].r), m[i].st, m[i].apart, 0};
+    a.x = static_cast<const S*>(m[i].p);
+    a.y = static_cast<S*>(m[i].q);
+    a.geom = static_cast<const T*>(vk == VK_F32 ? op->v32.geom : op->v64.geom);
+    block0_host[i] = b;
+    b += op->g.ntiles * (BL / C::CB);
+  }
+  block0_host[n] = b;
+  return MF_OK;
+}
+
+template <typename S, typename T, int N, int V>
+static mf_status batch_launch_v(const mf_operator* op0, const void* jobs_dev, const long long* block0_dev, int njobs,
+                                long long blocks, cudaStream_t s) {
+  using C = Cfg<T, N, V>;
+  ApplyBatch<S, T, N> B;
+  fill_tab<T, N>(op0, B.tab);
+  B.jobs = static_cast<const ApplyJob<S, T>*>(jobs_dev);
+  B.block0 = block0_dev;
+  B.njobs = njobs;
+  const bool helm = op0->kind == MF_HELMHOLTZ;
+  const size_t smem = (op0->path == PATH_CARTESIAN ? 2 : 3) * sizeof(T) * N * N * N * C::CB;
+  if (blocks <= 0 || njobs <= 0) return MF_OK;
+  void (*k)(ApplyBatch<S, T, N>) = nullptr;
+  if (op0->path == PATH_CARTESIAN)
+    k = helm ? apply_cartesian_batch<S, T, N, C::CB, C::MINB, true> : apply_cartesian_batch<S, T, N, C::CB, C::MINB, false>;
+  else if (op0->path == PATH_AFFINE)
+    k = helm ? apply_general_batch<S, T, N, C::CB, C::MINB, false, true>
+             : apply_general_batch<S, T, N, C::CB, C::MINB, false, false>;
+  else
+    k = helm ? apply_general_batch<S, T, N, C::CB, C::MINB, true, true>
+             : apply_general_batch<S, T, N, C::CB, C::MINB, true, false>;
+  if (smem > 227 * 1024) return set_error(MF_ERR_UNSUPPORTED, "apply variant needs %zu bytes of shared memory", smem);
+  if (smem + sizeof(double) * C::NT + sizeof(ApplyJob<S, T>) + 1024 > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(batched apply)");
+  }
+  if (blocks > 0x7fffffffLL) return set_error(MF_ERR_UNSUPPORTED, "batched apply of %lld CTAs", blocks);
+  k<<<(unsigned)blocks, C::NT, smem, s>>>(B);
+  return cuda_check(cudaGetLastError(), "batched apply launch");
+}
+
+template <typename S, typename T, int N>
+static mf_status batch_fill_t(const BatchMember* m, int n, int vk, int variant, void* jobs_host, long long* block0_host) {
+  if (variant == 1) return batch_fill_v<S, T, N, 1>(m, n, vk, jobs_host, block0_host);
+  if (variant == 2) return batch_fill_v<S, T, N, 2>(m, n, vk, jobs_host, block0_host);
+  return batch_fill_v<S, T, N, 0>(m, n, vk, jobs_host, block0_host);
+}
+template <typename S, typename T, int N>
+static mf_status batch_launch_t(const mf_operator* op0, int variant, const void* jobs_dev, const long long* block0_dev,
+                                int njobs, long long blocks, cudaStream_t s) {
+  if (variant == 1) return batch_launch_v<S, T, N, 1>(op0, jobs_dev, block0_dev, njobs, blocks, s);
+  if (variant == 2) return batch_launch_v<S, T, N, 2>(op0, jobs_dev, block0_dev, njobs, blocks, s);
+  return batch_launch_v<S, T, N, 0>(op0, jobs_dev, block0_dev, njobs, blocks, s);
+}
+
+template <int N>
+mf_status apply_batch_fill_n(const BatchMember* m, int n, int vk, void* jobs_host, long long* block0_host) {
+  const int v = m[0].op->variant[vk == VK_DDS ? VK_DD : vk];
+  if (vk == VK_F32) return batch_fill_t<float, float, N>(m, n, vk, v, jobs_host, block0_host);
+  if (vk == VK_DDS) return batch_fill_t<dd, dd, N>(m, n, vk, v, jobs_host, block0_host);
+  if (vk == VK_DD) return batch_fill_t<double, dd, N>(m, n, vk, v, jobs_host, block0_host);
+  return batch_fill_t<double, double, N>(m, n, vk, v, jobs_host, block0_host);
+}
+template <int N>
+mf_status apply_batch_launch_n(const mf_operator* op0, int vk, const void* jobs_dev, const long long* block0_dev,
+                               int njobs, long long blocks, cudaStream_t s) {
+  const int v = op0->variant[vk == VK_DDS ? VK_DD : vk];
+  if (vk == VK_F32) return batch_launch_t<float, float, N>(op0, v, jobs_dev, block0_dev, njobs, blocks, s);
+  if (vk == VK_DDS) return batch_launch_t<dd, dd, N>(op0, v, jobs_dev, block0_dev, njobs, blocks, s);
+  if (vk == VK_DD) return batch_launch_t<double, dd, N>(op0, v, jobs_dev, block0_dev, njobs, blocks, s);
+  return batch_launch_t<double, double, N>(op0, v, jobs_dev, block0_dev, njobs, blocks, s);
+}
 template <int N>
 mf_status dss_n(const mf_operator* op, int elem, void* y, cudaStream_t s) {
   const long long total = op->n_unique;
@@ -854,6 +1000,9 @@ mf_status layout_n(const mf_operator* op, int elem, int mode, const void* in, vo
   template mf_status apply_cg_n<NN>(const mf_operator*, int, void*, const void*, void*, CgState*, double*, \
                                     int, long long*, cudaStream_t);                                     \
   template mf_status dss_n<NN>(const mf_operator*, int, void*, cudaStream_t);                           \
+  template mf_status apply_batch_fill_n<NN>(const BatchMember*, int, int, void*, long long*);            \
+  template mf_status apply_batch_launch_n<NN>(const mf_operator*, int, const void*, const long long*, int,  \
+                                              long long, cudaStream_t);                                 \
   template mf_status geometry_n<NN>(const mf_operator*, int, void*, cudaStream_t);                      \
   template mf_status layout_n<NN>(const mf_operator*, int, int, const void*, void*, cudaStream_t);      \
   }

@@ -5,10 +5,13 @@
 // caller's device arena are free; a request that does not fit yet does not block smaller
 // ones behind it.  Each admitted request keeps its geometry, vectors and CG state resident
 // in its own arena block and runs the solver engine (FP64 CG, or FP32 CG inside FP64
-// defect correction) on its slot's stream, as CUDA-graph chunks of CG iterations; the chunks
-// of all active requests are in flight together and overlap on the GPU.  A scheduler thread
-// (native) polls one event per slot, advances each request when its scalars have landed,
-// admits new requests as slots and memory free up, and retires finished ones.
+// defect correction).  Its set-up, outer defect-correction steps and finish run on its
+// slot's stream.  Its CG iterations run in a continuous batch: the requests in the inner-CG
+// phase are grouped by class (degree, path, kind, vector type, launch variant), and each
+// class runs chunks of batched iterations -- one launch per kernel for all its members --
+// on the class's stream; requests join and leave between chunks.  A scheduler thread
+// (native) polls one event per slot and per class, advances requests when their scalars
+// have landed, admits new requests as slots and memory free up, and retires finished ones.
 //
 // Results (status, iterations, residual, L2 error for manufactured right-hand sides, and the
 // submit / admit / finish times) are kept until mf_batch_poll has returned them.
@@ -96,6 +99,10 @@ __global__ void random_unique_kernel(double* u, long long n, unsigned long long 
 
 enum Stage { ST_QUEUED = 0, ST_SOLVING = 1, ST_FINISHING = 2, ST_DONE = 3 };
 
+// Requests whose apply launches at most this many CTAs join continuous batches (about two
+// waves of two CTAs per SM on 152 SMs).
+constexpr long long BATCH_MAX_CTAS = 1024;
+
 struct Job {
   uint64_t ticket = 0;
   mf_request req{};
@@ -114,6 +121,24 @@ struct Job {
   double l2 = -1.0;
   bool cancel = false;
   long long steps = 0, max_steps = 0; // engine advances (bounded: see job_start)
+  bool batch_ready = false;           // in the inner CG with scalars landed: joins the next chunk
+  bool in_batch = false;              // a chunk of its class is in flight
+};
+
+// A class of requests whose CG iterations share batched launches.
+struct BatchClass {
+  int n = 0, path = 0, kind = 0, elem = 0, variant = 0;
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev = nullptr;
+  int cap = 0;              // members the buffers hold
+  char* dev = nullptr;      // arena: descriptors, then the gathered states
+  size_t dev_bytes = 0;
+  char* host = nullptr;     // pinned: descriptor staging, then the states read back
+  size_t host_bytes = 0, states_off = 0;
+  std::vector<Job*> members;      // of the chunk in flight
+  std::vector<uint64_t> planned;  // tickets whose descriptors are on the device
+  BatchPlan plan;
+  bool running = false;
 };
 
 struct Slot {
@@ -137,6 +162,7 @@ struct mf_server {
   std::deque<mf::Job*> pending;
   std::map<uint64_t, mf::Job*> jobs;
   uint64_t next_ticket = 1;
+  std::vector<mf::BatchClass*> classes;
   std::thread th;
   std::atomic<bool> stop{false};
   std::chrono::steady_clock::time_point t0;
@@ -203,6 +229,14 @@ mf_status job_start(mf_server* sv, Job* j, Slot& sl, HostMirror* hm) {
   engine_init(&j->eng, j->op, j->req.mixed ? 1 : 0, j->b, j->x, j->req.rtol, j->req.maxit, j->cgws, s, hm);
   if (sv->cfg.chunk_iterations > 0) j->eng.chunk = sv->cfg.chunk_iterations;
   if (sv->cfg.inner_rtol > 0) j->eng.inner_rtol = sv->cfg.inner_rtol;
+  // Inner iterations come from the class batches for requests whose apply is a few waves of
+  // CTAs at most: those are launch- and latency-bound alone, and batched with others they
+  // share launches.  A larger request fills the GPU by itself and runs its own graph chunks
+  // (batched with small ones it would hold them to its own chunk time).
+  // (the default launch variant puts 8 to 32 cells of a 32-cell tile in one CTA: at most 4
+  // CTAs per tile below degree 8)
+  const long long ctas = j->op->g.ntiles * 4;
+  j->eng.external = sv->cfg.batching >= 0 && ctas <= BATCH_MAX_CTAS;
   if ((st = engine_start(&j->eng))) return st;
   // every advance finishes or moves the iteration count forward by a chunk
   j->max_steps = 2LL * ((long long)j->req.maxit / j->eng.chunk + 2) * (j->eng.max_outer + 2) + 16;
@@ -265,6 +299,164 @@ void job_fail(mf_server* sv, Job* j, Slot* sl, mf_status st) {
   sv->cv.notify_all();
 }
 
+int class_view(const Job* j) {
+  return j->eng.vt == ELEM_DD ? VK_DDS : (j->eng.vt == 4 ? VK_F32 : fp64_view(j->op));
+}
+
+// The batch class of a request in its inner CG (created on first use).  nullptr when its
+// buffers do not fit: the request then runs its own chunks.
+BatchClass* class_of(mf_server* sv, const Job* j) {
+  const int vk = class_view(j);
+  const int variant = j->op->variant[vk == VK_DDS ? VK_DD : vk];
+  for (BatchClass* c : sv->classes)
+    if (c->n == j->op->n && c->path == j->op->path && c->kind == j->op->kind && c->elem == j->eng.vt &&
+        c->variant == variant)
+      return c;
+  BatchClass* c = new (std::nothrow) BatchClass;
+  if (!c) return nullptr;
+  c->n = j->op->n;
+  c->path = j->op->path;
+  c->kind = j->op->kind;
+  c->elem = j->eng.vt;
+  c->variant = variant;
+  c->cap = (int)sv->slots.size();
+  const size_t desc = batch_plan_bytes(c->cap, vk);
+  c->states_off = desc;
+  c->dev_bytes = desc + a256(sizeof(CgState) * (size_t)c->cap);
+  c->host_bytes = c->dev_bytes;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    c->dev = sv->arena.alloc(c->dev_bytes);
+  }
+  bool ok = c->dev != nullptr && cudaMallocHost(&c->host, c->host_bytes) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    if (c->ev) cudaEventDestroy(c->ev);
+    if (c->s) cudaStreamDestroy(c->s);
+    if (c->host) cudaFreeHost(c->host);
+    if (c->dev) {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->arena.release(c->dev, c->dev_bytes);
+    }
+    delete c;
+    return nullptr;
+  }
+  sv->classes.push_back(c);
+  return c;
+}
+
+void class_destroy(mf_server* sv, BatchClass* c) {
+  if (c->s) cudaStreamSynchronize(c->s);
+  if (c->ev) cudaEventDestroy(c->ev);
+  if (c->s) cudaStreamDestroy(c->s);
+  if (c->host) cudaFreeHost(c->host);
+  (void)sv; // the arena block goes with the arena
+  delete c;
+}
+
+// After the engine advanced: finish, wait for the next batch, or continue on the own stream.
+mf_status after_advance(mf_server* sv, Job* j, Slot& sl) {
+  if (j->eng.phase == PH_DONE) return job_finish_enqueue(sv, j, sl, j->slot);
+  // idle: the mirrored scalars are current and nothing is in flight on the request's stream
+  if (j->eng.idle && !j->cancel) {
+    j->batch_ready = true;
+    return MF_OK;
+  }
+  return cuda_check(cudaEventRecord(sl.ev, sl.s), "event record");
+}
+
+// Chunks of batched CG iterations: collect finished ones, then start new ones.
+bool run_batches(mf_server* sv) {
+  bool progressed = false;
+  for (BatchClass* c : sv->classes) {
+    if (!c->running) continue;
+    const cudaError_t q = cudaEventQuery(c->ev);
+    if (q == cudaErrorNotReady) continue;
+    progressed = true;
+    c->running = false;
+    const CgState* hs = reinterpret_cast<const CgState*>(c->host + c->states_off);
+    for (size_t k = 0; k < c->members.size(); ++k) {
+      Job* j = c->members[k];
+      Slot& sl = sv->slots[j->slot];
+      j->in_batch = false;
+      if (q != cudaSuccess) {
+        job_fail(sv, j, &sl, cuda_check(q, "batch stream"));
+        continue;
+      }
+      j->eng.hm->st = hs[k];
+      if (++j->steps > j->max_steps) {
+        job_fail(sv, j, &sl, set_error(MF_ERR_TIMEOUT, "request %llu made no progress", (unsigned long long)j->ticket));
+        continue;
+      }
+      j->eng.cancel = j->cancel;
+      mf_status st = engine_advance(&j->eng);
+      if (!st) st = after_advance(sv, j, sl);
+      if (st) job_fail(sv, j, &sl, st);
+    }
+    c->members.clear();
+  }
+  // group the waiting requests by class
+  std::vector<std::pair<BatchClass*, Job*>> ready;
+  for (auto& sl : sv->slots) {
+    Job* j = sl.job;
+    if (!j || !j->batch_ready || j->in_batch) continue;
+    BatchClass* c = class_of(sv, j);
+    if (!c) { // no batch buffers: run this request's own chunks
+      j->batch_ready = false;
+      j->eng.external = false;
+      mf_status st = engine_advance(&j->eng);
+      if (!st) st = after_advance(sv, j, sl);
+      if (st) job_fail(sv, j, &sl, st);
+      progressed = true;
+      continue;
+    }
+    ready.emplace_back(c, j);
+  }
+  for (BatchClass* c : sv->classes) {
+    if (c->running) continue;
+    std::vector<Job*> mem;
+    for (auto& pr : ready)
+      if (pr.first == c && (int)mem.size() < c->cap) mem.push_back(pr.second);
+    if (mem.empty()) continue;
+    progressed = true;
+    std::vector<uint64_t> tickets;
+    for (Job* j : mem) tickets.push_back(j->ticket);
+    mf_status st = MF_OK;
+    if (tickets != c->planned) {
+      std::vector<BatchMember> bm;
+      for (Job* j : mem) bm.push_back(engine_batch_member(&j->eng));
+      st = batch_plan_build(&c->plan, bm.data(), (int)bm.size(), c->elem, c->dev, c->host, c->s);
+      c->planned = st ? std::vector<uint64_t>() : tickets;
+    }
+    const int chunk = mem[0]->eng.chunk;
+    for (int it = 0; it < chunk && st == MF_OK; ++it) st = batch_iteration(c->plan, c->s);
+    CgState* states_dev = reinterpret_cast<CgState*>(c->dev + c->states_off);
+    if (!st) st = batch_gather_states(c->plan, states_dev, c->s);
+    if (!st)
+      st = cuda_check(cudaMemcpyAsync(c->host + c->states_off, states_dev, sizeof(CgState) * mem.size(),
+                                      cudaMemcpyDeviceToHost, c->s), "batch states D2H");
+    if (!st) st = cuda_check(cudaEventRecord(c->ev, c->s), "batch event");
+    if (st) {
+      cudaStreamSynchronize(c->s);
+      c->planned.clear();
+      for (Job* j : mem) {
+        j->batch_ready = false;
+        job_fail(sv, j, &sv->slots[j->slot], st);
+      }
+      continue;
+    }
+    for (Job* j : mem) {
+      j->batch_ready = false;
+      j->in_batch = true;
+    }
+    c->members = mem;
+    c->running = true;
+  }
+  return progressed;
+}
+
 void scheduler(mf_server* sv) {
   cudaSetDevice(sv->device);
   const int nslot = (int)sv->slots.size();
@@ -311,7 +503,17 @@ void scheduler(mf_server* sv) {
     for (int i = 0; i < nslot; ++i) {
       Slot& sl = sv->slots[i];
       Job* j = sl.job;
-      if (!j) continue;
+      if (!j || j->in_batch) continue;
+      if (j->batch_ready) {
+        if (!j->cancel) continue; // waits for its class's next chunk
+        j->batch_ready = false;   // cancelled while waiting: finish on its own stream
+        j->eng.cancel = true;
+        mf_status st = engine_advance(&j->eng);
+        if (!st) st = after_advance(sv, j, sl);
+        if (st) job_fail(sv, j, &sl, st);
+        progressed = true;
+        continue;
+      }
       const cudaError_t q = cudaEventQuery(sl.ev);
       if (q == cudaErrorNotReady) continue;
       progressed = true;
@@ -324,16 +526,14 @@ void scheduler(mf_server* sv) {
           continue;
         }
         st = engine_advance(&j->eng);
-        if (!st) {
-          if (j->eng.phase == PH_DONE) st = job_finish_enqueue(sv, j, sl, i);
-          else st = cuda_check(cudaEventRecord(sl.ev, sl.s), "event record");
-        }
+        if (!st) st = after_advance(sv, j, sl);
       } else if (j->stage == ST_FINISHING) {
         job_retire(sv, j, sl, i);
         continue;
       }
       if (st) job_fail(sv, j, &sl, st);
     }
+    if (run_batches(sv)) progressed = true;
     if (!progressed) {
       std::unique_lock<std::mutex> lk(sv->mu);
       bool idle = true;
@@ -507,6 +707,8 @@ void mf_server_destroy(mf_server* sv) {
   sv->stop.store(true);
   sv->cv.notify_all();
   if (sv->th.joinable()) sv->th.join();
+  for (BatchClass* c : sv->classes) class_destroy(sv, c);
+  sv->classes.clear();
   for (auto& sl : sv->slots) {
     if (sl.s) cudaStreamSynchronize(sl.s);
     if (sl.job) engine_release(&sl.job->eng);

@@ -50,10 +50,32 @@ struct SolverEngine {
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   bool record = false, cancel = false;
+  bool external = false; // inner CG iterations are run by a batch (the server), not by chunks
+  bool idle = false;     // the last advance enqueued nothing (external inner CG waiting for a batch)
   int hist_off = 0;
 };
 
 size_t solve_ws_layout(const mf_operator* op, int mixed, char* base, SolveWs* w);
+
+// A continuous batch of CG solves of one class (degree, path, kind, vector element type and
+// launch variant): descriptors of all members in device memory, and the CTA counts of the
+// batched launches.  batch_plan_build stages the descriptors in host (pinned) memory and
+// copies them on stream s; batch_iteration enqueues one CG iteration of every member (four
+// launches); batch_gather_states copies every member's CgState to states_dev[i].
+struct BatchPlan {
+  int n = 0, elem = 0, vk = 0;
+  const mf_operator* op0 = nullptr;
+  char* dev = nullptr;
+  size_t jobs_off = 0, block0_off = 0, vec_off = 0;
+  long long apply_blocks = 0, up_blocks = 0, pp_blocks = 0;
+};
+size_t batch_plan_bytes(int n, int vk);
+mf_status batch_plan_build(BatchPlan* plan, const BatchMember* m, int n, int elem, void* dev, void* host_stage,
+                           cudaStream_t s);
+mf_status batch_iteration(const BatchPlan& plan, cudaStream_t s);
+mf_status batch_gather_states(const BatchPlan& plan, CgState* states_dev, cudaStream_t s);
+// the members a SolverEngine in the inner phase contributes to a batch
+BatchMember engine_batch_member(const SolverEngine* e);
 mf_status engine_init(SolverEngine* e, const mf_operator* op, int mixed, const void* b, void* x, double rtol, int maxit,
                       void* ws, cudaStream_t s, HostMirror* hm);
 // Enqueue the first phase (ends with a D2H copy into e->hm).

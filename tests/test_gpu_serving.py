@@ -33,9 +33,9 @@ def run(server, reqs, timeout=300.0):
     return res, outs
 
 
-def make_server(arena_gb=2.0, slots=16):
+def make_server(arena_gb=2.0, slots=16, batching=0):
     arena = torch.empty(int(arena_gb * 2**30), dtype=torch.uint8, device="cuda")
-    return mf.mf_server_create(arena.data_ptr(), arena.numel(), max_slots=slots), arena
+    return mf.mf_server_create(arena.data_ptr(), arena.numel(), max_slots=slots, batching=batching), arena
 
 
 MIX = [
@@ -61,6 +61,16 @@ def test_mix_results_equal_alone_and_converge(oracle):
         assert r["t_submit"] <= r["t_admit"] <= r["t_done"]
         if p["rhs"] == mf.MF_RHS_MANUFACTURED:
             assert 0 < r["l2_error"] < 0.1
+    # the same mix with every request on its own graph chunks (no batched launches): bitwise equal
+    sv, arena = make_server(batching=-1)
+    try:
+        res_solo, x_solo = run(sv, [mf.make_request(**p) for p in MIX])
+    finally:
+        mf.mf_server_destroy(sv)
+    for p, r, r1, x, x1 in zip(MIX, res_mix, res_solo, x_mix, x_solo):
+        assert r1["status"] == mf.MF_OK
+        assert r1["iterations"] == r["iterations"], p
+        assert np.array_equal(x1, x), p
     # each request alone on a fresh server: bitwise the same solution
     for p, x in zip(MIX, x_mix):
         sv, arena = make_server(slots=1)
@@ -77,6 +87,28 @@ def test_mix_results_equal_alone_and_converge(oracle):
     b[o.boundary_mask()] = 0.0
     xo = solve_direct(o, b)
     assert np.abs(x_mix[1] - xo).max() <= 1e-8 * np.abs(xo).max()
+
+
+def test_batches_of_one_class_match_solo_solves():
+    """Eight requests of one class (Q3 curved Laplace, mixed) of different sizes and seeds run in
+    one continuous batch; each result equals the request solved alone, bitwise, and FP64 ones
+    (double-float CG vectors) batch the same way."""
+    reqs = [dict(nx=4 + i, ny=5, nz=3 + (i % 3), degree=3, geometry=mf.MF_CURVED_SIN, rhs=mf.MF_RHS_RANDOM,
+                 seed=30 + i, mixed=i % 2) for i in range(8)]
+    sv, arena = make_server(slots=16)
+    try:
+        res, xs = run(sv, [mf.make_request(**p) for p in reqs])
+    finally:
+        mf.mf_server_destroy(sv)
+    for p, r, x in zip(reqs, res, xs):
+        assert r["status"] == mf.MF_OK and r["rel_residual"] <= 1e-10
+        sv1, arena1 = make_server(slots=1, batching=-1)
+        try:
+            (r1,), (x1,) = run(sv1, [mf.make_request(**p)])
+        finally:
+            mf.mf_server_destroy(sv1)
+        assert r1["iterations"] == r["iterations"]
+        assert np.array_equal(x1, x), p
 
 
 def test_admission_by_memory_and_queueing():
