@@ -139,6 +139,8 @@ struct BatchClass {
   std::vector<uint64_t> planned;  // tickets whose descriptors are on the device
   BatchPlan plan;
   bool running = false;
+  cudaGraphExec_t exec = nullptr; // the chunk of the planned composition
+  bool exec_current = false;
 };
 
 struct Slot {
@@ -349,6 +351,7 @@ BatchClass* class_of(mf_server* sv, const Job* j) {
 
 void class_destroy(mf_server* sv, BatchClass* c) {
   if (c->s) cudaStreamSynchronize(c->s);
+  if (c->exec) cudaGraphExecDestroy(c->exec);
   if (c->ev) cudaEventDestroy(c->ev);
   if (c->s) cudaStreamDestroy(c->s);
   if (c->host) cudaFreeHost(c->host);
@@ -365,6 +368,39 @@ mf_status after_advance(mf_server* sv, Job* j, Slot& sl) {
     return MF_OK;
   }
   return cuda_check(cudaEventRecord(sl.ev, sl.s), "event record");
+}
+
+// The chunk of a class's planned batch as a CUDA graph: chunk batched iterations, the state
+// gather and its copy to the pinned mirror.  An existing executable graph is updated in place
+// when the new one differs only in parameters (launch sizes, copy size), else rebuilt.
+mf_status capture_chunk(BatchClass* c, int chunk, int n) {
+  mf_status st = cuda_check(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal), "batch capture");
+  if (st) return st;
+  mf_status cst = MF_OK;
+  for (int it = 0; it < chunk && cst == MF_OK; ++it) cst = batch_iteration(c->plan, c->s);
+  CgState* states_dev = reinterpret_cast<CgState*>(c->dev + c->states_off);
+  if (!cst) cst = batch_gather_states(c->plan, states_dev, c->s);
+  if (!cst)
+    cst = cuda_check(cudaMemcpyAsync(c->host + c->states_off, states_dev, sizeof(CgState) * (size_t)n,
+                                     cudaMemcpyDeviceToHost, c->s), "batch states D2H");
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(c->s, &g);
+  if (cst || ce != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cst ? cst : cuda_check(ce, "batch capture end");
+  }
+  if (c->exec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(c->exec, g, &info) != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(c->exec);
+      c->exec = nullptr;
+    }
+  }
+  if (!c->exec) st = cuda_check(cudaGraphInstantiate(&c->exec, g, 0), "batch graph instantiate");
+  cudaGraphDestroy(g);
+  c->exec_current = st == MF_OK;
+  return st;
 }
 
 // Chunks of batched CG iterations: collect finished ones, then start new ones.
@@ -429,18 +465,15 @@ bool run_batches(mf_server* sv) {
       for (Job* j : mem) bm.push_back(engine_batch_member(&j->eng));
       st = batch_plan_build(&c->plan, bm.data(), (int)bm.size(), c->elem, c->dev, c->host, c->s);
       c->planned = st ? std::vector<uint64_t>() : tickets;
+      c->exec_current = false;
     }
-    const int chunk = mem[0]->eng.chunk;
-    for (int it = 0; it < chunk && st == MF_OK; ++it) st = batch_iteration(c->plan, c->s);
-    CgState* states_dev = reinterpret_cast<CgState*>(c->dev + c->states_off);
-    if (!st) st = batch_gather_states(c->plan, states_dev, c->s);
-    if (!st)
-      st = cuda_check(cudaMemcpyAsync(c->host + c->states_off, states_dev, sizeof(CgState) * mem.size(),
-                                      cudaMemcpyDeviceToHost, c->s), "batch states D2H");
+    if (!st && !c->exec_current) st = capture_chunk(c, mem[0]->eng.chunk, (int)mem.size());
+    if (!st) st = cuda_check(cudaGraphLaunch(c->exec, c->s), "batch chunk launch");
     if (!st) st = cuda_check(cudaEventRecord(c->ev, c->s), "batch event");
     if (st) {
       cudaStreamSynchronize(c->s);
       c->planned.clear();
+      c->exec_current = false;
       for (Job* j : mem) {
         j->batch_ready = false;
         job_fail(sv, j, &sv->slots[j->slot], st);
