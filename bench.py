@@ -267,6 +267,34 @@ def profile_apply(args):
     mf.mf_mesh_destroy(mesh)
 
 
+def profile_cg(args):
+    """A few CG iterations of one case through mf_cg_profile (each kernel launched directly),
+    for ncu captures of the CG kernels: the apply with <p, A p>, alpha, update, direction."""
+    import torch
+
+    import paper_2609_04534_gb300 as mf
+
+    N, k, geom, prec = args.profile_cg.split(",")
+    N, k = int(N), int(k)
+    g = mf.MF_CURVED_SIN if geom == "curved" else mf.MF_AFFINE
+    p = {"fp64": mf.MF_FP64, "fp32": mf.MF_FP32}[prec]
+    dt = torch.float64 if p == mf.MF_FP64 else torch.float32
+    stream = torch.cuda.Stream()
+    s = stream.cuda_stream
+    mesh, op, info, ws = make_op(mf, torch, N, k, g, mf.MF_LAPLACE, p, mf.MF_BC_DIRICHLET0, s)
+    with torch.cuda.stream(stream):
+        b = random_native(mf, torch, op, info, N, k, 1, dt, s)
+        x = torch.zeros_like(b)
+        cws = torch.empty(mf.mf_cg_workspace_bytes(op, 0), dtype=torch.uint8, device="cuda")
+    stream.synchronize()
+    r = mf.mf_cg_profile(op, b.data_ptr(), x.data_ptr(), args.reps, mf.MF_CG_SPLIT_DUAL, cws.data_ptr(),
+                         cws.numel(), s)
+    print(json.dumps({"case": args.profile_cg, "n_cellwise": info["n_cellwise"],
+                      **{kk: round(v, 4) for kk, v in r.items()}}), flush=True)
+    mf.mf_operator_destroy(op)
+    mf.mf_mesh_destroy(mesh)
+
+
 def solve_run(args):
     """Mixed-precision Poisson solve: Q4 on the curved N^3 mesh (default 96^3), manufactured
     u = sin(2 pi x) sin(2 pi y) sin(2 pi z), FP32 apply inside FP64 defect correction to
@@ -388,6 +416,8 @@ def main():
     ap.add_argument("--solve", action="store_true")
     ap.add_argument("--profile-apply", default=None, metavar="N,k,geom,prec,kind",
                     help="only run a few applies of one case (for ncu), e.g. 32,4,curved,fp64,laplace")
+    ap.add_argument("--profile-cg", default=None, metavar="N,k,geom,prec",
+                    help="only run --reps CG iterations of one case (for ncu), e.g. 48,4,curved,fp64")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--variant", type=int, default=-1, help="--profile-apply: launch variant (-1: all)")
     ap.add_argument("--serve", type=int, default=0, metavar="NREQ",
@@ -399,6 +429,9 @@ def main():
     args = ap.parse_args()
     if args.profile_apply:
         profile_apply(args)
+        return
+    if args.profile_cg:
+        profile_cg(args)
         return
     if args.solve:
         solve_run(args)
@@ -475,8 +508,14 @@ def main():
     # costs 12 FP32 instructions (TwoProd 4 + TwoSum 6 + 2 adds), so the ALU roof of the
     # emulated arithmetic is the FP32 issue rate / 12, in FP64-equivalent FLOP/s.
     emu_peak = pk["fp32_tflops"] / 12.0
+    # DRAM bytes of this kernel (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
+    # capture of the same kernel on the curved Q4 48^3 case: 78.5 bytes per cell-wise DoF,
+    # scaled here to the bench's DoFs (traffic grows in proportion to the cells).
+    traffic = 78.48 * ncw
     roof = {"bound": "alu", "achieved": flops / t_fused / 1e12, "peak": emu_peak, "unit": "TFLOP/s",
-            "frac": flops / t_fused / 1e12 / emu_peak, "traffic": None,
+            "frac": flops / t_fused / 1e12 / emu_peak, "traffic": traffic,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of apply_general<dd,dd,5,16,2,1,0> "
+                              "on Q4 curved 48^3 (13.82 M DoFs): 1084.9 MB, scaled by DoFs",
             "kernel": "apply_general<double,dd,5,curved,laplace> as the split-dual CG apply "
                       "(A_K p and <p, A_K p> at the quadrature points)",
             "kernel_ms": round(t_fused * 1e3, 4),
