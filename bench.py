@@ -361,10 +361,12 @@ def serve_run(args):
     ks = rng.integers(2, 7, n)
     geo = rng.integers(0, 2, n)
     arena = torch.empty(int(120 * 2**30), dtype=torch.uint8, device="cuda")
-    sv = mf.mf_server_create(arena.data_ptr(), arena.numel(), max_slots=64, autotune=1,
-                             batching=-1 if args.no_batching else 0)
+    # --fp64-single: the baseline of the same stream, the plain FP64 solver one request at a time
+    single = args.fp64_single
+    sv = mf.mf_server_create(arena.data_ptr(), arena.numel(), max_slots=1 if single else 64, autotune=1,
+                             batching=-1 if (args.no_batching or single) else 0)
     reqs = [mf.make_request(int(N), int(N), int(N), int(k), geometry=mf.MF_CURVED_SIN if g else mf.MF_AFFINE,
-                            rhs=mf.MF_RHS_MANUFACTURED, rtol=1e-10, maxit=400000, mixed=1)
+                            rhs=mf.MF_RHS_MANUFACTURED, rtol=1e-10, maxit=400000, mixed=0 if single else 1)
             for N, k, g in zip(Ns, ks, geo)]
     rate = args.rate
     gaps = rng.exponential(1.0 / rate, n) if rate > 0 else np.zeros(n)
@@ -400,8 +402,9 @@ def serve_run(args):
            "failed": [dict(N=int(Ns[i]), k=int(ks[i]), curved=int(geo[i]), status=int(rs[i]["status"]),
                            iterations=int(rs[i]["iterations"]), outer=int(rs[i]["outer_iterations"]),
                            rel=float(rs[i]["rel_residual"])) for i in range(n) if rs[i]["status"] != 0][:10],
-           "batching": not args.no_batching,
-           "arena_peak_gb": st["arena_peak"] / 2**30, "slots": 64}
+           "batching": not (args.no_batching or single),
+           "solver": "plain FP64 CG, one request at a time" if single else "mixed precision, 64 slots",
+           "arena_peak_gb": st["arena_peak"] / 2**30, "slots": 1 if single else 64}
     print(json.dumps(out), flush=True)
 
 
@@ -424,6 +427,8 @@ def main():
                     help="serving run: NREQ solve requests with Poisson arrivals (prints its own JSON line)")
     ap.add_argument("--rate", type=float, default=0.0, help="serving arrival rate (requests/s); 0 = measure capacity")
     ap.add_argument("--no-batching", action="store_true", help="serving: every request on its own graph chunks")
+    ap.add_argument("--fp64-single", action="store_true",
+                    help="serving baseline: the same stream through the plain FP64 solver, one request at a time")
     ap.add_argument("--solve-n", type=int, default=96, help="cells per axis of the --solve mesh")
     ap.add_argument("--inner-rtol", type=float, nargs="+", default=[1e-3], help="inner FP32 CG tolerances to run")
     args = ap.parse_args()
