@@ -37,6 +37,18 @@ __device__ __forceinline__ dd fma(dd a, dd b, dd c) {
   return dd(s, t + (c.lo + e));
 }
 
+// a*b as the first term of a chain: TwoProd of the leading parts plus the cross terms, not
+// renormalised (an fma() into a zero accumulator would spend a TwoSum on the zero).
+__device__ __forceinline__ dd mul0(dd a, dd b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return dd(p, e);
+}
+__device__ __forceinline__ double mul0(double a, double b) { return a * b; }
+__device__ __forceinline__ float mul0(float a, float b) { return a * b; }
+
 __device__ __forceinline__ dd finish(dd a) {
   const float h = a.hi + a.lo;
   return dd(h, a.lo - (h - a.hi));

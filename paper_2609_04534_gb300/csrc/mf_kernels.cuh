@@ -204,9 +204,9 @@ __device__ __forceinline__ void cartesian_body(const ApplyJob<S, T>& a, const Ta
     for (int i = 0; i < N; ++i) in[i] = buf0[(i + N * pa + N2 * pb) * CB + c];
 #pragma unroll
     for (int q = 0; q < N; ++q) {
-      T m = T(0), s = T(0);
+      T m = mul0(M[q * N], in[0]), s = mul0(K[q * N], in[0]);
 #pragma unroll
-      for (int i = 0; i < N; ++i) { m = fma(M[q * N + i], in[i], m); s = fma(K[q * N + i], in[i], s); }
+      for (int i = 1; i < N; ++i) { m = fma(M[q * N + i], in[i], m); s = fma(K[q * N + i], in[i], s); }
       buf0[(q + N * pa + N2 * pb) * CB + c] = finish(m);
       buf1[(q + N * pa + N2 * pb) * CB + c] = finish(s);
     }
@@ -221,9 +221,9 @@ __device__ __forceinline__ void cartesian_body(const ApplyJob<S, T>& a, const Ta
     }
 #pragma unroll
     for (int q = 0; q < N; ++q) {
-      T mm = T(0), km = T(0), mk = T(0);
+      T mm = mul0(M[q * N], am[0]), km = mul0(K[q * N], am[0]), mk = mul0(M[q * N], ak[0]);
 #pragma unroll
-      for (int j = 0; j < N; ++j) {
+      for (int j = 1; j < N; ++j) {
         mm = fma(M[q * N + j], am[j], mm);
         km = fma(K[q * N + j], am[j], km);
         mk = fma(M[q * N + j], ak[j], mk);
@@ -245,9 +245,9 @@ __device__ __forceinline__ void cartesian_body(const ApplyJob<S, T>& a, const Ta
     }
 #pragma unroll
     for (int q = 0; q < N; ++q) {
-      T s = T(0), r = T(0);
+      T s = mul0(M[q * N], w[0]), r = mul0(K[q * N], mm[0]);
 #pragma unroll
-      for (int k = 0; k < N; ++k) { s = fma(M[q * N + k], w[k], s); r = fma(K[q * N + k], mm[k], r); }
+      for (int k = 1; k < N; ++k) { s = fma(M[q * N + k], w[k], s); r = fma(K[q * N + k], mm[k], r); }
       o[q] = finish(fma(a.gz, finish(r), s));
     }
     __syncthreads();
@@ -305,9 +305,9 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
     for (int i = 0; i < N; ++i) in[i] = buf0[(i + N * pa + N2 * pb) * CB + c];
 #pragma unroll
     for (int q = 0; q < N; ++q) {
-      T s = T(0);
+      T s = mul0(Sm[q * N], in[0]);
 #pragma unroll
-      for (int i = 0; i < N; ++i) s = fma(Sm[q * N + i], in[i], s);
+      for (int i = 1; i < N; ++i) s = fma(Sm[q * N + i], in[i], s);
       buf0[(q + N * pa + N2 * pb) * CB + c] = finish(s);
     }
   }
@@ -318,9 +318,9 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
     for (int j = 0; j < N; ++j) in[j] = buf0[(pa + N * j + N2 * pb) * CB + c];
 #pragma unroll
     for (int q = 0; q < N; ++q) {
-      T s = T(0);
+      T s = mul0(Sm[q * N], in[0]);
 #pragma unroll
-      for (int j = 0; j < N; ++j) s = fma(Sm[q * N + j], in[j], s);
+      for (int j = 1; j < N; ++j) s = fma(Sm[q * N + j], in[j], s);
       buf0[(pa + N * q + N2 * pb) * CB + c] = finish(s);
     }
   }
@@ -334,17 +334,17 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
     for (int k = 0; k < N; ++k) in[k] = buf0[(pa + N * pb + N2 * k) * CB + c];
 #pragma unroll
     for (int q = 0; q < N; ++q) {
-      T s = T(0);
+      T s = mul0(Sm[q * N], in[0]);
 #pragma unroll
-      for (int k = 0; k < N; ++k) s = fma(Sm[q * N + k], in[k], s);
+      for (int k = 1; k < N; ++k) s = fma(Sm[q * N + k], in[k], s);
       U[q] = finish(s);
       buf1[(pa + N * pb + N2 * q) * CB + c] = U[q];
     }
 #pragma unroll
     for (int q = 0; q < N; ++q) {
-      T s = T(0);
+      T s = mul0(Dc[q * N], U[0]);
 #pragma unroll
-      for (int r = 0; r < N; ++r) s = fma(Dc[q * N + r], U[r], s);
+      for (int r = 1; r < N; ++r) s = fma(Dc[q * N + r], U[r], s);
       d3[q] = finish(s);
     }
   }
@@ -375,9 +375,10 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
 #pragma unroll
   for (int q = 0; q < N; ++q) {
     const int l = pa + N * pb + N2 * q;
-    T s1 = T(0), s2 = T(0);
+    T s1 = mul0(Dc[pa * N], buf1[(N * pb + N2 * q) * CB + c]);
+    T s2 = mul0(Dc[pb * N], buf1[(pa + N2 * q) * CB + c]);
 #pragma unroll
-    for (int r = 0; r < N; ++r) {
+    for (int r = 1; r < N; ++r) {
       s1 = fma(Dc[pa * N + r], buf1[(r + N * pb + N2 * q) * CB + c], s1);
       s2 = fma(Dc[pb * N + r], buf1[(pa + N * r + N2 * q) * CB + c], s2);
     }
@@ -419,9 +420,9 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
       if (HELM) m = w * a.mdet;
     }
     const T d3q = d3[q];
-    const T v1 = finish(fma(g0, d1, fma(g1, d2, g2 * d3q)));
-    const T v2 = finish(fma(g1, d1, fma(g3, d2, g4 * d3q)));
-    const T v3 = finish(fma(g2, d1, fma(g4, d2, g5 * d3q)));
+    const T v1 = finish(fma(g0, d1, fma(g1, d2, mul0(g2, d3q))));
+    const T v2 = finish(fma(g1, d1, fma(g3, d2, mul0(g4, d3q))));
+    const T v3 = finish(fma(g2, d1, fma(g4, d2, mul0(g5, d3q))));
     buf0[l * CB + c] = v1;
     buf2[l * CB + c] = v2;
     d3[q] = v3;
@@ -437,9 +438,12 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
     T tq[N];
 #pragma unroll
     for (int q = 0; q < N; ++q) {
-      T s = HELM ? U[q] : T(0);
+      T s = mul0(Dc[pa], buf0[(N * pb + N2 * q) * CB + c]);
+      if (HELM) s = s + U[q];
+      s = fma(Dc[pb], buf2[(pa + N2 * q) * CB + c], s);
+      s = fma(Dc[q], d3[0], s);
 #pragma unroll
-      for (int r = 0; r < N; ++r) {
+      for (int r = 1; r < N; ++r) {
         s = fma(Dc[r * N + pa], buf0[(r + N * pb + N2 * q) * CB + c], s);
         s = fma(Dc[r * N + pb], buf2[(pa + N * r + N2 * q) * CB + c], s);
         s = fma(Dc[r * N + q], d3[r], s);
@@ -448,9 +452,9 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
     }
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-      T s = T(0);
+      T s = mul0(Sm[k], tq[0]);
 #pragma unroll
-      for (int q = 0; q < N; ++q) s = fma(Sm[q * N + k], tq[q], s);
+      for (int q = 1; q < N; ++q) s = fma(Sm[q * N + k], tq[q], s);
       buf1[(pa + N * pb + N2 * k) * CB + c] = finish(s);
     }
   }
@@ -461,9 +465,9 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
     for (int q = 0; q < N; ++q) in[q] = buf1[(pa + N * q + N2 * pb) * CB + c];
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      T s = T(0);
+      T s = mul0(Sm[j], in[0]);
 #pragma unroll
-      for (int q = 0; q < N; ++q) s = fma(Sm[q * N + j], in[q], s);
+      for (int q = 1; q < N; ++q) s = fma(Sm[q * N + j], in[q], s);
       buf1[(pa + N * j + N2 * pb) * CB + c] = finish(s);
     }
   }
@@ -475,9 +479,9 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
     for (int q = 0; q < N; ++q) in[q] = buf1[(q + N * pa + N2 * pb) * CB + c];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      T s = T(0);
+      T s = mul0(Sm[i], in[0]);
 #pragma unroll
-      for (int q = 0; q < N; ++q) s = fma(Sm[q * N + i], in[q], s);
+      for (int q = 1; q < N; ++q) s = fma(Sm[q * N + i], in[q], s);
       o[i] = finish(s);
     }
     store_xpencil<S, T, N, CB>(a, t, lane0, c, pa, pb, o, acc, static_cast<const S*>(nullptr));
