@@ -32,9 +32,23 @@ struct GridInfo {
 //   Dc[q][r] = psi_r'(x_q)            derivative of the Gauss-point Lagrange basis (collocation)
 //   W[q]                               Gauss weights
 //   M[i][j] = sum_q W_q S[q][i] S[q][j],  K[i][j] = sum_q W_q D[q][i] D[q][j]  (1D mass, stiffness)
+//
+// Even-odd forms (for 1D contractions y = A x with A centro-symmetric, A[n-1-q][n-1-i] =
+// A[q][i] -- S, S^T, M, K -- or centro-antisymmetric, A[n-1-q][n-1-i] = -A[q][i] -- Dc, Dc^T):
+// with H = n/2, e_i = x_i + x_{n-1-i}, o_i = x_i - x_{n-1-i} (i < H) and e_H = x_H for odd n,
+//   F[q][i] = (A[q][i] + A[q][n-1-i]) / 2 (i < H), F[q][H] = A[q][H];  G[q][i] = (A[q][i] - A[q][n-1-i]) / 2
+// give u = F e and w = G o for q < H, and then y_q = u + w and y_{n-1-q} = u - w (symmetric)
+// or w - u (antisymmetric); the middle output of odd n is Mid . e (symmetric, Mid = A[H][0..H])
+// or Mid . o (antisymmetric, Mid = A[H][0..H-1]).
+template <typename T, int N>
+struct EoTab {
+  static constexpr int H = N / 2, HE = (N + 1) / 2;
+  T F[H * HE], G[H * H > 0 ? H * H : 1], Mid[HE];
+};
 template <typename T, int N>
 struct Tab {
   T S[N * N], Dc[N * N], W[N], M[N * N], K[N * N];
+  EoTab<T, N> eS, eSt, eD, eDt, eM, eK; // S, S^T, Dc, Dc^T, M, K
 };
 
 // Precision views of an operator: storage type of the vectors / compute type of the apply.

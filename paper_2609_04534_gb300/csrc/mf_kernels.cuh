@@ -102,6 +102,55 @@ __device__ __forceinline__ void prefetch_next_wave(const ApplyJob<S, T>& a, long
   }
 }
 
+// Sum and difference of two values without renormalisation (inputs of further products).
+__device__ __forceinline__ dd add_lazy(dd a, dd b) {
+  const float s = a.hi + b.hi;
+  const float v = s - a.hi;
+  const float t = (a.hi - (s - v)) + (b.hi - v);
+  return dd(s, t + (a.lo + b.lo));
+}
+__device__ __forceinline__ dd sub_lazy(dd a, dd b) { return add_lazy(a, dd(-b.hi, -b.lo)); }
+__device__ __forceinline__ double add_lazy(double a, double b) { return a + b; }
+__device__ __forceinline__ double sub_lazy(double a, double b) { return a - b; }
+__device__ __forceinline__ float add_lazy(float a, float b) { return a + b; }
+__device__ __forceinline__ float sub_lazy(float a, float b) { return a - b; }
+
+// sum_i c[i] x[i], i < M (M >= 1), not renormalised
+template <typename T, int M>
+__device__ __forceinline__ T chain(const T* c, const T* x) {
+  T s = mul0(c[0], x[0]);
+#pragma unroll
+  for (int i = 1; i < M; ++i) s = fma(c[i], x[i], s);
+  return s;
+}
+
+// Even-odd 1D contraction of one pencil (see EoTab): the pencil folded into its sum and
+// difference halves, H (H + 1) products per half instead of n^2 in all.  ANTI: the matrix is
+// centro-antisymmetric.  out[q] finished.
+template <typename T, int N, bool ANTI>
+struct Fold {
+  static constexpr int H = N / 2, HE = (N + 1) / 2;
+  T e[HE], o[H > 0 ? H : 1];
+  __device__ __forceinline__ explicit Fold(const T* in) {
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      e[i] = add_lazy(in[i], in[N - 1 - i]);
+      o[i] = sub_lazy(in[i], in[N - 1 - i]);
+    }
+    if (N % 2) e[H] = in[H];
+  }
+  __device__ __forceinline__ void apply(const EoTab<T, N>& t, T* out) const {
+#pragma unroll
+    for (int q = 0; q < H; ++q) {
+      const T u = chain<T, HE>(t.F + q * HE, e);
+      const T w = chain<T, H>(t.G + q * H, o);
+      out[q] = finish(add_lazy(u, w));
+      out[N - 1 - q] = finish(ANTI ? sub_lazy(w, u) : sub_lazy(u, w));
+    }
+    if (N % 2) out[H] = finish(ANTI ? chain<T, H>(t.Mid, o) : chain<T, HE>(t.Mid, e));
+  }
+};
+
 // Load the CB cells [lane0, lane0+CB) of tile t into smem as buf[l*CB + c] (cell fastest),
 // zeroing padding cells and, for Dirichlet, the constrained nodes (the P of P A P).  In a
 // CG step with update_p the loaded vector is the new direction p = r + beta p, written back.
@@ -196,63 +245,54 @@ __device__ __forceinline__ void cartesian_body(const ApplyJob<S, T>& a, const Ta
   load_tile<S, T, N, CB, NT>(a, t, lane0, buf0);
   __syncthreads();
   const int c = threadIdx.x % CB, p = threadIdx.x / CB, pa = p % N, pb = p / N;
-  const T* M = tab.M;
-  const T* K = tab.K;
-  { // x: pencil (j=pa, k=pb)
-    T in[N];
+  { // x: pencil (j=pa, k=pb): M and K share one fold of the pencil
+    T in[N], mo[N], ko[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) in[i] = buf0[(i + N * pa + N2 * pb) * CB + c];
+    const Fold<T, N, false> f(in);
+    f.apply(tab.eM, mo);
+    f.apply(tab.eK, ko);
 #pragma unroll
     for (int q = 0; q < N; ++q) {
-      T m = mul0(M[q * N], in[0]), s = mul0(K[q * N], in[0]);
-#pragma unroll
-      for (int i = 1; i < N; ++i) { m = fma(M[q * N + i], in[i], m); s = fma(K[q * N + i], in[i], s); }
-      buf0[(q + N * pa + N2 * pb) * CB + c] = finish(m);
-      buf1[(q + N * pa + N2 * pb) * CB + c] = finish(s);
+      buf0[(q + N * pa + N2 * pb) * CB + c] = mo[q];
+      buf1[(q + N * pa + N2 * pb) * CB + c] = ko[q];
     }
   }
   __syncthreads();
   { // y: pencil (i=pa, k=pb)
-    T am[N], ak[N];
+    T am[N], ak[N], mm[N], km[N], mk[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       am[j] = buf0[(pa + N * j + N2 * pb) * CB + c];
       ak[j] = buf1[(pa + N * j + N2 * pb) * CB + c];
     }
+    {
+      const Fold<T, N, false> fa(am);
+      fa.apply(tab.eM, mm);
+      fa.apply(tab.eK, km);
+    }
+    Fold<T, N, false>(ak).apply(tab.eM, mk);
 #pragma unroll
     for (int q = 0; q < N; ++q) {
-      T mm = mul0(M[q * N], am[0]), km = mul0(K[q * N], am[0]), mk = mul0(M[q * N], ak[0]);
-#pragma unroll
-      for (int j = 1; j < N; ++j) {
-        mm = fma(M[q * N + j], am[j], mm);
-        km = fma(K[q * N + j], am[j], km);
-        mk = fma(M[q * N + j], ak[j], mk);
-      }
-      mm = finish(mm);
-      T w = fma(a.gx, finish(mk), a.gy * finish(km));
-      if (HELM) w = fma(a.cmass, mm, w);
+      T w = fma(a.gx, mk[q], mul0(a.gy, km[q]));
+      if (HELM) w = fma(a.cmass, mm[q], w);
       buf0[(pa + N * q + N2 * pb) * CB + c] = finish(w);
-      buf1[(pa + N * q + N2 * pb) * CB + c] = mm;
+      buf1[(pa + N * q + N2 * pb) * CB + c] = mm[q];
     }
   }
   __syncthreads();
   { // z: pencil (i=pa, j=pb); result rows go straight back to smem, then out by x-pencils
-    T w[N], mm[N], o[N];
+    T w[N], mm[N], so[N], ro[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       w[k] = buf0[(pa + N * pb + N2 * k) * CB + c];
       mm[k] = buf1[(pa + N * pb + N2 * k) * CB + c];
     }
-#pragma unroll
-    for (int q = 0; q < N; ++q) {
-      T s = mul0(M[q * N], w[0]), r = mul0(K[q * N], mm[0]);
-#pragma unroll
-      for (int k = 1; k < N; ++k) { s = fma(M[q * N + k], w[k], s); r = fma(K[q * N + k], mm[k], r); }
-      o[q] = finish(fma(a.gz, finish(r), s));
-    }
+    Fold<T, N, false>(w).apply(tab.eM, so);
+    Fold<T, N, false>(mm).apply(tab.eK, ro);
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < N; ++q) buf0[(pa + N * pb + N2 * q) * CB + c] = o[q];
+    for (int q = 0; q < N; ++q) buf0[(pa + N * pb + N2 * q) * CB + c] = finish(fma(a.gz, ro[q], so[q]));
   }
   __syncthreads();
   PairAcc<S> acc;
@@ -297,32 +337,23 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
   load_tile<S, T, N, CB, NT>(a, t, lane0, buf0);
   __syncthreads();
   const int c = threadIdx.x % CB, p = threadIdx.x / CB, pa = p % N, pb = p / N;
-  const T* Sm = tab.S;
   const T* Dc = tab.Dc;
   { // x-sweep with S, pencil (j=pa, k=pb), in place
-    T in[N];
+    T in[N], out[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) in[i] = buf0[(i + N * pa + N2 * pb) * CB + c];
+    Fold<T, N, false>(in).apply(tab.eS, out);
 #pragma unroll
-    for (int q = 0; q < N; ++q) {
-      T s = mul0(Sm[q * N], in[0]);
-#pragma unroll
-      for (int i = 1; i < N; ++i) s = fma(Sm[q * N + i], in[i], s);
-      buf0[(q + N * pa + N2 * pb) * CB + c] = finish(s);
-    }
+    for (int q = 0; q < N; ++q) buf0[(q + N * pa + N2 * pb) * CB + c] = out[q];
   }
   __syncthreads();
   { // y-sweep, pencil (i=pa, k=pb)
-    T in[N];
+    T in[N], out[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) in[j] = buf0[(pa + N * j + N2 * pb) * CB + c];
+    Fold<T, N, false>(in).apply(tab.eS, out);
 #pragma unroll
-    for (int q = 0; q < N; ++q) {
-      T s = mul0(Sm[q * N], in[0]);
-#pragma unroll
-      for (int j = 1; j < N; ++j) s = fma(Sm[q * N + j], in[j], s);
-      buf0[(pa + N * q + N2 * pb) * CB + c] = finish(s);
-    }
+    for (int q = 0; q < N; ++q) buf0[(pa + N * q + N2 * pb) * CB + c] = out[q];
   }
   __syncthreads();
   // z-sweep, pencil (i=pa, j=pb): values U and the z-derivative stay in registers, U also goes
@@ -332,21 +363,10 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
     T in[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) in[k] = buf0[(pa + N * pb + N2 * k) * CB + c];
+    Fold<T, N, false>(in).apply(tab.eS, U);
 #pragma unroll
-    for (int q = 0; q < N; ++q) {
-      T s = mul0(Sm[q * N], in[0]);
-#pragma unroll
-      for (int k = 1; k < N; ++k) s = fma(Sm[q * N + k], in[k], s);
-      U[q] = finish(s);
-      buf1[(pa + N * pb + N2 * q) * CB + c] = U[q];
-    }
-#pragma unroll
-    for (int q = 0; q < N; ++q) {
-      T s = mul0(Dc[q * N], U[0]);
-#pragma unroll
-      for (int r = 1; r < N; ++r) s = fma(Dc[q * N + r], U[r], s);
-      d3[q] = finish(s);
-    }
+    for (int q = 0; q < N; ++q) buf1[(pa + N * pb + N2 * q) * CB + c] = U[q];
+    Fold<T, N, true>(U).apply(tab.eD, d3);
   }
   __syncthreads();
   // Per Gauss point (pa, pb, q): reference gradient (x and y parts from buf1), metric, and the
@@ -436,40 +456,33 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
   // t = Dc^T_x v1 + Dc^T_y v2 + Dc^T_z v3 (+ m u) at points (pa, pb, q), then S^T along z
   {
     T tq[N];
+    Fold<T, N, true>(d3).apply(tab.eDt, tq); // Dc^T_z v3 along this pencil
 #pragma unroll
     for (int q = 0; q < N; ++q) {
       T s = mul0(Dc[pa], buf0[(N * pb + N2 * q) * CB + c]);
-      if (HELM) s = s + U[q];
       s = fma(Dc[pb], buf2[(pa + N2 * q) * CB + c], s);
-      s = fma(Dc[q], d3[0], s);
 #pragma unroll
       for (int r = 1; r < N; ++r) {
         s = fma(Dc[r * N + pa], buf0[(r + N * pb + N2 * q) * CB + c], s);
         s = fma(Dc[r * N + pb], buf2[(pa + N * r + N2 * q) * CB + c], s);
-        s = fma(Dc[r * N + q], d3[r], s);
       }
+      s = add_lazy(s, tq[q]);
+      if (HELM) s = add_lazy(s, U[q]);
       tq[q] = finish(s);
     }
+    T out[N];
+    Fold<T, N, false>(tq).apply(tab.eSt, out);
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-      T s = mul0(Sm[k], tq[0]);
-#pragma unroll
-      for (int q = 1; q < N; ++q) s = fma(Sm[q * N + k], tq[q], s);
-      buf1[(pa + N * pb + N2 * k) * CB + c] = finish(s);
-    }
+    for (int k = 0; k < N; ++k) buf1[(pa + N * pb + N2 * k) * CB + c] = out[k];
   }
   __syncthreads();
   { // S^T along y, pencil (i=pa, k=pb), in place
-    T in[N];
+    T in[N], out[N];
 #pragma unroll
     for (int q = 0; q < N; ++q) in[q] = buf1[(pa + N * q + N2 * pb) * CB + c];
+    Fold<T, N, false>(in).apply(tab.eSt, out);
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-      T s = mul0(Sm[j], in[0]);
-#pragma unroll
-      for (int q = 1; q < N; ++q) s = fma(Sm[q * N + j], in[q], s);
-      buf1[(pa + N * j + N2 * pb) * CB + c] = finish(s);
-    }
+    for (int j = 0; j < N; ++j) buf1[(pa + N * j + N2 * pb) * CB + c] = out[j];
   }
   __syncthreads();
   NoAcc acc;
@@ -477,13 +490,7 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
     T in[N], o[N];
 #pragma unroll
     for (int q = 0; q < N; ++q) in[q] = buf1[(q + N * pa + N2 * pb) * CB + c];
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      T s = mul0(Sm[i], in[0]);
-#pragma unroll
-      for (int q = 1; q < N; ++q) s = fma(Sm[q * N + i], in[q], s);
-      o[i] = finish(s);
-    }
+    Fold<T, N, false>(in).apply(tab.eSt, o);
     store_xpencil<S, T, N, CB>(a, t, lane0, c, pa, pb, o, acc, static_cast<const S*>(nullptr));
   }
   if (fuse) { // after the last barrier, so that no warp waits for warp 0's fold
@@ -748,9 +755,31 @@ static void fill_job(const mf_operator* op, ApplyJob<S, T>& a) {
   a.cg = CgFuse<S>{};
   a.pf_tiles = 0;
 }
+// A(q, i) = a[q * MAXN + i], or a[i * MAXN + q] for the transpose
+template <typename T, int N>
+static void fill_eo(const double* a, bool transpose, EoTab<T, N>& e) {
+  constexpr int H = N / 2, HE = (N + 1) / 2;
+  auto A = [&](int q, int i) { return transpose ? a[i * MAXN + q] : a[q * MAXN + i]; };
+  for (int q = 0; q < H; ++q) {
+    for (int i = 0; i < H; ++i) {
+      e.F[q * HE + i] = host_from_double<T>(0.5 * (A(q, i) + A(q, N - 1 - i)));
+      e.G[q * H + i] = host_from_double<T>(0.5 * (A(q, i) - A(q, N - 1 - i)));
+    }
+    if (N % 2) e.F[q * HE + H] = host_from_double<T>(A(q, H));
+  }
+  if (N % 2)
+    for (int i = 0; i < HE; ++i) e.Mid[i] = host_from_double<T>(A(H, i));
+}
+
 template <typename T, int N>
 static void fill_tab(const mf_operator* op, Tab<T, N>& tab) {
   const HostTables& h = op->tab;
+  fill_eo<T, N>(h.S, false, tab.eS);
+  fill_eo<T, N>(h.S, true, tab.eSt);
+  fill_eo<T, N>(h.Dc, false, tab.eD);
+  fill_eo<T, N>(h.Dc, true, tab.eDt);
+  fill_eo<T, N>(h.M, false, tab.eM);
+  fill_eo<T, N>(h.K, false, tab.eK);
   for (int q = 0; q < N; ++q) {
     tab.W[q] = host_from_double<T>(h.qw[q]);
     for (int i = 0; i < N; ++i) {
