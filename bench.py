@@ -295,6 +295,54 @@ def profile_cg(args):
     mf.mf_mesh_destroy(mesh)
 
 
+def dss_ablation(args):
+    """Sec. 6 ablations: the deterministic layer-disjoint duplicate summation against an
+    atomic one (one line per case), and the apply's launch variants (cells per CTA and
+    resident CTAs per SM)."""
+    import torch
+
+    import paper_2609_04534_gb300 as mf
+
+    stream = torch.cuda.Stream()
+    s = stream.cuda_stream
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for N, k, geom, prec in ((64, 4, "curved", "fp64"), (64, 3, "curved", "fp64"), (64, 4, "curved", "fp32"),
+                             (123, 2, "affine", "fp64")):
+        g = mf.MF_CURVED_SIN if geom == "curved" else mf.MF_AFFINE
+        p = {"fp64": mf.MF_FP64, "fp32": mf.MF_FP32}[prec]
+        dt = torch.float64 if p == mf.MF_FP64 else torch.float32
+        mesh, op, info, ws = make_op(mf, torch, N, k, g, mf.MF_LAPLACE, p, 0, s)
+        with torch.cuda.stream(stream):
+            x = random_native(mf, torch, op, info, N, k, 1, dt, s)
+            y = torch.empty_like(x)
+            sc = torch.empty(mf.mf_dss_atomic_workspace_bytes(op), dtype=torch.uint8, device="cuda")
+        mf.mf_apply_split(op, x.data_ptr(), y.data_ptr(), s)
+        out = {"case": f"Q{k} {geom} {N}^3 {prec}", "n_cellwise": info["n_cellwise"], "n_unique": info["n_unique"]}
+        for name, fn in (("sweep_dss_ms", lambda: mf.mf_dss(op, y.data_ptr(), s)),
+                         ("atomic_dss_ms", lambda: mf.mf_dss_atomic(op, y.data_ptr(), sc.data_ptr(), sc.numel(), s))):
+            for _ in range(3):
+                fn()
+            stream.synchronize()
+            ev[0].record(stream)
+            for _ in range(args.reps):
+                fn()
+            ev[1].record(stream)
+            ev[1].synchronize()
+            out[name] = round(ev[0].elapsed_time(ev[1]) / args.reps, 4)
+        out["atomic_over_sweep"] = round(out["atomic_dss_ms"] / out["sweep_dss_ms"], 3)
+        variants = {}
+        for v in (0, 1, 2):
+            mf.mf_operator_set_variant(op, v)
+            t = time_apply(mf, torch, op, x, y, stream, args.reps, 2)
+            variants[f"variant{v}"] = {"apply_ms": round(t * 1e3, 4), "gdofs": round(info["n_cellwise"] / t / 1e9, 3)}
+        out["apply_variants"] = variants
+        print(json.dumps(out), flush=True)
+        mf.mf_operator_destroy(op)
+        mf.mf_mesh_destroy(mesh)
+        del ws, x, y, sc
+        torch.cuda.empty_cache()
+
+
 def solve_run(args):
     """Mixed-precision Poisson solve: Q4 on the curved N^3 mesh (default 96^3), manufactured
     u = sin(2 pi x) sin(2 pi y) sin(2 pi z), FP32 apply inside FP64 defect correction to
@@ -421,6 +469,8 @@ def main():
                     help="only run a few applies of one case (for ncu), e.g. 32,4,curved,fp64,laplace")
     ap.add_argument("--profile-cg", default=None, metavar="N,k,geom,prec",
                     help="only run --reps CG iterations of one case (for ncu), e.g. 48,4,curved,fp64")
+    ap.add_argument("--dss-ablation", action="store_true",
+                    help="only time the sweep vs atomic duplicate summation and the apply's launch variants")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--variant", type=int, default=-1, help="--profile-apply: launch variant (-1: all)")
     ap.add_argument("--serve", type=int, default=0, metavar="NREQ",
@@ -437,6 +487,9 @@ def main():
         return
     if args.profile_cg:
         profile_cg(args)
+        return
+    if args.dss_ablation:
+        dss_ablation(args)
         return
     if args.solve:
         solve_run(args)

@@ -142,6 +142,14 @@ mf_status mf_apply(const mf_operator* op, const void* x_dev, void* y_dev, void* 
 mf_status mf_apply_split(const mf_operator* op, const void* x_dev, void* y_dev, void* stream);
 /* In-place duplicate summation y <- G G^T y (and P y for Dirichlet). */
 mf_status mf_dss(const mf_operator* op, void* y_dev, void* stream);
+/* Ablation of the duplicate summation (a measurement entry; the paper compares its layer-
+ * disjoint sweeps against an atomic variant in Sec. 6): every copy atomically adds its value
+ * into an accumulator over unique nodes (scratch: mf_dss_atomic_workspace_bytes() device
+ * bytes, 256-byte aligned), then every copy reads the sum back.  Consistent, but the order of
+ * the atomic additions -- hence the last bits of the sums -- is not reproducible.  Same
+ * precision as the operator's vectors; P y for Dirichlet. */
+size_t mf_dss_atomic_workspace_bytes(const mf_operator* op);
+mf_status mf_dss_atomic(const mf_operator* op, void* y_dev, void* scratch_dev, size_t scratch_bytes, void* stream);
 /* End to end from host memory: copies canonical x_host to the device, applies, copies the
  * canonical result to y_host and synchronises `stream`.  Uses the caller's device
  * workspace of >= mf_apply_host_workspace_bytes() bytes. */

@@ -123,6 +123,9 @@ def lib() -> C.CDLL:
     L.mf_cg_record_history.argtypes = [vp, i32]
     L.mf_cg_solve_ex.argtypes = [vp, vp, vp, d, i32, i32, C.POINTER(mf_solve_options), C.POINTER(mf_solve_stats),
                                  vp, sz, vp]
+    L.mf_dss_atomic_workspace_bytes.argtypes = [vp]
+    L.mf_dss_atomic_workspace_bytes.restype = sz
+    L.mf_dss_atomic.argtypes = [vp, vp, vp, sz, vp]
     L.mf_cg_profile.argtypes = [vp, vp, vp, i32, i32, vp, sz, vp, C.POINTER(C.c_double)]
     L.mf_server_create.argtypes = [C.POINTER(mf_server_config), vp, sz, C.POINTER(vp)]
     L.mf_batch_submit.argtypes = [vp, C.POINTER(mf_request), C.POINTER(C.c_uint64)]
@@ -276,6 +279,14 @@ def mf_cg_solve(op, b_ptr: int, x_ptr: int, rtol: float, maxit: int, mixed: int,
     out = {f: getattr(st, f) for f, _ in mf_solve_stats._fields_}
     out["code"] = code
     return out
+
+
+def mf_dss_atomic_workspace_bytes(op) -> int:
+    return int(lib().mf_dss_atomic_workspace_bytes(op))
+
+
+def mf_dss_atomic(op, y_ptr: int, scratch_ptr: int, nbytes: int, stream: int = 0) -> None:
+    _check(lib().mf_dss_atomic(op, y_ptr, scratch_ptr, nbytes, stream or None))
 
 
 def mf_cg_profile(op, b_ptr: int, x_ptr: int, iterations: int, cg_form: int, workspace_ptr: int, nbytes: int,

@@ -280,6 +280,19 @@ mf_status mf_dss(const mf_operator* op, void* y_dev, void* stream) {
   return launch_dss(op, elem_of(op), y_dev, static_cast<cudaStream_t>(stream));
 }
 
+size_t mf_dss_atomic_workspace_bytes(const mf_operator* op) {
+  return op ? (size_t)op->n_unique * (size_t)elem_of(op) : 0;
+}
+
+mf_status mf_dss_atomic(const mf_operator* op, void* y_dev, void* scratch_dev, size_t scratch_bytes, void* stream) {
+  if (!op || !y_dev) return set_error(MF_ERR_ARG, "mf_dss_atomic: NULL argument");
+  if (!scratch_dev || scratch_bytes < mf_dss_atomic_workspace_bytes(op))
+    return set_error(MF_ERR_OOM, "mf_dss_atomic: scratch %zu < %zu bytes", scratch_bytes,
+                     mf_dss_atomic_workspace_bytes(op));
+  if (reinterpret_cast<uintptr_t>(scratch_dev) & 255) return set_error(MF_ERR_ARG, "mf_dss_atomic: scratch alignment");
+  MF_DISPATCH_N(op->n, dss_atomic_n, op, elem_of(op), y_dev, scratch_dev, static_cast<cudaStream_t>(stream));
+}
+
 mf_status mf_apply(const mf_operator* op, const void* x_dev, void* y_dev, void* stream) {
   mf_status st = mf_apply_split(op, x_dev, y_dev, stream);
   if (st) return st;

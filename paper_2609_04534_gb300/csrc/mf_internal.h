@@ -200,6 +200,8 @@ mf_status apply_cg_n(const mf_operator* op, int vk, void* p, const void* r, void
 template <int N>
 mf_status dss_n(const mf_operator* op, int elem, void* y, cudaStream_t s);
 template <int N>
+mf_status dss_atomic_n(const mf_operator* op, int elem, void* y, void* acc, cudaStream_t s);
+template <int N>
 mf_status apply_batch_fill_n(const BatchMember* m, int n, int vk, void* jobs_host, long long* block0_host);
 template <int N>
 mf_status apply_batch_launch_n(const mf_operator* op0, int vk, const void* jobs_dev, const long long* block0_dev,

@@ -610,6 +610,60 @@ __global__ void dss_kernel(T* __restrict__ y, GridInfo g) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Atomic duplicate summation (ablation of dss_kernel): pass 1 adds every copy into its
+// unique node's accumulator with atomicAdd; pass 2 writes the accumulated sum (zero on the
+// Dirichlet boundary) back to every copy.  One thread per native element in both passes.
+// ---------------------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ bool unique_of(const GridInfo& g, long long e, long long* I, bool* bnd) {
+  constexpr int K = N - 1, N2 = N * N, N3 = N2 * N;
+  const int lane = (int)(e % BL);
+  const int l = (int)((e / BL) % N3);
+  const long long t = e / ((long long)BL * N3);
+  int cx, cy, cz;
+  cell_of(g, t, lane, cx, cy, cz);
+  if (cx >= g.nx || cy >= g.ny || cz >= g.nz) return false;
+  const long long NX = (long long)g.nx * K + 1, NY = (long long)g.ny * K + 1, NZ = (long long)g.nz * K + 1;
+  const long long gi = (long long)cx * K + l % N, gj = (long long)cy * K + (l / N) % N, gk = (long long)cz * K + l / N2;
+  *I = gi + NX * (gj + NY * gk);
+  *bnd = g.bc && (gi == 0 || gi == NX - 1 || gj == 0 || gj == NY - 1 || gk == 0 || gk == NZ - 1);
+  return true;
+}
+template <typename T, int N>
+__global__ void dss_atomic_add_kernel(const T* __restrict__ y, T* __restrict__ acc, GridInfo g, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    long long I;
+    bool bnd;
+    if (unique_of<N>(g, e, &I, &bnd) && !bnd) atomicAdd(&acc[I], y[e]);
+  }
+}
+template <typename T, int N>
+__global__ void dss_atomic_read_kernel(T* __restrict__ y, const T* __restrict__ acc, GridInfo g, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    long long I;
+    bool bnd;
+    if (unique_of<N>(g, e, &I, &bnd)) y[e] = bnd ? T(0) : acc[I];
+  }
+}
+template <int N>
+mf_status dss_atomic_n(const mf_operator* op, int elem, void* y, void* acc, cudaStream_t s) {
+  const long long n = op->n_native;
+  const int thr = 256;
+  long long blocks = (n + thr - 1) / thr;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  mf_status st = cuda_check(cudaMemsetAsync(acc, 0, (size_t)op->n_unique * elem, s), "dss atomic clear");
+  if (st) return st;
+  if (elem == 8) {
+    dss_atomic_add_kernel<double, N><<<(unsigned)blocks, thr, 0, s>>>((const double*)y, (double*)acc, op->g, n);
+    dss_atomic_read_kernel<double, N><<<(unsigned)blocks, thr, 0, s>>>((double*)y, (const double*)acc, op->g, n);
+  } else {
+    dss_atomic_add_kernel<float, N><<<(unsigned)blocks, thr, 0, s>>>((const float*)y, (float*)acc, op->g, n);
+    dss_atomic_read_kernel<float, N><<<(unsigned)blocks, thr, 0, s>>>((float*)y, (const float*)acc, op->g, n);
+  }
+  return cuda_check(cudaGetLastError(), "dss atomic launch");
+}
+
+// ---------------------------------------------------------------------------------------
 // Per-point geometry of the curved map (Sec. 2: six metric entries plus det J per point):
 // G = w |det J| J^-1 J^-T (xx,xy,xz,yy,yz,zz) and, for Helmholtz, m = w |det J| c_m, computed
 // in FP64 from the analytic Jacobian and stored in T, layout [tile][comp][l][lane].
@@ -1033,6 +1087,7 @@ mf_status layout_n(const mf_operator* op, int elem, int mode, const void* in, vo
   template mf_status apply_cg_n<NN>(const mf_operator*, int, void*, const void*, void*, CgState*, double*, \
                                     int, long long*, cudaStream_t);                                     \
   template mf_status dss_n<NN>(const mf_operator*, int, void*, cudaStream_t);                           \
+  template mf_status dss_atomic_n<NN>(const mf_operator*, int, void*, void*, cudaStream_t);              \
   template mf_status apply_batch_fill_n<NN>(const BatchMember*, int, int, void*, long long*);            \
   template mf_status apply_batch_launch_n<NN>(const mf_operator*, int, const void*, const long long*, int,  \
                                               long long, cudaStream_t);                                 \

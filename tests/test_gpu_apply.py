@@ -261,3 +261,29 @@ def test_launch_variants_agree_bitwise_and_autotune(k, geom, prec):
     assert v in (0, 1, 2)
     assert torch.equal(d.apply(xn), y0)
     d.close()
+
+
+@pytest.mark.parametrize("prec,dims,k,bc", [(mf.MF_FP64, (7, 6, 5), 3, 0), (mf.MF_FP64, (5, 9, 4), 5, 1),
+                                             (mf.MF_FP32, (6, 5, 7), 4, 1)])
+def test_atomic_dss_ablation_matches_sweep_dss(prec, dims, k, bc):
+    """The atomic duplicate summation (ablation entry) gives the sweep's sums up to the order
+    of the additions, and a consistent vector."""
+    d = DevOp(*dims, k, "curved", mf.MF_LAPLACE, 1.0, prec, bc)
+    x = d.native_from_unique(inputs.random_unique(*dims, k, 41))
+    ys = d.apply(x, split=True)
+    y_sweep = ys.clone()
+    mf.mf_dss(d.op, y_sweep.data_ptr())
+    y_atomic = ys.clone()
+    sc = torch.empty(max(mf.mf_dss_atomic_workspace_bytes(d.op), 256), dtype=torch.uint8, device="cuda")
+    mf.mf_dss_atomic(d.op, y_atomic.data_ptr(), sc.data_ptr(), sc.numel())
+    torch.cuda.synchronize()
+    a, b = y_atomic.double().cpu().numpy(), y_sweep.double().cpu().numpy()
+    tol = 1e-6 if prec == mf.MF_FP32 else 1e-14
+    assert np.abs(a - b).max() <= tol * np.abs(b).max()
+    u = torch.empty(d.n_unique, dtype=d.dtype, device="cuda")
+    mf.mf_gather_unique(d.op, y_atomic.data_ptr(), u.data_ptr())
+    back = torch.empty_like(y_atomic)
+    mf.mf_scatter_unique(d.op, u.data_ptr(), back.data_ptr())
+    torch.cuda.synchronize()
+    assert torch.equal(back, y_atomic)
+    d.close()
