@@ -57,7 +57,7 @@ mf_status apply_batch_launch(const mf_operator* op0, int vk, const void* jobs_de
 }
 size_t apply_job_bytes(int vk) {
   // the description layout depends only on the element types, not on the degree
-  return vk == VK_F32 ? sizeof(ApplyJob<float, float>)
+  return vk == VK_F32 ? sizeof(ApplyJob<float, FP32C>)
                       : (vk == VK_DDS ? sizeof(ApplyJob<dd, dd>)
                                       : (vk == VK_DD ? sizeof(ApplyJob<double, dd>) : sizeof(ApplyJob<double, double>)));
 }

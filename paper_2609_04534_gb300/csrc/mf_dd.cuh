@@ -107,6 +107,50 @@ __device__ __forceinline__ double f2d_bits(float f) {
 // dd -> double: exact sum of the two parts (one FP64 add).
 __device__ __forceinline__ double dd_to_double(dd a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
 
+// Two FP32 values of neighbouring cells processed by one thread (the FP32 apply): every
+// operation acts on both lanes; table coefficients stay scalar floats.
+struct __align__(8) f2 {
+  float x, y;
+  __host__ __device__ f2() {}
+  __host__ __device__ constexpr f2(float a, float b) : x(a), y(b) {}
+  __host__ __device__ explicit constexpr f2(int v) : x((float)v), y((float)v) {}
+};
+__device__ __forceinline__ f2 fma(float c, f2 a, f2 b) { return f2(fmaf(c, a.x, b.x), fmaf(c, a.y, b.y)); }
+__device__ __forceinline__ f2 fma(f2 c, f2 a, f2 b) { return f2(fmaf(c.x, a.x, b.x), fmaf(c.y, a.y, b.y)); }
+__device__ __forceinline__ f2 mul0(float c, f2 a) { return f2(c * a.x, c * a.y); }
+__device__ __forceinline__ f2 mul0(f2 c, f2 a) { return f2(c.x * a.x, c.y * a.y); }
+__device__ __forceinline__ f2 finish(f2 a) { return a; }
+__device__ __forceinline__ f2 operator*(float c, f2 a) { return f2(c * a.x, c * a.y); }
+__device__ __forceinline__ f2 operator*(f2 c, f2 a) { return f2(c.x * a.x, c.y * a.y); }
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ f2 operator-(f2 a) { return f2(-a.x, -a.y); }
+
+// Coefficient type of the 1D tables for a compute type, and cells per compute value.
+template <typename T>
+struct CoefOf { using type = T; };
+template <>
+struct CoefOf<f2> { using type = float; };
+template <typename T>
+struct CellsPer { static constexpr int value = 1; };
+template <>
+struct CellsPer<f2> { static constexpr int value = 2; };
+template <typename T>
+struct IsF32 { static constexpr bool value = false; };
+template <>
+struct IsF32<float> { static constexpr bool value = true; };
+template <>
+struct IsF32<f2> { static constexpr bool value = true; };
+
+// Compute type of the FP32 view: pairs of cells per thread (MF_FP32_PAIRS=0: one cell).
+#ifndef MF_FP32_PAIRS
+#define MF_FP32_PAIRS 1
+#endif
+#if MF_FP32_PAIRS
+using FP32C = f2;
+#else
+using FP32C = float;
+#endif
+
 // A double scalar (a CG coefficient) in a vector element type.
 template <typename S>
 __device__ __forceinline__ S scalar_from_double(double v) { return (S)v; }
@@ -127,6 +171,8 @@ __device__ __forceinline__ double to_storage<double, dd>(dd v) { return dd_to_do
 // host: double -> compute type
 template <typename C>
 inline C host_from_double(double v) { return (C)v; }
+template <>
+inline f2 host_from_double<f2>(double v) { return f2((float)v, (float)v); }
 template <>
 inline dd host_from_double<dd>(double v) {
   const float h = (float)v;

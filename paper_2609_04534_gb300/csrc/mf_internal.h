@@ -14,6 +14,9 @@
 
 namespace mf {
 
+template <typename T>
+struct CoefOf; // coefficient type of the 1D tables for a compute type (mf_dd.cuh)
+
 constexpr int TX = 4, TY = 4, TZ = 2, BL = TX * TY * TZ;
 constexpr int MAXN = 9;
 
@@ -104,21 +107,22 @@ struct ApplyJob {
   float amp, cm, h[3];
   CgFuse<S> cg; // cg.st == nullptr: plain apply
   // L2 prefetch distance in tiles (about one wave of resident CTAs ahead; 0 = off): the first
-  // CTA of tile t prefetches the input and geometry of tile t + pf_tiles
-  int pf_tiles;
+  // CTA of tile t prefetches the input and geometry of tile t + pf_tiles; pf_geom = 1 only
+  // when geom is a streamed per-point metric of this operator's full tile range
+  int pf_tiles, pf_geom;
 };
 
 template <typename S, typename T, int N>
 struct ApplyArgs {
   ApplyJob<S, T> j;
-  Tab<T, N> tab;
+  Tab<typename CoefOf<T>::type, N> tab;
 };
 
 // A batched apply over several requests of one degree, path and precision: CTA b belongs to
 // job i with block0[i] <= b < block0[i + 1] and runs that job's CTA b - block0[i].
 template <typename S, typename T, int N>
 struct ApplyBatch {
-  Tab<T, N> tab;
+  Tab<typename CoefOf<T>::type, N> tab;
   const ApplyJob<S, T>* jobs;
   const long long* block0; // njobs + 1 entries
   int njobs;

@@ -21,13 +21,18 @@ namespace mf {
 // (Staging the streamed geometry into shared memory with cp.async was measured and lost:
 // the 2-CTA configuration already hides its load latency.)
 constexpr int MF_NUM_VARIANTS = 3;
+// CB counts compute values per pencil position: cells for double / dd / float, cell pairs for
+// the FP32 pair type f2 (CPL cells per value); a CTA holds CB * CPL cells.
 template <typename T, int N, int V>
 struct Cfg {
-  static constexpr int CB0 = (N <= 4) ? 32 : (N <= 6) ? 16 : (N <= 8) ? 8 : (sizeof(T) == 4 ? 8 : 4);
-  static constexpr int CB = V == 0 ? CB0 : ((CB0 / 2) >= 4 ? (CB0 / 2) : 4);
+  static constexpr int CPL = CellsPer<T>::value;
+  static constexpr int CELLS0 = (N <= 4) ? 32 : (N <= 6) ? 16 : (N <= 8) ? 8 : (IsF32<T>::value ? 8 : 4);
+  static constexpr int CB0 = CELLS0 / CPL;
+  static constexpr int CBH = (CB0 / 2) * CPL >= 4 ? CB0 / 2 : 4 / CPL;
+  static constexpr int CB = V == 0 ? CB0 : CBH;
   static constexpr int MINB = V == 0 ? 2 : (V == 1 ? 3 : 1);
   static constexpr int NT = N * N * CB;
-  static_assert(CB >= 4 && BL % CB == 0, "a CTA holds at least 4 cells of a tile (apply_max_blocks)");
+  static_assert(CB * CPL >= 4 && BL % (CB * CPL) == 0, "a CTA holds at least 4 cells of a tile (apply_max_blocks)");
 };
 
 __device__ __forceinline__ void cell_of(const GridInfo& g, long long t64, int lane, int& cx, int& cy, int& cz) {
@@ -72,6 +77,7 @@ struct NoAcc {
 __device__ __forceinline__ double to_double(double v) { return v; }
 __device__ __forceinline__ double to_double(float v) { return (double)v; }
 __device__ __forceinline__ double to_double(dd v) { return dd_to_double(v); }
+__device__ __forceinline__ double to_double(f2 v) { return (double)v.x + (double)v.y; }
 
 // Bulk prefetch of [p, p + bytes) into L2 (16-byte aligned, size a multiple of 16), split into
 // 16 KB requests over the lanes of the calling warp.
@@ -96,7 +102,7 @@ __device__ __forceinline__ void prefetch_next_wave(const ApplyJob<S, T>& a, long
   const unsigned long long xb = (unsigned long long)N3 * BL * sizeof(S);
   prefetch_l2_warp(xin + tn * (long long)N3 * BL, xb);
   if (a.cg.st != nullptr && a.cg.update_p) prefetch_l2_warp(a.cg.r + tn * (long long)N3 * BL, xb);
-  if (NC > 0 && a.geom != nullptr) {
+  if (NC > 0 && a.pf_geom && a.geom != nullptr) {
     const unsigned long long gb = (unsigned long long)NC * N3 * BL * sizeof(T);
     prefetch_l2_warp(a.geom + tn * (long long)NC * N3 * BL, gb);
   }
@@ -116,13 +122,15 @@ __device__ __forceinline__ float add_lazy(float a, float b) { return a + b; }
 __device__ __forceinline__ float sub_lazy(float a, float b) { return a - b; }
 
 // sum_i c[i] x[i], i < M (M >= 1), not renormalised
-template <typename T, int M>
-__device__ __forceinline__ T chain(const T* c, const T* x) {
+template <typename C, typename T, int M>
+__device__ __forceinline__ T chain(const C* c, const T* x) {
   T s = mul0(c[0], x[0]);
 #pragma unroll
   for (int i = 1; i < M; ++i) s = fma(c[i], x[i], s);
   return s;
 }
+__device__ __forceinline__ f2 add_lazy(f2 a, f2 b) { return f2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ f2 sub_lazy(f2 a, f2 b) { return f2(a.x - b.x, a.y - b.y); }
 
 // Even-odd 1D contraction of one pencil (see EoTab): the pencil folded into its sum and
 // difference halves, H (H + 1) products per half instead of n^2 in all.  ANTI: the matrix is
@@ -139,24 +147,26 @@ struct Fold {
     }
     if (N % 2) e[H] = in[H];
   }
-  __device__ __forceinline__ void apply(const EoTab<T, N>& t, T* out) const {
+  template <typename C>
+  __device__ __forceinline__ void apply(const EoTab<C, N>& t, T* out) const {
 #pragma unroll
     for (int q = 0; q < H; ++q) {
-      const T u = chain<T, HE>(t.F + q * HE, e);
-      const T w = chain<T, H>(t.G + q * H, o);
+      const T u = chain<C, T, HE>(t.F + q * HE, e);
+      const T w = chain<C, T, H>(t.G + q * H, o);
       out[q] = finish(add_lazy(u, w));
       out[N - 1 - q] = finish(ANTI ? sub_lazy(w, u) : sub_lazy(u, w));
     }
-    if (N % 2) out[H] = finish(ANTI ? chain<T, H>(t.Mid, o) : chain<T, HE>(t.Mid, e));
+    if (N % 2) out[H] = finish(ANTI ? chain<C, T, H>(t.Mid, o) : chain<C, T, HE>(t.Mid, e));
   }
 };
 
-// Load the CB cells [lane0, lane0+CB) of tile t into smem as buf[l*CB + c] (cell fastest),
-// zeroing padding cells and, for Dirichlet, the constrained nodes (the P of P A P).  In a
-// CG step with update_p the loaded vector is the new direction p = r + beta p, written back.
+// Load the CB values (CB * CPL cells from lane0) of tile t into smem as buf[l*CB + c] (cell
+// fastest; a pair value holds cells lane0 + 2c and lane0 + 2c + 1), zeroing padding cells and,
+// for Dirichlet, the constrained nodes (the P of P A P).  In a CG step with update_p the loaded
+// vector is the new direction p = r + beta p, written back.
 template <typename S, typename T, int N, int CB, int NT>
 __device__ __forceinline__ void load_tile(const ApplyJob<S, T>& a, long long t, int lane0, T* buf) {
-  constexpr int N2 = N * N, N3 = N2 * N;
+  constexpr int N2 = N * N, N3 = N2 * N, CPL = CellsPer<T>::value;
   const long long base = t * (long long)N3 * BL + lane0;
   const bool fuse = a.cg.st != nullptr && a.cg.update_p;
   const S beta = fuse ? scalar_from_double<S>(a.cg.st->beta) : S(0);
@@ -165,48 +175,96 @@ __device__ __forceinline__ void load_tile(const ApplyJob<S, T>& a, long long t, 
 #pragma unroll
   for (int idx = threadIdx.x; idx < N3 * CB; idx += NT) {
     const int l = idx / CB, c = idx - l * CB;
-    const long long e = base + (long long)l * BL + c;
-    int cx, cy, cz;
-    cell_of(a.g, t, lane0 + c, cx, cy, cz);
-    T v = T(0);
-    if (cx < a.g.nx && cy < a.g.ny && cz < a.g.nz) {
-      S xv;
-      if (fuse) {
-        xv = finish(fma(beta, pg[e], rg[e]));
-        pg[e] = xv;
-      } else {
-        xv = a.x[e];
+    const long long e = base + (long long)l * BL + c * CPL;
+    if constexpr (CPL == 1) {
+      int cx, cy, cz;
+      cell_of(a.g, t, lane0 + c, cx, cy, cz);
+      T v = T(0);
+      if (cx < a.g.nx && cy < a.g.ny && cz < a.g.nz) {
+        S xv;
+        if (fuse) {
+          xv = finish(fma(beta, pg[e], rg[e]));
+          pg[e] = xv;
+        } else {
+          xv = a.x[e];
+        }
+        v = to_compute<T, S>(xv);
+        if (a.g.bc) {
+          const int i = l % N, j = (l / N) % N, k = l / N2;
+          if (on_cube_boundary<N>(a.g, cx, cy, cz, i, j, k)) v = T(0);
+        }
+      } else if (fuse) {
+        pg[e] = S(0);
       }
-      v = to_compute<T, S>(xv);
+      buf[idx] = v;
+    } else { // a pair of cells (FP32): 8-byte accesses
+      int cx, cy, cz;
+      cell_of(a.g, t, lane0 + 2 * c, cx, cy, cz); // the second cell is at cx + 1
+      const bool yz = cy < a.g.ny && cz < a.g.nz;
+      const bool v0 = yz && cx < a.g.nx, v1 = yz && cx + 1 < a.g.nx;
+      float2 xv;
+      if (fuse) {
+        const float2 pv = *reinterpret_cast<const float2*>(pg + e);
+        const float2 rv = *reinterpret_cast<const float2*>(rg + e);
+        xv.x = v0 ? fmaf(beta, pv.x, rv.x) : 0.0f;
+        xv.y = v1 ? fmaf(beta, pv.y, rv.y) : 0.0f;
+        *reinterpret_cast<float2*>(pg + e) = xv;
+      } else {
+        xv = *reinterpret_cast<const float2*>(a.x + e);
+      }
+      float vx = v0 ? xv.x : 0.0f, vy = v1 ? xv.y : 0.0f;
       if (a.g.bc) {
         const int i = l % N, j = (l / N) % N, k = l / N2;
-        if (on_cube_boundary<N>(a.g, cx, cy, cz, i, j, k)) v = T(0);
+        if (v0 && on_cube_boundary<N>(a.g, cx, cy, cz, i, j, k)) vx = 0.0f;
+        if (v1 && on_cube_boundary<N>(a.g, cx + 1, cy, cz, i, j, k)) vy = 0.0f;
       }
-    } else if (fuse) {
-      pg[e] = S(0);
+      buf[idx] = T(vx, vy);
     }
-    buf[idx] = v;
   }
 }
 
-// Store one x-pencil (j, k) of cell c to global y, zeroing padding / constrained nodes.  In a
-// fused CG step each stored value is also paired with p (acc += p y over real copies).
+// Store one x-pencil (j, k) of value c to global y, zeroing padding / constrained nodes.  In a
+// CG step each stored value is also paired with p (acc += p y over real copies); pv holds p
+// of the pencil, CPL values per node.
 template <typename S, typename T, int N, int CB, typename Acc>
 __device__ __forceinline__ void store_xpencil(const ApplyJob<S, T>& a, long long t, int lane0, int c, int j, int k,
                                               const T* out, Acc& acc, const S* pv) {
-  constexpr int N2 = N * N, N3 = N2 * N;
+  constexpr int N2 = N * N, N3 = N2 * N, CPL = CellsPer<T>::value;
   int cx, cy, cz;
-  cell_of(a.g, t, lane0 + c, cx, cy, cz);
-  const bool valid = cx < a.g.nx && cy < a.g.ny && cz < a.g.nz;
-  const long long base = t * (long long)N3 * BL + lane0 + c;
+  cell_of(a.g, t, lane0 + c * CPL, cx, cy, cz);
+  const long long base = t * (long long)N3 * BL + lane0 + c * CPL;
+  if constexpr (CPL == 1) {
+    const bool valid = cx < a.g.nx && cy < a.g.ny && cz < a.g.nz;
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    S v = valid ? to_storage<S, T>(out[i]) : S(0);
-    if (valid && a.g.bc && on_cube_boundary<N>(a.g, cx, cy, cz, i, j, k)) v = S(0);
-    const long long e = base + (long long)(i + N * j + N2 * k) * BL;
-    a.y[e] = v;
-    if constexpr (Acc::active) {
-      if (a.cg.st != nullptr && valid) acc.add(pv[i], v);
+    for (int i = 0; i < N; ++i) {
+      S v = valid ? to_storage<S, T>(out[i]) : S(0);
+      if (valid && a.g.bc && on_cube_boundary<N>(a.g, cx, cy, cz, i, j, k)) v = S(0);
+      const long long e = base + (long long)(i + N * j + N2 * k) * BL;
+      a.y[e] = v;
+      if constexpr (Acc::active) {
+        if (a.cg.st != nullptr && valid) acc.add(pv[i], v);
+      }
+    }
+  } else {
+    const bool yz = cy < a.g.ny && cz < a.g.nz;
+    const bool v0 = yz && cx < a.g.nx, v1 = yz && cx + 1 < a.g.nx;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      float2 v;
+      v.x = v0 ? out[i].x : 0.0f;
+      v.y = v1 ? out[i].y : 0.0f;
+      if (a.g.bc) {
+        if (v0 && on_cube_boundary<N>(a.g, cx, cy, cz, i, j, k)) v.x = 0.0f;
+        if (v1 && on_cube_boundary<N>(a.g, cx + 1, cy, cz, i, j, k)) v.y = 0.0f;
+      }
+      const long long e = base + (long long)(i + N * j + N2 * k) * BL;
+      *reinterpret_cast<float2*>(a.y + e) = v;
+      if constexpr (Acc::active) {
+        if (a.cg.st != nullptr) {
+          if (v0) acc.add(pv[2 * i], v.x);
+          if (v1) acc.add(pv[2 * i + 1], v.y);
+        }
+      }
     }
   }
 }
@@ -234,7 +292,8 @@ __device__ __forceinline__ void cta_partial_after_barrier(const double* red, dou
 // One CTA: cells [lane0, lane0 + CB) of tile t; cta = the CTA's index in its operator's grid
 // (where its CG partial goes).
 template <typename S, typename T, int N, int CB, bool HELM>
-__device__ __forceinline__ void cartesian_body(const ApplyJob<S, T>& a, const Tab<T, N>& tab, long long t, int lane0,
+__device__ __forceinline__ void cartesian_body(const ApplyJob<S, T>& a, const Tab<typename CoefOf<T>::type, N>& tab,
+                                               long long t, int lane0,
                                                long long cta) {
   constexpr int N2 = N * N, N3 = N2 * N, NT = N2 * CB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -298,11 +357,14 @@ __device__ __forceinline__ void cartesian_body(const ApplyJob<S, T>& a, const Ta
   PairAcc<S> acc;
   { // write out as x-pencils (j=pa, k=pb) so the Dirichlet mask indexes match; a fused CG step
     // pairs each stored value with p (this CTA wrote p during the load, before the barriers)
-    S pv[N];
+    constexpr int CPL = CellsPer<T>::value;
+    S pv[N * CPL];
     if (a.cg.st != nullptr) {
-      const S* __restrict__ pg = (a.cg.update_p ? a.cg.p : a.x) + t * (long long)N3 * BL + lane0 + c;
+      const S* __restrict__ pg = (a.cg.update_p ? a.cg.p : a.x) + t * (long long)N3 * BL + lane0 + c * CPL;
 #pragma unroll
-      for (int i = 0; i < N; ++i) pv[i] = pg[(long long)(i + N * pa + N2 * pb) * BL];
+      for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) pv[i * CPL + j] = pg[(long long)(i + N * pa + N2 * pb) * BL + j];
     }
     T o[N];
 #pragma unroll
@@ -317,6 +379,36 @@ __device__ __forceinline__ void cartesian_body(const ApplyJob<S, T>& a, const Ta
   }
 }
 
+// The metric of the FP32 curved view at one Gauss point of one cell, computed from the sin
+// and cos of pi xh per direction: the map x = xh + amp s(xh) (1,1,1) has J = (I + u v^T) D
+// with u = amp (1,1,1), v = grad s, D = diag(h); Sherman-Morrison gives J^-1 = D^-1 (I - u v^T
+// / beta), beta = 1 + v.u, and J^-1 J^-T = D^-1 (I - (u v^T + v u^T)/beta + |v|^2 u u^T /
+// beta^2) D^-1.  g[0..5] = w |det J| J^-1 J^-T (xx, xy, xz, yy, yz, zz), g[6] = w |det J| c_m.
+template <typename S, typename T>
+__device__ __forceinline__ void curved_metric_f32(float sx, float cxv, float sy, float cyv, float sz, float czv,
+                                                  float wq, const ApplyJob<S, T>& a, float* g) {
+  const float pi = 3.14159265358979f;
+  const float v1 = pi * cxv * sy * sz, v2 = pi * sx * cyv * sz, v3 = pi * sx * sy * czv;
+  const float beta = fmaf(a.amp, v1 + v2 + v3, 1.0f);
+  const float ib = 1.0f / beta;
+  const float au = a.amp * ib;
+  const float c2 = au * au * (v1 * v1 + v2 * v2 + v3 * v3);
+  const float wd = wq * (a.h[0] * a.h[1] * a.h[2]) * fabsf(beta);
+  const float i0 = 1.0f / a.h[0], i1 = 1.0f / a.h[1], i2 = 1.0f / a.h[2];
+  g[0] = wd * i0 * i0 * (1.0f - 2.0f * au * v1 + c2);
+  g[1] = wd * i0 * i1 * (c2 - au * (v1 + v2));
+  g[2] = wd * i0 * i2 * (c2 - au * (v1 + v3));
+  g[3] = wd * i1 * i1 * (1.0f - 2.0f * au * v2 + c2);
+  g[4] = wd * i1 * i2 * (c2 - au * (v2 + v3));
+  g[5] = wd * i2 * i2 * (1.0f - 2.0f * au * v3 + c2);
+  g[6] = wd * a.cm;
+}
+template <typename T>
+__device__ __forceinline__ T pack_lanes(const float (*g)[7], int m) {
+  if constexpr (CellsPer<T>::value == 2) return T(g[0][m], g[1][m]);
+  else return T(g[0][m]);
+}
+
 // ---------------------------------------------------------------------------------------
 // General cells (affine with a full metric, or curved with per-point geometry):
 // interpolate to Gauss points with S (three sweeps), reference gradients by the collocation
@@ -324,7 +416,8 @@ __device__ __forceinline__ void cartesian_body(const ApplyJob<S, T>& a, const Ta
 // m u), then the transposes: Dc^T per direction summed, and S^T along z, y, x.
 // ---------------------------------------------------------------------------------------
 template <typename S, typename T, int N, int CB, bool CURVED, bool HELM>
-__device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<T, N>& tab, long long t, int lane0,
+__device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<typename CoefOf<T>::type, N>& tab,
+                                             long long t, int lane0,
                                              long long cta) {
   constexpr int N2 = N * N, N3 = N2 * N, NT = N2 * CB;
   constexpr int NC = HELM ? 7 : 6;
@@ -333,11 +426,12 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
   T* buf1 = buf0 + N3 * CB;
   T* buf2 = buf1 + N3 * CB;
   if (a.cg.st != nullptr && a.cg.st->flag != 0) return; // CG step after convergence: no work
-  prefetch_next_wave<S, T, N, (CURVED && sizeof(T) != 4) ? NC : 0>(a, t, lane0);
+  // streamed geometry exists only for the FP64 views (the FP32 view computes its metric)
+  prefetch_next_wave<S, T, N, (CURVED && !IsF32<T>::value) ? NC : 0>(a, t, lane0);
   load_tile<S, T, N, CB, NT>(a, t, lane0, buf0);
   __syncthreads();
   const int c = threadIdx.x % CB, p = threadIdx.x / CB, pa = p % N, pb = p / N;
-  const T* Dc = tab.Dc;
+  const auto* Dc = tab.Dc;
   { // x-sweep with S, pencil (j=pa, k=pb), in place
     T in[N], out[N];
 #pragma unroll
@@ -373,22 +467,28 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
   // fluxes v = G grad u; v1 -> buf0, v2 -> buf2, v3 stays in registers (Helmholtz: m u too).
   // A fused CG step also sums grad u . v (+ m u^2): p_K^T A_K p_K of this pencil's points,
   // equal to the pairing of p with the split product written below (Lemma 1).
-  const long long gbase = (t * NC * (long long)N3) * BL + lane0 + c;
+  const long long gbase = (t * NC * (long long)N3) * BL + lane0 + c * CellsPer<T>::value;
   const bool fuse = a.cg.st != nullptr;
   T pap = T(0);
   // FP32 curved: sin / cos of pi xh at this thread's x and y points and at every z point of
-  // the cell's layer, loaded before the point loop
-  float sx = 0.f, cxv = 0.f, sy = 0.f, cyv = 0.f, szq[N], czq[N];
-  if constexpr (CURVED && sizeof(T) == 4) {
+  // the cell's layer, loaded before the point loop (per cell of the value: the cells of a
+  // pair are x-neighbours, so only the x tables differ)
+  constexpr int CPL = CellsPer<T>::value;
+  float sx[CPL], cxv[CPL], sy = 0.f, cyv = 0.f, szq[N], czq[N];
+  if constexpr (CURVED && IsF32<T>::value) {
     int ccx, ccy, ccz;
-    cell_of(a.g, t, lane0 + c, ccx, ccy, ccz);
-    ccx = min(ccx, a.g.nx - 1);
+    cell_of(a.g, t, lane0 + c * CPL, ccx, ccy, ccz);
     ccy = min(ccy, a.g.ny - 1);
     ccz = min(ccz, a.g.nz - 1);
-    const float* tx = a.gtab + 2 * (ccx * N + pa);
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) {
+      const float* tx = a.gtab + 2 * (min(ccx + j, a.g.nx - 1) * N + pa);
+      sx[j] = tx[0];
+      cxv[j] = tx[1];
+    }
     const float* ty = a.gtab + 2 * ((a.g.nx + ccy) * N + pb);
     const float* tz = a.gtab + 2 * ((a.g.nx + a.g.ny + ccz) * N);
-    sx = tx[0]; cxv = tx[1]; sy = ty[0]; cyv = ty[1];
+    sy = ty[0]; cyv = ty[1];
 #pragma unroll
     for (int q = 0; q < N; ++q) { szq[q] = tz[2 * q]; czq[q] = tz[2 * q + 1]; }
   }
@@ -404,26 +504,14 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
     }
     const T d1 = finish(s1), d2 = finish(s2);
     T g0, g1, g2, g3, g4, g5, m = T(0);
-    if constexpr (CURVED && sizeof(T) == 4) {
-      // x = xh + amp s(xh) (1,1,1): J = (I + u v^T) D with u = amp (1,1,1), v = grad s,
-      // D = diag(h).  Sherman-Morrison: J^-1 = D^-1 (I - u v^T / beta), beta = 1 + v.u, and
-      // J^-1 J^-T = D^-1 (I - (u v^T + v u^T)/beta + |v|^2 u u^T / beta^2) D^-1.
-      const float sz = szq[q], czv = czq[q];
-      const float pi = 3.14159265358979f;
-      const float v1 = pi * cxv * sy * sz, v2 = pi * sx * cyv * sz, v3 = pi * sx * sy * czv;
-      const float beta = fmaf(a.amp, v1 + v2 + v3, 1.0f);
-      const float ib = 1.0f / beta;
-      const float au = a.amp * ib;
-      const float c2 = au * au * (v1 * v1 + v2 * v2 + v3 * v3);
-      const float wd = tab.W[pa] * tab.W[pb] * tab.W[q] * (a.h[0] * a.h[1] * a.h[2]) * fabsf(beta);
-      const float i0 = 1.0f / a.h[0], i1 = 1.0f / a.h[1], i2 = 1.0f / a.h[2];
-      g0 = wd * i0 * i0 * (1.0f - 2.0f * au * v1 + c2);
-      g1 = wd * i0 * i1 * (c2 - au * (v1 + v2));
-      g2 = wd * i0 * i2 * (c2 - au * (v1 + v3));
-      g3 = wd * i1 * i1 * (1.0f - 2.0f * au * v2 + c2);
-      g4 = wd * i1 * i2 * (c2 - au * (v2 + v3));
-      g5 = wd * i2 * i2 * (1.0f - 2.0f * au * v3 + c2);
-      if (HELM) m = wd * a.cm;
+    if constexpr (CURVED && IsF32<T>::value) {
+      float gg[CPL][7];
+#pragma unroll
+      for (int j = 0; j < CPL; ++j)
+        curved_metric_f32(sx[j], cxv[j], sy, cyv, szq[q], czq[q], tab.W[pa] * tab.W[pb] * tab.W[q], a, gg[j]);
+      g0 = pack_lanes<T>(gg, 0); g1 = pack_lanes<T>(gg, 1); g2 = pack_lanes<T>(gg, 2);
+      g3 = pack_lanes<T>(gg, 3); g4 = pack_lanes<T>(gg, 4); g5 = pack_lanes<T>(gg, 5);
+      if (HELM) m = pack_lanes<T>(gg, 6);
     } else if (CURVED) {
       const T* gp = a.geom + gbase + (long long)l * BL;
       g0 = gp[0];
@@ -434,7 +522,7 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
       g5 = gp[(long long)5 * N3 * BL];
       if (HELM) m = gp[(long long)6 * N3 * BL];
     } else {
-      const T w = tab.W[pa] * tab.W[pb] * tab.W[q];
+      const auto w = tab.W[pa] * tab.W[pb] * tab.W[q];
       g0 = w * a.G[0]; g1 = w * a.G[1]; g2 = w * a.G[2];
       g3 = w * a.G[3]; g4 = w * a.G[4]; g5 = w * a.G[5];
       if (HELM) m = w * a.mdet;
@@ -506,13 +594,13 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
 // over the block offsets and copies the job's description into shared memory.
 template <typename S, typename T, int N, int CB, int MINB, bool HELM>
 __global__ void __launch_bounds__(N * N * CB, MINB) apply_cartesian(ApplyArgs<S, T, N> A) {
-  constexpr int GPT = BL / CB;
-  cartesian_body<S, T, N, CB, HELM>(A.j, A.tab, blockIdx.x / GPT, (blockIdx.x % GPT) * CB, blockIdx.x);
+  constexpr int CC = CB * CellsPer<T>::value, GPT = BL / CC; // cells per CTA, CTAs per tile
+  cartesian_body<S, T, N, CB, HELM>(A.j, A.tab, blockIdx.x / GPT, (blockIdx.x % GPT) * CC, blockIdx.x);
 }
 template <typename S, typename T, int N, int CB, int MINB, bool CURVED, bool HELM>
 __global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T, N> A) {
-  constexpr int GPT = BL / CB;
-  general_body<S, T, N, CB, CURVED, HELM>(A.j, A.tab, blockIdx.x / GPT, (blockIdx.x % GPT) * CB, blockIdx.x);
+  constexpr int CC = CB * CellsPer<T>::value, GPT = BL / CC;
+  general_body<S, T, N, CB, CURVED, HELM>(A.j, A.tab, blockIdx.x / GPT, (blockIdx.x % GPT) * CC, blockIdx.x);
 }
 
 // the job of batched CTA blockIdx.x into shared memory; returns its local CTA index
@@ -540,17 +628,17 @@ __device__ __forceinline__ long long batch_job(const ApplyJob<S, T>* jobs, const
 }
 template <typename S, typename T, int N, int CB, int MINB, bool HELM>
 __global__ void __launch_bounds__(N * N * CB, MINB) apply_cartesian_batch(ApplyBatch<S, T, N> B) {
-  constexpr int GPT = BL / CB;
+  constexpr int CC = CB * CellsPer<T>::value, GPT = BL / CC;
   __shared__ __align__(16) ApplyJob<S, T> sj;
   const long long b = batch_job(B.jobs, B.block0, B.njobs, sj);
-  cartesian_body<S, T, N, CB, HELM>(sj, B.tab, b / GPT, (int)(b % GPT) * CB, b);
+  cartesian_body<S, T, N, CB, HELM>(sj, B.tab, b / GPT, (int)(b % GPT) * CC, b);
 }
 template <typename S, typename T, int N, int CB, int MINB, bool CURVED, bool HELM>
 __global__ void __launch_bounds__(N * N * CB, MINB) apply_general_batch(ApplyBatch<S, T, N> B) {
-  constexpr int GPT = BL / CB;
+  constexpr int CC = CB * CellsPer<T>::value, GPT = BL / CC;
   __shared__ __align__(16) ApplyJob<S, T> sj;
   const long long b = batch_job(B.jobs, B.block0, B.njobs, sj);
-  general_body<S, T, N, CB, CURVED, HELM>(sj, B.tab, b / GPT, (int)(b % GPT) * CB, b);
+  general_body<S, T, N, CB, CURVED, HELM>(sj, B.tab, b / GPT, (int)(b % GPT) * CC, b);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -808,6 +896,7 @@ static void fill_job(const mf_operator* op, ApplyJob<S, T>& a) {
   a.h[2] = 1.0f / op->g.nz;
   a.cg = CgFuse<S>{};
   a.pf_tiles = 0;
+  a.pf_geom = 0;
 }
 // A(q, i) = a[q * MAXN + i], or a[i * MAXN + q] for the transpose
 template <typename T, int N>
@@ -880,14 +969,14 @@ static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, co
   using C = Cfg<T, N, V>;
   ApplyArgs<S, T, N> a;
   fill_job<S, T>(op, a.j);
-  fill_tab<T, N>(op, a.tab);
+  fill_tab<typename CoefOf<T>::type, N>(op, a.tab);
   a.j.cg = cg;
   a.j.x = static_cast<const S*>(x);
   a.j.y = static_cast<S*>(y);
   a.j.geom = static_cast<const T*>(geom);
   const bool helm = op->kind == MF_HELMHOLTZ;
   const size_t smem = (op->path == PATH_CARTESIAN ? 2 : 3) * sizeof(T) * N * N * N * C::CB;
-  const long long blocks = op->g.ntiles * (BL / C::CB);
+  const long long blocks = op->g.ntiles * (BL / (C::CB * C::CPL));
   if (nblocks) *nblocks = blocks;
   if (blocks <= 0) return MF_OK;
   void (*k)(ApplyArgs<S, T, N>) = nullptr;
@@ -904,7 +993,8 @@ static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, co
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(apply)");
   }
-  a.j.pf_tiles = prefetch_distance_tiles((const void*)k, C::NT, smem, BL / C::CB);
+  a.j.pf_tiles = prefetch_distance_tiles((const void*)k, C::NT, smem, BL / (C::CB * C::CPL));
+  a.j.pf_geom = (op->path == PATH_CURVED && !IsF32<T>::value) ? 1 : 0;
   k<<<(unsigned)blocks, C::NT, smem, s>>>(a);
   return cuda_check(cudaGetLastError(), "apply launch");
 }
@@ -925,7 +1015,7 @@ mf_status apply_split_n(const mf_operator* op, int vk, const void* x, void* y, c
   if (vk == VK_F64) return apply_split_t<double, double, N>(op, v, x, y, op->v64.geom, CgFuse<double>{}, nullptr, s);
   if (vk == VK_DD) return apply_split_t<double, dd, N>(op, v, x, y, op->v64.geom, CgFuse<double>{}, nullptr, s);
   if (vk == VK_DDS) return apply_split_t<dd, dd, N>(op, v, x, y, op->v64.geom, CgFuse<dd>{}, nullptr, s);
-  return apply_split_t<float, float, N>(op, v, x, y, op->v32.geom, CgFuse<float>{}, nullptr, s);
+  return apply_split_t<float, FP32C, N>(op, v, x, y, op->v32.geom, CgFuse<float>{}, nullptr, s);
 }
 
 template <int N>
@@ -935,7 +1025,7 @@ mf_status apply_cg_n(const mf_operator* op, int vk, void* p, const void* r, void
   void* x = update_p ? nullptr : p;
   if (vk == VK_F32) {
     const CgFuse<float> cg{static_cast<float*>(p), static_cast<const float*>(r), st, partials, update_p};
-    return apply_split_t<float, float, N>(op, v, x, y, op->v32.geom, cg, nblocks, s);
+    return apply_split_t<float, FP32C, N>(op, v, x, y, op->v32.geom, cg, nblocks, s);
   }
   if (vk == VK_DDS) {
     const CgFuse<dd> cg{static_cast<dd*>(p), static_cast<const dd*>(r), st, partials, update_p};
@@ -966,7 +1056,7 @@ static mf_status batch_fill_v(const BatchMember* m, int n, int vk, void* jobs_ho
     a.y = static_cast<S*>(m[i].q);
     a.geom = static_cast<const T*>(vk == VK_F32 ? op->v32.geom : op->v64.geom);
     block0_host[i] = b;
-    b += op->g.ntiles * (BL / C::CB);
+    b += op->g.ntiles * (BL / (C::CB * C::CPL));
   }
   block0_host[n] = b;
   return MF_OK;
@@ -977,7 +1067,7 @@ static mf_status batch_launch_v(const mf_operator* op0, const void* jobs_dev, co
                                 long long blocks, cudaStream_t s) {
   using C = Cfg<T, N, V>;
   ApplyBatch<S, T, N> B;
-  fill_tab<T, N>(op0, B.tab);
+  fill_tab<typename CoefOf<T>::type, N>(op0, B.tab);
   B.jobs = static_cast<const ApplyJob<S, T>*>(jobs_dev);
   B.block0 = block0_dev;
   B.njobs = njobs;
@@ -1020,7 +1110,7 @@ static mf_status batch_launch_t(const mf_operator* op0, int variant, const void*
 template <int N>
 mf_status apply_batch_fill_n(const BatchMember* m, int n, int vk, void* jobs_host, long long* block0_host) {
   const int v = m[0].op->variant[vk == VK_DDS ? VK_DD : vk];
-  if (vk == VK_F32) return batch_fill_t<float, float, N>(m, n, vk, v, jobs_host, block0_host);
+  if (vk == VK_F32) return batch_fill_t<float, FP32C, N>(m, n, vk, v, jobs_host, block0_host);
   if (vk == VK_DDS) return batch_fill_t<dd, dd, N>(m, n, vk, v, jobs_host, block0_host);
   if (vk == VK_DD) return batch_fill_t<double, dd, N>(m, n, vk, v, jobs_host, block0_host);
   return batch_fill_t<double, double, N>(m, n, vk, v, jobs_host, block0_host);
@@ -1029,7 +1119,7 @@ template <int N>
 mf_status apply_batch_launch_n(const mf_operator* op0, int vk, const void* jobs_dev, const long long* block0_dev,
                                int njobs, long long blocks, cudaStream_t s) {
   const int v = op0->variant[vk == VK_DDS ? VK_DD : vk];
-  if (vk == VK_F32) return batch_launch_t<float, float, N>(op0, v, jobs_dev, block0_dev, njobs, blocks, s);
+  if (vk == VK_F32) return batch_launch_t<float, FP32C, N>(op0, v, jobs_dev, block0_dev, njobs, blocks, s);
   if (vk == VK_DDS) return batch_launch_t<dd, dd, N>(op0, v, jobs_dev, block0_dev, njobs, blocks, s);
   if (vk == VK_DD) return batch_launch_t<double, dd, N>(op0, v, jobs_dev, block0_dev, njobs, blocks, s);
   return batch_launch_t<double, double, N>(op0, v, jobs_dev, block0_dev, njobs, blocks, s);
