@@ -54,24 +54,33 @@ def flops_per_dof(path: int, n: int, helm: bool) -> float:
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling (every 100 ms) around the timed region; samples are timestamped and
+    only those inside [mark_start, mark_end] are summarised (all of them if none fall inside)."""
 
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
         self.p = None
+        self.t0 = self.t1 = None
+        self.lines = []
 
     def __enter__(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
         return self
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
 
     def __exit__(self, *a):
         self.lines = []
@@ -85,23 +94,30 @@ class Clocks:
             self.lines = [ln for ln in out.splitlines() if ln.strip()]
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
+        import datetime
+
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 8:
+            if len(f) < 9:
                 continue
             try:
-                sm.append(float(f[0]))
-                mx = float(f[1])
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(f[1]), float(f[2]), f[5:9]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[4:8]):
+        inside = [r for r in rows if self.t0 is not None and self.t1 is not None and self.t0 - 0.05 <= r[0] <= self.t1 + 0.05]
+        use = inside if inside else rows
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        reasons = set()
+        for r in use:
+            for nm, v in zip(names, r[3]):
                 if v.lower() == "active":
                     reasons.add(nm)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": use[-1][2], "reasons": sorted(reasons),
+                "samples": len(use), "window": "timed region" if inside else "whole run (none inside the timed region)"}
 
 
 def aggregate_ranks(dist, device, t_local: float, units_local: float):
@@ -459,7 +475,7 @@ def serve_run(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-sweep", action="store_true")
@@ -531,19 +547,21 @@ def main():
         cws = torch.empty(mf.mf_cg_workspace_bytes(op, 0), dtype=torch.uint8, device="cuda")
     stream.synchronize()
     variant = autotune(mf, torch, op, b, s)
-    # warm-up (also builds and caches the solve's graph path once)
-    mf.mf_cg_solve(op, b.data_ptr(), x.data_ptr(), 0.0, args.warmup, 0, cws.data_ptr(), cws.numel(), s,
-                   allow_not_converged=True)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     with Clocks(local) as clk:
+        # warm-up (also builds and caches the solve's graph path once)
+        mf.mf_cg_solve(op, b.data_ptr(), x.data_ptr(), 0.0, args.warmup, 0, cws.data_ptr(), cws.numel(), s,
+                       allow_not_converged=True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk.mark_start()
         ev[0].record(stream)
         st = mf.mf_cg_solve(op, b.data_ptr(), x.data_ptr(), 0.0, args.steps, 0, cws.data_ptr(), cws.numel(), s,
                             allow_not_converged=True)
         ev[1].record(stream)
         ev[1].synchronize()
+        clk.mark_end()
     torch.cuda.synchronize()
     t_steps = ev[0].elapsed_time(ev[1]) / 1e3
     its = st["iterations"]
