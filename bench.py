@@ -74,6 +74,7 @@ class Clocks:
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
+        time.sleep(1.0)  # nvidia-smi takes a moment before its first sample
         return self
 
     def mark_start(self):
