@@ -148,6 +148,13 @@ mf_status mf_dss(const mf_operator* op, void* y_dev, void* stream);
  * bytes, 256-byte aligned), then every copy reads the sum back.  Consistent, but the order of
  * the atomic additions -- hence the last bits of the sums -- is not reproducible.  Same
  * precision as the operator's vectors; P y for Dirichlet. */
+/* The assembled diagonal of the operator (P A P for Dirichlet: 0 on constrained nodes), as a
+ * consistent native vector of FP32 values (n_native floats), computed from the same
+ * quadrature and metric as the apply, for Jacobi preconditioning of CG (the paper's smoother,
+ * Sec. 5.2, is a Chebyshev-accelerated block Jacobi inside multigrid).  Scratch:
+ * mf_diagonal_workspace_bytes() device bytes. */
+size_t mf_diagonal_workspace_bytes(const mf_operator* op);
+mf_status mf_diagonal(const mf_operator* op, float* diag_dev, void* scratch_dev, size_t scratch_bytes, void* stream);
 size_t mf_dss_atomic_workspace_bytes(const mf_operator* op);
 mf_status mf_dss_atomic(const mf_operator* op, void* y_dev, void* scratch_dev, size_t scratch_bytes, void* stream);
 /* End to end from host memory: copies canonical x_host to the device, applies, copies the
@@ -226,12 +233,16 @@ mf_status mf_cg_solve(const mf_operator* op, const void* b_dev, void* x_dev, dou
  *     load (three kernels per iteration).
  * All compute the same iterates up to rounding (only <p, A p> is summed differently). */
 enum { MF_CG_DEFAULT = 0, MF_CG_SPLIT_DUAL = 1, MF_CG_ASSEMBLED = 2, MF_CG_SPLIT_DUAL_FUSED = 3 };
+/* Preconditioner (mf_solve_options.precond): none (default), or Jacobi -- z = r / diag(P A P)
+ * with the assembled diagonal of mf_diagonal (0 on Dirichlet nodes); split-dual form only.
+ * The convergence test stays ||r|| <= rtol ||b||; alpha and beta use <r, z>. */
+enum { MF_PRECOND_NONE = 0, MF_PRECOND_JACOBI = 1 };
 typedef struct {
   double inner_rtol;
   int32_t chunk_iterations;
   int32_t max_outer;
   int32_t cg_form; /* MF_CG_* */
-  int32_t reserved;
+  int32_t precond; /* MF_PRECOND_* */
 } mf_solve_options;
 mf_status mf_cg_solve_ex(const mf_operator* op, const void* b_dev, void* x_dev, double rtol, int maxit, int mixed,
                          const mf_solve_options* opts, mf_solve_stats* stats, void* workspace_dev, size_t bytes,

@@ -22,6 +22,7 @@ MF_LAPLACE, MF_HELMHOLTZ = 0, 1
 MF_FP64, MF_FP32, MF_MIXED, MF_FP64_DFMA = 0, 1, 2, 3
 MF_BC_NONE, MF_BC_DIRICHLET0 = 0, 1
 MF_CG_DEFAULT, MF_CG_SPLIT_DUAL, MF_CG_ASSEMBLED, MF_CG_SPLIT_DUAL_FUSED = 0, 1, 2, 3
+MF_PRECOND_NONE, MF_PRECOND_JACOBI = 0, 1
 
 _STATUS = {0: "MF_OK", -1: "MF_ERR_ARG", -2: "MF_ERR_OOM", -3: "MF_ERR_CUDA", -4: "MF_ERR_NOT_CONVERGED",
            -5: "MF_ERR_BREAKDOWN", -6: "MF_ERR_TIMEOUT", -7: "MF_ERR_BUSY", -8: "MF_ERR_UNSUPPORTED",
@@ -48,7 +49,7 @@ class mf_solve_stats(C.Structure):
 
 class mf_solve_options(C.Structure):
     _fields_ = [("inner_rtol", C.c_double), ("chunk_iterations", C.c_int32), ("max_outer", C.c_int32),
-                ("cg_form", C.c_int32), ("reserved", C.c_int32)]
+                ("cg_form", C.c_int32), ("precond", C.c_int32)]
 
 
 class mf_server_config(C.Structure):
@@ -123,6 +124,9 @@ def lib() -> C.CDLL:
     L.mf_cg_record_history.argtypes = [vp, i32]
     L.mf_cg_solve_ex.argtypes = [vp, vp, vp, d, i32, i32, C.POINTER(mf_solve_options), C.POINTER(mf_solve_stats),
                                  vp, sz, vp]
+    L.mf_diagonal_workspace_bytes.argtypes = [vp]
+    L.mf_diagonal_workspace_bytes.restype = sz
+    L.mf_diagonal.argtypes = [vp, vp, vp, sz, vp]
     L.mf_dss_atomic_workspace_bytes.argtypes = [vp]
     L.mf_dss_atomic_workspace_bytes.restype = sz
     L.mf_dss_atomic.argtypes = [vp, vp, vp, sz, vp]
@@ -269,9 +273,9 @@ def mf_cg_workspace_bytes(op, mixed: int = 0) -> int:
 
 def mf_cg_solve(op, b_ptr: int, x_ptr: int, rtol: float, maxit: int, mixed: int, workspace_ptr: int,
                 nbytes: int, stream: int = 0, allow_not_converged: bool = False, inner_rtol: float = 0.0,
-                chunk_iterations: int = 0, max_outer: int = 0, cg_form: int = 0) -> dict:
+                chunk_iterations: int = 0, max_outer: int = 0, cg_form: int = 0, precond: int = 0) -> dict:
     st = mf_solve_stats()
-    opts = mf_solve_options(inner_rtol, chunk_iterations, max_outer, cg_form, 0)
+    opts = mf_solve_options(inner_rtol, chunk_iterations, max_outer, cg_form, precond)
     code = lib().mf_cg_solve_ex(op, b_ptr, x_ptr, rtol, maxit, mixed, C.byref(opts), C.byref(st), workspace_ptr,
                                 nbytes, stream or None)
     if not (code == MF_OK or (allow_not_converged and code == MF_ERR_NOT_CONVERGED)):
@@ -279,6 +283,14 @@ def mf_cg_solve(op, b_ptr: int, x_ptr: int, rtol: float, maxit: int, mixed: int,
     out = {f: getattr(st, f) for f, _ in mf_solve_stats._fields_}
     out["code"] = code
     return out
+
+
+def mf_diagonal_workspace_bytes(op) -> int:
+    return int(lib().mf_diagonal_workspace_bytes(op))
+
+
+def mf_diagonal(op, diag_ptr: int, scratch_ptr: int, nbytes: int, stream: int = 0) -> None:
+    _check(lib().mf_diagonal(op, diag_ptr, scratch_ptr, nbytes, stream or None))
 
 
 def mf_dss_atomic_workspace_bytes(op) -> int:

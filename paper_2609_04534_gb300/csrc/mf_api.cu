@@ -61,6 +61,9 @@ size_t apply_job_bytes(int vk) {
                       : (vk == VK_DDS ? sizeof(ApplyJob<dd, dd>)
                                       : (vk == VK_DD ? sizeof(ApplyJob<double, dd>) : sizeof(ApplyJob<double, double>)));
 }
+mf_status launch_diagonal(const mf_operator* op, float* diag, float* gtab, cudaStream_t s) {
+  MF_DISPATCH_N(op->n, diagonal_n, op, diag, gtab, s);
+}
 // every launch variant puts at least 4 cells of a 32-cell tile in one CTA
 long long apply_max_blocks(const mf_operator* op) { return op->g.ntiles * (BL / 4); }
 mf_status launch_dss(const mf_operator* op, int elem, void* y, cudaStream_t s) {
@@ -278,6 +281,15 @@ mf_status mf_apply_split(const mf_operator* op, const void* x_dev, void* y_dev, 
 mf_status mf_dss(const mf_operator* op, void* y_dev, void* stream) {
   if (!op || !y_dev) return set_error(MF_ERR_ARG, "mf_dss: NULL argument");
   return launch_dss(op, elem_of(op), y_dev, static_cast<cudaStream_t>(stream));
+}
+
+size_t mf_diagonal_workspace_bytes(const mf_operator* op) { return op ? diag_table_bytes(op) : 0; }
+
+mf_status mf_diagonal(const mf_operator* op, float* diag_dev, void* scratch_dev, size_t scratch_bytes, void* stream) {
+  if (!op || !diag_dev) return set_error(MF_ERR_ARG, "mf_diagonal: NULL argument");
+  if (!scratch_dev || scratch_bytes < diag_table_bytes(op))
+    return set_error(MF_ERR_OOM, "mf_diagonal: scratch %zu < %zu bytes", scratch_bytes, diag_table_bytes(op));
+  return launch_diagonal(op, diag_dev, static_cast<float*>(scratch_dev), static_cast<cudaStream_t>(stream));
 }
 
 size_t mf_dss_atomic_workspace_bytes(const mf_operator* op) {

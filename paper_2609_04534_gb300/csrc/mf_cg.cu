@@ -29,6 +29,7 @@ struct RedScratch {
   unsigned int counter;
   unsigned int pad[63];
   double partial[RED_MAX_BLOCKS];
+  double partial2[RED_MAX_BLOCKS]; // a second sum reduced alongside (the update's <r, z>)
 };
 
 size_t reduce_scratch_bytes() { return sizeof(RedScratch); }
@@ -85,6 +86,35 @@ __device__ __forceinline__ double block_sum(double v) {
 
 // Called by every thread of every block after the block partial is known.  Returns true
 // in thread 0 of the last block to finish, with *total = sum of partials in index order.
+// Two sums reduced together (partial and partial2), one counter; the last CTA gets both.
+__device__ __forceinline__ bool last_block_total2(RedScratch* sc, double part, double part2, double* total,
+                                                  double* total2, int cta, int ncta) {
+  __shared__ bool am_last2;
+  if (threadIdx.x == 0) {
+    sc->partial[cta] = part;
+    sc->partial2[cta] = part2;
+    __threadfence();
+    const unsigned prev = atomicAdd(&sc->counter, 1u);
+    am_last2 = (prev == (unsigned)ncta - 1);
+  }
+  __syncthreads();
+  if (!am_last2) return false;
+  __threadfence();
+  double s = 0.0, s2 = 0.0;
+  for (int b = threadIdx.x; b < ncta; b += RED_THREADS) {
+    s += ((volatile double*)sc->partial)[b];
+    s2 += ((volatile double*)sc->partial2)[b];
+  }
+  s = block_sum(s);
+  s2 = block_sum(s2);
+  if (threadIdx.x == 0) {
+    sc->counter = 0;
+    *total = s;
+    *total2 = s2;
+  }
+  return threadIdx.x == 0;
+}
+
 // cta / ncta: the CTA's index and the CTA count of its reduction (a batched launch runs
 // several reductions, each over its own CTA range and scratch).
 __device__ __forceinline__ bool last_block_total(RedScratch* sc, double part, double* total, int cta, int ncta) {
@@ -169,6 +199,7 @@ __global__ void __launch_bounds__(RED_THREADS) cg_xr_kernel(T* __restrict__ x, T
     if (st->flag == 0) {
       st->beta = tot / st->rr;
       st->rr = tot;
+      st->rz = tot;
       st->it += 1;
       if (hist && st->it < HIST_CAP) hist[st->it] = sqrt(tot) / st->bnorm;
       if (tot <= st->tol2) st->flag = 1;
@@ -180,6 +211,11 @@ __global__ void __launch_bounds__(RED_THREADS) cg_xr_kernel(T* __restrict__ x, T
   }
 }
 
+// z = M^-1 r of Jacobi preconditioning: the element-wise product with the inverse diagonal
+__device__ __forceinline__ double precond_z(double r, float d) { return r * (double)d; }
+__device__ __forceinline__ float precond_z(float r, float d) { return r * d; }
+__device__ __forceinline__ dd precond_z(dd r, float d) { return finish(mul0(r, dd(d, 0.0f))); }
+
 // Four consecutive vector elements (16 bytes of floats, 32 of doubles / double-floats): the
 // streaming kernels move them with 16-byte accesses.  Native vectors hold a multiple of 32
 // elements and start 256-byte aligned.
@@ -189,9 +225,10 @@ struct alignas(4 * sizeof(T) < 16 ? 16 : 4 * sizeof(T)) Quad {
 };
 
 // p = r + beta p, two quads per thread and trip so that four 16-byte loads are in flight
+// p = z + beta p, z = r or, with dinv, z = r / diag(A)
 template <typename T>
-__device__ __forceinline__ void cg_p_body(const T* __restrict__ r, T* __restrict__ p, long long n, const CgState* st,
-                                          long long cta, long long ncta) {
+__device__ __forceinline__ void cg_p_body(const T* __restrict__ r, T* __restrict__ p, const float* __restrict__ dinv,
+                                          long long n, const CgState* st, long long cta, long long ncta) {
   const T be = scalar_from_double<T>(st->beta);
   if (st->flag != 0 && st->flag != 1) return;
   const long long nq = n / 4;
@@ -202,6 +239,16 @@ __device__ __forceinline__ void cg_p_body(const T* __restrict__ r, T* __restrict
     const bool two = i + stride < nq;
     Quad<T> a = pq[i], b = rq[i], c, d;
     if (two) { c = pq[i + stride]; d = rq[i + stride]; }
+    if (dinv) {
+      const float4 d0 = reinterpret_cast<const float4*>(dinv)[i];
+      b.v[0] = precond_z(b.v[0], d0.x); b.v[1] = precond_z(b.v[1], d0.y);
+      b.v[2] = precond_z(b.v[2], d0.z); b.v[3] = precond_z(b.v[3], d0.w);
+      if (two) {
+        const float4 d1 = reinterpret_cast<const float4*>(dinv)[i + stride];
+        d.v[0] = precond_z(d.v[0], d1.x); d.v[1] = precond_z(d.v[1], d1.y);
+        d.v[2] = precond_z(d.v[2], d1.z); d.v[3] = precond_z(d.v[3], d1.w);
+      }
+    }
 #pragma unroll
     for (int j = 0; j < 4; ++j) a.v[j] = finish(fma(be, a.v[j], b.v[j]));
     pq[i] = a;
@@ -213,9 +260,9 @@ __device__ __forceinline__ void cg_p_body(const T* __restrict__ r, T* __restrict
   }
 }
 template <typename T>
-__global__ void cg_p_kernel(const T* __restrict__ r, T* __restrict__ p, long long n, const CgState* st, int was_running) {
-  (void)was_running;
-  cg_p_body<T>(r, p, n, st, blockIdx.x, gridDim.x);
+__global__ void cg_p_kernel(const T* __restrict__ r, T* __restrict__ p, const float* __restrict__ dinv, long long n,
+                            const CgState* st) {
+  cg_p_body<T>(r, p, dinv, n, st, blockIdx.x, gridDim.x);
 }
 
 // Split-dual CG update (Sec. 4: the Krylov loop on split data).  q~ = A_K p is the split
@@ -233,8 +280,9 @@ __global__ void cg_p_kernel(const T* __restrict__ r, T* __restrict__ p, long lon
 // loads in flight.
 template <typename T, int N>
 __device__ __forceinline__ void cg_update_body(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
-                                               const T* __restrict__ q, const GridInfo& g, RedScratch* sc, CgState* st,
-                                               double* hist, int cta, int ncta) {
+                                               const T* __restrict__ q, const float* __restrict__ dinv,
+                                               const GridInfo& g, RedScratch* sc, CgState* st, double* hist, int cta,
+                                               int ncta) {
   constexpr int N2 = N * N, N3 = N2 * N, K = N - 1;
   if (st->flag != 0) return; // uniform: converged or stopped, nothing changes
   const T al = scalar_from_double<T>(st->alpha);
@@ -253,7 +301,7 @@ __device__ __forceinline__ void cg_update_body(T* __restrict__ x, T* __restrict_
       lz < TZ - 1 ? -(long long)K * N2 * BL + TX * TY : tz_step - (long long)K * N2 * BL - TX * TY * (TZ - 1);
   const long long units = g.ntiles * N2;
   const long long warps = (long long)ncta * (RED_THREADS / 32);
-  typename AccOf<T>::type acc;
+  typename AccOf<T>::type acc, accz; // <r, r> and (preconditioned) <r, z>
   for (long long u = cta * (long long)(RED_THREADS / 32) + (threadIdx.x >> 5); u < units; u += warps) {
     const long long t = u / N2;
     const int jk = (int)(u - t * N2);
@@ -316,13 +364,18 @@ __device__ __forceinline__ void cg_update_body(T* __restrict__ x, T* __restrict_
       const T rn = finish(fma(-al, qv, rv[i]));
       r[e] = rn;
       const int sh = shyz + ((xl || xh) ? 1 : 0);
-      acc.add(sh == 0 ? 1.0f : (sh == 1 ? 0.5f : (sh == 2 ? 0.25f : 0.125f)), rn, rn);
+      const float w = sh == 0 ? 1.0f : (sh == 1 ? 0.5f : (sh == 2 ? 0.25f : 0.125f));
+      acc.add(w, rn, rn);
+      if (dinv) accz.add(w, rn, precond_z(rn, dinv[e]));
     }
   }
   const double s = block_sum(acc.value());
-  double tot;
-  if (last_block_total(sc, s, &tot, cta, ncta)) {
-    st->beta = tot / st->rr;
+  const double sz = dinv ? block_sum(accz.value()) : 0.0;
+  double tot, totz;
+  if (last_block_total2(sc, s, sz, &tot, &totz, cta, ncta)) {
+    const double rz = dinv ? totz : tot;
+    st->beta = rz / st->rz;
+    st->rz = rz;
     st->rr = tot;
     st->it += 1;
     if (hist && st->it < HIST_CAP) hist[st->it] = sqrt(tot) / st->bnorm;
@@ -334,8 +387,9 @@ __device__ __forceinline__ void cg_update_body(T* __restrict__ x, T* __restrict_
 template <typename T, int N>
 __global__ void __launch_bounds__(RED_THREADS) cg_update_kernel(T* __restrict__ x, T* __restrict__ r,
                                                                 const T* __restrict__ p, const T* __restrict__ q,
-                                                                GridInfo g, RedScratch* sc, CgState* st, double* hist) {
-  cg_update_body<T, N>(x, r, p, q, g, sc, st, hist, blockIdx.x, gridDim.x);
+                                                                const float* __restrict__ dinv, GridInfo g,
+                                                                RedScratch* sc, CgState* st, double* hist) {
+  cg_update_body<T, N>(x, r, p, q, dinv, g, sc, st, hist, blockIdx.x, gridDim.x);
 }
 
 // alpha = <r, r> / <p, A p> from the apply's per-CTA partials of <p, A p>, folded in a fixed
@@ -352,7 +406,7 @@ __device__ __forceinline__ void alpha_body(const double* __restrict__ partials, 
       st->flag = 2;
       st->alpha = 0.0;
     } else {
-      st->alpha = st->rr / s;
+      st->alpha = st->rz / s;
     }
   }
 }
@@ -369,6 +423,7 @@ __global__ void __launch_bounds__(1024) alpha_kernel(const double* __restrict__ 
 // ---------------------------------------------------------------------------------------
 struct VecJob {
   void *x, *r, *p, *q;
+  const float* dinv; // Jacobi: inverse diagonal (null: no preconditioner)
   GridInfo g;
   RedScratch* sc;
   CgState* st;
@@ -395,13 +450,13 @@ __global__ void __launch_bounds__(1024) alpha_batch_kernel(const VecJob* __restr
 template <typename T, int N>
 __global__ void __launch_bounds__(RED_THREADS) cg_update_batch_kernel(const VecJob* __restrict__ jobs, int njobs) {
   const VecJob& j = jobs[find_member(jobs, njobs, true)];
-  cg_update_body<T, N>((T*)j.x, (T*)j.r, (const T*)j.p, (const T*)j.q, j.g, j.sc, j.st, j.hist,
+  cg_update_body<T, N>((T*)j.x, (T*)j.r, (const T*)j.p, (const T*)j.q, j.dinv, j.g, j.sc, j.st, j.hist,
                        (int)((long long)blockIdx.x - j.up0), (int)(j.up1 - j.up0));
 }
 template <typename T>
 __global__ void cg_p_batch_kernel(const VecJob* __restrict__ jobs, int njobs) {
   const VecJob& j = jobs[find_member(jobs, njobs, false)];
-  cg_p_body<T>((const T*)j.r, (T*)j.p, j.n, j.st, (long long)blockIdx.x - j.pp0, j.pp1 - j.pp0);
+  cg_p_body<T>((const T*)j.r, (T*)j.p, j.dinv, j.n, j.st, (long long)blockIdx.x - j.pp0, j.pp1 - j.pp0);
 }
 
 // Small element-wise kernels of the drivers.
@@ -427,6 +482,19 @@ __global__ void axpy64_kernel(double* __restrict__ x, const float* __restrict__ 
   const double sc = sqrt(*rn2);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) x[e] += sc * (double)d[e];
 }
+// Jacobi: d <- 1 / d where positive (Dirichlet nodes and padding keep 0)
+__global__ void invert_diag_kernel(float* __restrict__ d, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    d[e] = d[e] > 0.0f ? 1.0f / d[e] : 0.0f;
+}
+// p = z = r / diag (the first search direction of the preconditioned CG)
+template <typename T>
+__global__ void precond_copy_kernel(const T* __restrict__ r, T* __restrict__ p, const float* __restrict__ dinv,
+                                    long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    p[e] = precond_z(r[e], dinv[e]);
+}
+
 // FP64 solver with double-float vectors: r = b 2^-s as double-float, where 2^s is the power of
 // two of max|b| (so every value of the iteration stays well inside the float exponent range,
 // for right-hand sides anywhere in the double range); the solution is converted back with
@@ -549,7 +617,7 @@ static mf_status cg_vec_n(const mf_operator* op, T* x, T* r, T* p, T* q, RedScra
   const int bl = red_blocks(n);
   cg_pq_kernel<T, N><<<bl, RED_THREADS, 0, s>>>(p, q, n, op->g, sc1, st);
   cg_xr_kernel<T, N><<<bl, RED_THREADS, 0, s>>>(x, r, p, q, n, op->g, sc2, st, hist);
-  cg_p_kernel<T><<<ew_blocks(n), 256, 0, s>>>(r, p, n, st, 1);
+  cg_p_kernel<T><<<ew_blocks(n), 256, 0, s>>>(r, p, nullptr, n, st);
   return cuda_check(cudaGetLastError(), "cg vector launch");
 }
 template <int N>
@@ -568,19 +636,20 @@ static mf_status launch_cg_vec(const mf_operator* op, int elem, void* x, void* r
 template <int N>
 static mf_status cg_update_e(const mf_operator* op, int elem, void* x, void* r, void* p, void* q, const SolveWs& w,
                              CgState* st, double* hist, cudaStream_t s) {
+  const float* dinv = w.dinv_active;
   // one warp per x-pencil unit, at most RED_MAX_BLOCKS CTAs (warps loop over further units)
   long long bl = (op->g.ntiles * (long long)N * N + RED_THREADS / 32 - 1) / (RED_THREADS / 32);
   if (bl > RED_MAX_BLOCKS) bl = RED_MAX_BLOCKS;
   if (bl < 1) bl = 1;
   if (elem == 8)
     cg_update_kernel<double, N><<<(unsigned)bl, RED_THREADS, 0, s>>>((double*)x, (double*)r, (const double*)p,
-                                                                      (const double*)q, op->g, w.sc2, st, hist);
+                                                                      (const double*)q, dinv, op->g, w.sc2, st, hist);
   else if (elem == ELEM_DD)
-    cg_update_kernel<dd, N><<<(unsigned)bl, RED_THREADS, 0, s>>>((dd*)x, (dd*)r, (const dd*)p, (const dd*)q, op->g,
-                                                                  w.sc2, st, hist);
+    cg_update_kernel<dd, N><<<(unsigned)bl, RED_THREADS, 0, s>>>((dd*)x, (dd*)r, (const dd*)p, (const dd*)q, dinv,
+                                                                  op->g, w.sc2, st, hist);
   else
     cg_update_kernel<float, N><<<(unsigned)bl, RED_THREADS, 0, s>>>((float*)x, (float*)r, (const float*)p,
-                                                                     (const float*)q, op->g, w.sc2, st, hist);
+                                                                     (const float*)q, dinv, op->g, w.sc2, st, hist);
   return cuda_check(cudaGetLastError(), "cg update launch");
 }
 static mf_status launch_cg_update(const mf_operator* op, int elem, void* x, void* r, void* p, void* q, const SolveWs& w,
@@ -588,15 +657,17 @@ static mf_status launch_cg_update(const mf_operator* op, int elem, void* x, void
   MF_SWITCH_N(op->n, cg_update_e, op, elem, x, r, p, q, w, st, hist, s);
 }
 template <int N>
-static mf_status cg_p_e(const mf_operator* op, int elem, const void* r, void* p, CgState* st, cudaStream_t s) {
+static mf_status cg_p_e(const mf_operator* op, int elem, const void* r, void* p, const float* dinv, CgState* st,
+                        cudaStream_t s) {
   const long long n = op->n_native;
-  if (elem == 8) cg_p_kernel<double><<<ew_blocks(n), 256, 0, s>>>((const double*)r, (double*)p, n, st, 1);
-  else if (elem == ELEM_DD) cg_p_kernel<dd><<<ew_blocks(n), 256, 0, s>>>((const dd*)r, (dd*)p, n, st, 1);
-  else cg_p_kernel<float><<<ew_blocks(n), 256, 0, s>>>((const float*)r, (float*)p, n, st, 1);
+  if (elem == 8) cg_p_kernel<double><<<ew_blocks(n), 256, 0, s>>>((const double*)r, (double*)p, dinv, n, st);
+  else if (elem == ELEM_DD) cg_p_kernel<dd><<<ew_blocks(n), 256, 0, s>>>((const dd*)r, (dd*)p, dinv, n, st);
+  else cg_p_kernel<float><<<ew_blocks(n), 256, 0, s>>>((const float*)r, (float*)p, dinv, n, st);
   return cuda_check(cudaGetLastError(), "cg p launch");
 }
-static mf_status launch_cg_p(const mf_operator* op, int elem, const void* r, void* p, CgState* st, cudaStream_t s) {
-  MF_SWITCH_N(op->n, cg_p_e, op, elem, r, p, st, s);
+static mf_status launch_cg_p(const mf_operator* op, int elem, const void* r, void* p, const float* dinv, CgState* st,
+                             cudaStream_t s) {
+  MF_SWITCH_N(op->n, cg_p_e, op, elem, r, p, dinv, st, s);
 }
 // One split-dual iteration: apply with <p, A_K p> (alpha), update (q = G G^T q~, x, r, beta),
 // then p = r + beta p -- or, with fused_p, the apply forms p = r + beta p itself at load.
@@ -615,7 +686,7 @@ static mf_status launch_cg_split(const mf_operator* op, int elem, void* x, void*
   mf_status rc = launch_apply_alpha(op, elem, p, r, q, w, st, fused_p, s);
   if (rc) return rc;
   if ((rc = launch_cg_update(op, elem, x, r, p, q, w, st, hist, s))) return rc;
-  return fused_p ? MF_OK : launch_cg_p(op, elem, r, p, st, s);
+  return fused_p ? MF_OK : launch_cg_p(op, elem, r, p, w.dinv_active, st, s);
 }
 
 // apply + duplicate summation with a given element type (selects the FP64 or FP32 view)
@@ -643,6 +714,9 @@ size_t solve_ws_layout(const mf_operator* op, int mixed, char* base, SolveWs* w)
   t.hist = (double*)take(sizeof(double) * HIST_CAP);
   t.scal = (double*)take(sizeof(double) * 16);
   t.apart = (double*)take(sizeof(double) * (size_t)apply_max_blocks(op));
+  t.dinv = (float*)take(sizeof(float) * n);        // Jacobi: inverse of the assembled diagonal
+  t.dtab = (float*)take(diag_table_bytes(op));     //   and the diagonal's sin / cos tables
+  t.dinv_active = nullptr;
   t.r = take(n * elem);
   t.p = take(n * elem);
   t.q = take(n * elem);
@@ -659,17 +733,18 @@ size_t solve_ws_layout(const mf_operator* op, int mixed, char* base, SolveWs* w)
 }
 
 // CG state from the first residual norm (kept on the device: no host round trip).
-__global__ void init_state_kernel(CgState* st, const double* rr0, double rtol, int maxit) {
+__global__ void init_state_kernel(CgState* st, const double* rr0, const double* rz0, double rtol, int maxit) {
   const double rr = *rr0;
   CgState h;
   h.rr = rr;
+  h.rz = *rz0;
   h.pq = h.alpha = h.beta = 0.0;
   h.bnorm = sqrt(rr);
   h.tol2 = (rtol * h.bnorm) * (rtol * h.bnorm);
   h.it = 0;
   h.maxit = maxit;
   h.pad = 0;
-  h.flag = !isfinite(rr) ? 2 : ((rr <= h.tol2 || rr == 0.0) ? 1 : (maxit <= 0 ? 3 : 0));
+  h.flag = !isfinite(rr) || !isfinite(h.rz) ? 2 : ((rr <= h.tol2 || rr == 0.0) ? 1 : (maxit <= 0 ? 3 : 0));
   *st = h;
 }
 
@@ -708,7 +783,16 @@ static mf_status eng_inner_start(SolverEngine* e, const void* rhs, void* x_in, d
   }
   if ((st = cuda_check(cudaGetLastError(), "cg init"))) return st;
   if ((st = dot_launch(e->op, el, e->w.r, e->w.r, 0, e->w.scal, e->w.sc3, s))) return st;
-  init_state_kernel<<<1, 1, 0, s>>>(e->w.st, e->w.scal, rtol, maxit);
+  const double* rz0 = e->w.scal;
+  if (e->w.dinv_active) { // preconditioned: p = z = r / diag, <r, z>
+    if (el == 8) precond_copy_kernel<double><<<ew_blocks(n), 256, 0, s>>>((const double*)e->w.r, (double*)e->w.p, e->w.dinv_active, n);
+    else if (el == ELEM_DD) precond_copy_kernel<dd><<<ew_blocks(n), 256, 0, s>>>((const dd*)e->w.r, (dd*)e->w.p, e->w.dinv_active, n);
+    else precond_copy_kernel<float><<<ew_blocks(n), 256, 0, s>>>((const float*)e->w.r, (float*)e->w.p, e->w.dinv_active, n);
+    if ((st = cuda_check(cudaGetLastError(), "precond init"))) return st;
+    if ((st = dot_launch(e->op, el, e->w.r, e->w.p, 0, e->w.scal + 5, e->w.sc3, s))) return st;
+    rz0 = e->w.scal + 5;
+  }
+  init_state_kernel<<<1, 1, 0, s>>>(e->w.st, e->w.scal, rz0, rtol, maxit);
   if ((st = cuda_check(cudaGetLastError(), "init state"))) return st;
   e->phase = PH_INNER;
   return cuda_check(cudaMemcpyAsync(&e->hm->st, e->w.st, sizeof(CgState), cudaMemcpyDeviceToHost, s), "state D2H");
@@ -797,6 +881,13 @@ mf_status engine_start(SolverEngine* e) {
   // double-float as well: every vector operation then runs on the FP32 pipe (GB300's FP64 pipe
   // could not keep up with HBM even for the vector updates).  b is scaled by a power of two
   // near 1/||b|| on entry and x converted back on exit.
+  e->w.dinv_active = nullptr;
+  if (e->precond == MF_PRECOND_JACOBI) {
+    if ((st = launch_diagonal(e->op, e->w.dinv, e->w.dtab, e->s))) return st;
+    invert_diag_kernel<<<ew_blocks(n), 256, 0, e->s>>>(e->w.dinv, n);
+    if ((st = cuda_check(cudaGetLastError(), "diagonal inverse"))) return st;
+    e->w.dinv_active = e->w.dinv;
+  }
   e->vt = e->elem_in;
   if (!e->mixed && e->elem_in == 8 && fp64_view(e->op) == VK_DD && e->form != MF_CG_ASSEMBLED && e->w.xdd) {
     e->vt = ELEM_DD;
@@ -886,6 +977,7 @@ BatchMember engine_batch_member(const SolverEngine* e) {
   m.apart = e->w.apart;
   m.sc = e->w.sc2;
   m.hist = nullptr;
+  m.dinv = e->w.dinv_active;
   return m;
 }
 
@@ -932,6 +1024,7 @@ mf_status batch_plan_build(BatchPlan* plan, const BatchMember* m, int n, int ele
     const mf_operator* o = m[i].op;
     VecJob& v = vj[i];
     v.x = m[i].x;
+    v.dinv = m[i].dinv;
     v.r = m[i].r;
     v.p = m[i].p;
     v.q = m[i].q;
@@ -1039,7 +1132,8 @@ mf_status mf_cg_solve_ex(const mf_operator* op, const void* b_dev, void* x_dev, 
   if (!op || !b_dev || !x_dev) return set_error(MF_ERR_ARG, "mf_cg_solve: NULL argument");
   if (opts && ((opts->inner_rtol != 0.0 && !(opts->inner_rtol > 0.0 && opts->inner_rtol < 1.0)) ||
                opts->chunk_iterations < 0 || opts->max_outer < 0 || opts->cg_form < 0 ||
-               opts->cg_form > MF_CG_SPLIT_DUAL_FUSED))
+               opts->cg_form > MF_CG_SPLIT_DUAL_FUSED || opts->precond < 0 || opts->precond > MF_PRECOND_JACOBI ||
+               (opts->precond == MF_PRECOND_JACOBI && opts->cg_form > MF_CG_SPLIT_DUAL)))
     return set_error(MF_ERR_ARG, "mf_cg_solve_ex: bad options");
   if (!op->ready) return set_error(MF_ERR_ARG, "mf_cg_solve: operator not set up");
   if (maxit < 0 || !(rtol >= 0.0)) return set_error(MF_ERR_ARG, "mf_cg_solve: bad rtol/maxit");
@@ -1072,6 +1166,7 @@ mf_status mf_cg_solve_ex(const mf_operator* op, const void* b_dev, void* x_dev, 
     if (opts->chunk_iterations > 0) e.chunk = opts->chunk_iterations;
     if (opts->max_outer > 0) e.max_outer = opts->max_outer;
     if (opts->cg_form != MF_CG_DEFAULT) e.form = opts->cg_form;
+    e.precond = opts->precond;
   }
   e.record = g_hist_host != nullptr;
   mf_status st = engine_start(&e);
@@ -1135,7 +1230,7 @@ mf_status mf_cg_profile(const mf_operator* op, const void* b_dev, void* x_dev, i
       cudaEventRecord(E[1], s);
       cudaEventRecord(E[2], s);
       if (st == MF_OK) st = launch_cg_update(op, el, e.x_in, e.w.r, e.w.p, e.w.q, e.w, e.w.st, nullptr, s);
-      if (st == MF_OK && !fp) st = launch_cg_p(op, el, e.w.r, e.w.p, e.w.st, s);
+      if (st == MF_OK && !fp) st = launch_cg_p(op, el, e.w.r, e.w.p, e.w.dinv_active, e.w.st, s);
     } else {
       st = launch_apply_split(op, view_of_elem(op, el), e.w.p, e.w.q, s);
       cudaEventRecord(E[1], s);

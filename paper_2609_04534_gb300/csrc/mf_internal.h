@@ -4,7 +4,7 @@
 // free parameter"): cells are grouped in tiles of BL = 32 spatially adjacent cells (a
 // TX x TY x TZ = 4 x 4 x 2 brick); inside a tile the cell lane is the fastest address, so a
 // warp reading one local DoF of 32 cells touches 32 consecutive words (the coalescing rule
-// of Sec. 6.4).  Element (tile t, local dof l, lane c) lives at (t * n^3 + l) * BL + c.
+// of Sec. 6.3).  Element (tile t, local dof l, lane c) lives at (t * n^3 + l) * BL + c.
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -63,7 +63,8 @@ constexpr int ELEM_DD = 9;
 
 // Device-resident CG scalars.
 struct CgState {
-  double rr;    // <r, r> (assembled)
+  double rr;    // <r, r> (assembled): the convergence test
+  double rz;    // <r, z>, z = M^-1 r (= rr without preconditioner): alpha and beta
   double pq;    // <p, A p>
   double alpha, beta;
   double bnorm; // ||b|| of this CG
@@ -136,6 +137,7 @@ struct BatchMember {
   double* apart;       // per-CTA <p, A p> partials of its apply
   void* sc;            // reduction scratch of its update
   double* hist;        // residual history (may be null)
+  const float* dinv;   // Jacobi: inverse diagonal (null: no preconditioner)
 };
 
 // Host-side double tables (any n <= MAXN).
@@ -205,6 +207,13 @@ template <int N>
 mf_status dss_n(const mf_operator* op, int elem, void* y, cudaStream_t s);
 template <int N>
 mf_status dss_atomic_n(const mf_operator* op, int elem, void* y, void* acc, cudaStream_t s);
+template <int N>
+mf_status diagonal_n(const mf_operator* op, float* diag, float* gtab, cudaStream_t s);
+// assembled diagonal (FP32, consistent, 0 on Dirichlet nodes); gtab: diag_table_bytes(op) bytes
+mf_status launch_diagonal(const mf_operator* op, float* diag, float* gtab, cudaStream_t s);
+inline size_t diag_table_bytes(const mf_operator* op) {
+  return sizeof(float) * 2 * (size_t)(op->g.nx + op->g.ny + op->g.nz) * (size_t)op->n;
+}
 template <int N>
 mf_status apply_batch_fill_n(const BatchMember* m, int n, int vk, void* jobs_host, long long* block0_host);
 template <int N>

@@ -839,6 +839,115 @@ __global__ void geometry_kernel(T* __restrict__ geom, GeomArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Diagonal of the operator (Jacobi preconditioning, FP32): per cell-local node i,
+// (A_K)_ii = sum_q grad phi_i^T G_q grad phi_i + m_q phi_i^2 with the same quadrature and
+// metric as the apply (grad phi_i = (D S S, S D S, S S D) from the 1D GLL basis S and its
+// derivative D at the Gauss points); the split diagonal is then summed over copies.
+// ---------------------------------------------------------------------------------------
+struct DiagArgs {
+  GridInfo g;
+  float S[MAXN * MAXN], D[MAXN * MAXN], W[MAXN];
+  int curved;
+  float G[6], mdet;                 // affine metric (w-free) and mass * det
+  const float* gtab;                // curved: sin / cos of pi xh per cell layer and direction
+  float amp, cm, h[3];
+};
+
+template <int N>
+__global__ void diag_kernel(float* __restrict__ dg, DiagArgs a) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= a.g.ntiles * N3 * BL) return;
+  const int lane = (int)(e % BL);
+  const int l = (int)((e / BL) % N3);
+  const long long t = e / ((long long)BL * N3);
+  int cx, cy, cz;
+  cell_of(a.g, t, lane, cx, cy, cz);
+  if (cx >= a.g.nx || cy >= a.g.ny || cz >= a.g.nz) {
+    dg[e] = 0.0f;
+    return;
+  }
+  const int ix = l % N, iy = (l / N) % N, iz = l / N2;
+  const float* tx = a.gtab + 2 * (cx * N);
+  const float* ty = a.gtab + 2 * ((a.g.nx + cy) * N);
+  const float* tz = a.gtab + 2 * ((a.g.nx + a.g.ny + cz) * N);
+  const float pi = 3.14159265358979f;
+  float acc = 0.0f;
+  for (int qz = 0; qz < N; ++qz) {
+    const float Sz = a.S[qz * MAXN + iz], Dz = a.D[qz * MAXN + iz];
+    for (int qy = 0; qy < N; ++qy) {
+      const float Sy = a.S[qy * MAXN + iy], Dy = a.D[qy * MAXN + iy];
+#pragma unroll
+      for (int qx = 0; qx < N; ++qx) {
+        const float Sx = a.S[qx * MAXN + ix], Dx = a.D[qx * MAXN + ix];
+        const float gx = Dx * Sy * Sz, gy = Sx * Dy * Sz, gz = Sx * Sy * Dz, ph = Sx * Sy * Sz;
+        const float w = a.W[qx] * a.W[qy] * a.W[qz];
+        float g0, g1, g2, g3, g4, g5, m;
+        if (a.curved) {
+          // the metric of the curved map (same closed form as the FP32 apply)
+          const float sx = tx[2 * qx], cxv = tx[2 * qx + 1], sy = ty[2 * qy], cyv = ty[2 * qy + 1];
+          const float sz = tz[2 * qz], czv = tz[2 * qz + 1];
+          const float v1 = pi * cxv * sy * sz, v2 = pi * sx * cyv * sz, v3 = pi * sx * sy * czv;
+          const float beta = fmaf(a.amp, v1 + v2 + v3, 1.0f);
+          const float au = a.amp / beta;
+          const float c2 = au * au * (v1 * v1 + v2 * v2 + v3 * v3);
+          const float wd = w * (a.h[0] * a.h[1] * a.h[2]) * fabsf(beta);
+          const float i0 = 1.0f / a.h[0], i1 = 1.0f / a.h[1], i2 = 1.0f / a.h[2];
+          g0 = wd * i0 * i0 * (1.0f - 2.0f * au * v1 + c2);
+          g1 = wd * i0 * i1 * (c2 - au * (v1 + v2));
+          g2 = wd * i0 * i2 * (c2 - au * (v1 + v3));
+          g3 = wd * i1 * i1 * (1.0f - 2.0f * au * v2 + c2);
+          g4 = wd * i1 * i2 * (c2 - au * (v2 + v3));
+          g5 = wd * i2 * i2 * (1.0f - 2.0f * au * v3 + c2);
+          m = wd * a.cm;
+        } else {
+          g0 = w * a.G[0]; g1 = w * a.G[1]; g2 = w * a.G[2];
+          g3 = w * a.G[3]; g4 = w * a.G[4]; g5 = w * a.G[5];
+          m = w * a.mdet;
+        }
+        acc += gx * (g0 * gx + 2.0f * (g1 * gy + g2 * gz)) + gy * (g3 * gy + 2.0f * g4 * gz) + g5 * gz * gz +
+               m * ph * ph;
+      }
+    }
+  }
+  dg[e] = acc;
+}
+
+// diag (n_native floats) = the assembled diagonal (consistent; 0 on Dirichlet nodes and
+// padding); gtab: (nx + ny + nz) * N * 2 floats of scratch for curved meshes
+template <int N>
+mf_status diagonal_n(const mf_operator* op, float* diag, float* gtab, cudaStream_t s) {
+  DiagArgs a;
+  a.g = op->g;
+  const HostTables& h = op->tab;
+  for (int q = 0; q < MAXN * MAXN; ++q) {
+    a.S[q] = (float)h.S[q];
+    a.D[q] = (float)h.D[q];
+  }
+  for (int q = 0; q < MAXN; ++q) a.W[q] = (float)h.qw[q];
+  a.curved = op->path == PATH_CURVED;
+  for (int m = 0; m < 6; ++m) a.G[m] = (float)op->G[m];
+  a.mdet = (float)(op->kind == MF_HELMHOLTZ ? op->mdet : 0.0);
+  a.gtab = gtab;
+  a.amp = (float)op->mesh.amp;
+  a.cm = (float)(op->kind == MF_HELMHOLTZ ? op->mass : 0.0);
+  a.h[0] = 1.0f / op->g.nx;
+  a.h[1] = 1.0f / op->g.ny;
+  a.h[2] = 1.0f / op->g.nz;
+  if (a.curved) {
+    GeomArgsQ q;
+    for (int i = 0; i < N; ++i) q.qx[i] = op->tab.qx[i];
+    const int nt = (op->g.nx + op->g.ny + op->g.nz) * N;
+    geom_table_kernel<N><<<(nt + 127) / 128, 128, 0, s>>>(gtab, op->g, q);
+  }
+  const long long total = op->g.ntiles * (long long)N * N * N * BL;
+  diag_kernel<N><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(diag, a);
+  mf_status st = cuda_check(cudaGetLastError(), "diagonal launch");
+  if (st) return st;
+  return dss_n<N>(op, 4, diag, s);
+}
+
+// ---------------------------------------------------------------------------------------
 // Layout conversion: canonical <-> native, unique -> native (gather G), native -> unique.
 // ---------------------------------------------------------------------------------------
 template <typename T, int N>
@@ -1178,6 +1287,7 @@ mf_status layout_n(const mf_operator* op, int elem, int mode, const void* in, vo
                                     int, long long*, cudaStream_t);                                     \
   template mf_status dss_n<NN>(const mf_operator*, int, void*, cudaStream_t);                           \
   template mf_status dss_atomic_n<NN>(const mf_operator*, int, void*, void*, cudaStream_t);              \
+  template mf_status diagonal_n<NN>(const mf_operator*, float*, float*, cudaStream_t);                   \
   template mf_status apply_batch_fill_n<NN>(const BatchMember*, int, int, void*, long long*);            \
   template mf_status apply_batch_launch_n<NN>(const mf_operator*, int, const void*, const long long*, int,  \
                                               long long, cudaStream_t);                                 \

@@ -16,6 +16,8 @@ struct SolveWs {
   double* hist;
   double* scal;          // [0] inner <r,r>, [1] outer ||b||^2, [2] outer ||r||^2
   double* apart;         // split-dual iteration: per-CTA partials of <p, A p> from the apply
+  float *dinv, *dtab;    // Jacobi preconditioning: inverse diagonal, scratch of its computation
+  float* dinv_active;    // dinv when the solve is preconditioned, else null
   void *r, *p, *q;       // CG vectors of the (inner) element type
   void *r64, *q64, *b64; // mixed: FP64 outer residual, A x, masked b
   void* d32;             // mixed: inner solution
@@ -43,6 +45,7 @@ struct SolverEngine {
   int maxit = 0, chunk = 20, max_outer = 60;
   int form = MF_CG_SPLIT_DUAL; // MF_CG_SPLIT_DUAL, MF_CG_ASSEMBLED or MF_CG_SPLIT_DUAL_FUSED
   int vt = 8;                  // element type of the CG vectors (8, 4 or ELEM_DD), set at start
+  int precond = MF_PRECOND_NONE;
   HostMirror* hm = nullptr;
   int phase = 0, total_it = 0, outer = 0;
   double bn = 0.0, rel = 0.0;

@@ -85,6 +85,10 @@ def test_operator_argument_validation_and_info(L):
     with pytest.raises(mf.MfError) as e:
         mf.mf_cg_solve(op, 16, 32, 1e-10, 10, 0, 256, 1 << 30, cg_form=7)
     assert e.value.code == mf.MF_ERR_ARG
+    with pytest.raises(mf.MfError) as e:  # Jacobi needs the split-dual form
+        mf.mf_cg_solve(op, 16, 32, 1e-10, 10, 0, 256, 1 << 30, cg_form=mf.MF_CG_ASSEMBLED,
+                       precond=mf.MF_PRECOND_JACOBI)
+    assert e.value.code == mf.MF_ERR_ARG
     for its, form in [(10, 0), (0, 1), (1001, 1), (5, 4)]:
         with pytest.raises(mf.MfError) as e:
             mf.mf_cg_profile(op, 16, 32, its, form, 256, 1 << 30)
