@@ -202,9 +202,13 @@ mf_status mf_dot_noalloc(const mf_operator* op, const void* a_dev, const void* b
                          void* stream);
 
 /* ------------------------------------------------------------------ CG solver
- * Unpreconditioned CG on (P A P) x = P b from x = 0 for consistent native b, to
+ * CG (unpreconditioned unless mf_cg_solve_ex asks for Jacobi) on (P A P) x = P b from x = 0 for
+ * consistent native b, to
  * ||b - A x|| <= rtol ||b|| (assembled Euclidean norm = the pairing <r, r> of Sec. 4) or
- * maxit iterations.  mixed = 0: FP64 (or FP32 for an MF_FP32 operator) CG.  mixed = 1
+ * maxit iterations.  mixed = 0: FP64 (or FP32 for an MF_FP32 operator) CG; for MF_FP64 and
+ * MF_MIXED operators its iteration keeps x, r, p and A p as double-float pairs (about 48
+ * significant bits, FP32-pipe arithmetic; b enters scaled by the power of two of max|b|, x
+ * leaves scaled back), MF_FP64_DFMA keeps doubles.  mixed = 1
  * (operator MF_MIXED): FP64 defect correction -- outer residual r = b - A x, the update and
  * all dot products in FP64, inner CG with the FP32 apply.  Synchronous.  Workspace:
  * mf_cg_workspace_bytes(op, mixed) device bytes. */
