@@ -374,6 +374,8 @@ def solve_run(args):
     out = {"metric": "solved DoF/s at relative residual 1e-10", "workload":
            f"Q4 Poisson curved {N}^3, manufactured sin(2 pi x)sin(2 pi y)sin(2 pi z), Dirichlet"}
     mesh, op, info, ws = make_op(mf, torch, N, k, mf.MF_CURVED_SIN, mf.MF_LAPLACE, mf.MF_MIXED, 1, s)
+    # the plain FP64 solver runs on an MF_FP64 operator of the same mesh (double-float apply)
+    mesh64, op64, _, ws64 = make_op(mf, torch, N, k, mf.MF_CURVED_SIN, mf.MF_LAPLACE, mf.MF_FP64, 1, s)
     b = torch.empty(info["n_native"], dtype=torch.float64, device="cuda")
     sc = torch.empty(mf.mf_manufactured_workspace_bytes(op), dtype=torch.uint8, device="cuda")
     t0 = time.perf_counter()
@@ -382,13 +384,15 @@ def solve_run(args):
     out["rhs_setup_s"] = time.perf_counter() - t0
     x = torch.zeros_like(b)
     autotune(mf, torch, op, b, s)
+    autotune(mf, torch, op64, b, s)
     l2 = torch.zeros(1, dtype=torch.float64, device="cuda")
     runs = [(1, t, 0) for t in args.inner_rtol] + [(0, 0.0, 0), (1, args.inner_rtol[0], 1), (0, 0.0, 1)]
     for mixed, itol, pre in runs:
-        cws = torch.empty(mf.mf_cg_workspace_bytes(op, mixed), dtype=torch.uint8, device="cuda")
+        sop = op if mixed else op64
+        cws = torch.empty(mf.mf_cg_workspace_bytes(sop, mixed), dtype=torch.uint8, device="cuda")
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         ev[0].record(stream)
-        st = mf.mf_cg_solve(op, b.data_ptr(), x.data_ptr(), 1e-10, 400000, mixed, cws.data_ptr(), cws.numel(), s,
+        st = mf.mf_cg_solve(sop, b.data_ptr(), x.data_ptr(), 1e-10, 400000, mixed, cws.data_ptr(), cws.numel(), s,
                             allow_not_converged=True, inner_rtol=itol,
                             precond=mf.MF_PRECOND_JACOBI if pre else mf.MF_PRECOND_NONE)
         ev[1].record(stream)
@@ -410,6 +414,8 @@ def solve_run(args):
     print(json.dumps(out), flush=True)
     mf.mf_operator_destroy(op)
     mf.mf_mesh_destroy(mesh)
+    mf.mf_operator_destroy(op64)
+    mf.mf_mesh_destroy(mesh64)
 
 
 def serve_run(args):

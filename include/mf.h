@@ -57,7 +57,8 @@ enum { MF_LAPLACE = 0, MF_HELMHOLTZ = 1 };
  *   FP32 pipe (about 48 significant bits, results within 1e-12 of FP64), because GB300 issues
  *   64x more FP32 than FP64 FMAs per clock.
  * MF_FP32: float vectors, geometry and arithmetic.
- * MF_MIXED: as MF_FP64, plus an FP32 view for the inner solver of mf_cg_solve(mixed = 1).
+ * MF_MIXED: an FP32 view for the inner solver of mf_cg_solve(mixed = 1), and an FP64 view on
+ *   the native FP64 pipe for its outer residual (as MF_FP64_DFMA).
  * MF_FP64_DFMA: as MF_FP64 but the apply uses the native FP64 FMA pipe. */
 enum { MF_FP64 = 0, MF_FP32 = 1, MF_MIXED = 2, MF_FP64_DFMA = 3 };
 enum { MF_BC_NONE = 0, MF_BC_DIRICHLET0 = 1 };

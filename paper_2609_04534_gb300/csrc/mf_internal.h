@@ -235,9 +235,15 @@ enum { LAYOUT_TO_NATIVE = 0, LAYOUT_FROM_NATIVE = 1, LAYOUT_SCATTER_UNIQUE = 2, 
 // geometry components per point
 inline int geom_comps(const mf_operator* op) { return op->kind == MF_HELMHOLTZ ? 7 : 6; }
 
-// View kind of the FP64 apply (double-float compute unless native DFMA was requested) and
-// the view kind matching an element size.
-inline int fp64_view(const mf_operator* op) { return op->precision == MF_FP64_DFMA ? VK_F64 : VK_DD; }
+// View kind of the FP64 apply, and the view kind matching an element size.  MF_FP64 computes
+// in double-float.  MF_FP64_DFMA, and the FP64 view of MF_MIXED, use the native FP64 pipe:
+// the mixed solver applies it only for the outer residual b - A x (a few times per solve),
+// whose 53-bit evaluation keeps the true residual's floor well below the tolerances asked of
+// it (double-float evaluation noise, about 2^-48 relative per value, left curved Q6 64^3
+// requests stagnating near 1e-10).
+inline int fp64_view(const mf_operator* op) {
+  return (op->precision == MF_FP64_DFMA || op->precision == MF_MIXED) ? VK_F64 : VK_DD;
+}
 inline int view_of_elem(const mf_operator* op, int elem) { return elem == 8 ? fp64_view(op) : VK_F32; }
 
 // Reductions and CG vector kernels (mf_cg.cu)
