@@ -631,8 +631,6 @@ static mf_status launch_cg_vec(const mf_operator* op, int elem, void* x, void* r
   MF_SWITCH_N(op->n, cg_vec_e, op, elem, x, r, p, q, sc1, sc2, st, hist, s);
 }
 
-// One split-dual CG iteration: fused apply (p = r + beta p, q~ = A_K p, alpha) and the fused
-// update (q = G G^T q~, x, r, beta).
 template <int N>
 static mf_status cg_update_e(const mf_operator* op, int elem, void* x, void* r, void* p, void* q, const SolveWs& w,
                              CgState* st, double* hist, cudaStream_t s) {

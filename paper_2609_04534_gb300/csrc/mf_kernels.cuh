@@ -1,6 +1,7 @@
-// mf_kernels.cuh -- sum-factorised apply, duplicate summation (DSS), geometry and layout
-// kernels.  The apply kernels are templated on the storage type S of the vectors (double /
-// float), the compute type T (double, float, or double-float dd) and n = k+1.
+// mf_kernels.cuh -- sum-factorised apply, duplicate summation (DSS), geometry, diagonal and
+// layout kernels.  The apply kernels are templated on the storage type S of the vectors
+// (double, float, or double-float dd) and the compute type T (double, dd, or the FP32 pair f2),
+// and on n = k+1; each comes as a one-operator kernel and a batched kernel over several.
 //
 // Included once per degree by mf_apply_k<k>.cu so the eight degrees compile in parallel.
 #pragma once
@@ -13,7 +14,8 @@
 namespace mf {
 
 // Cells processed by one CTA of the apply kernels (a divisor of BL).  One thread owns one
-// pencil (a 1D line of n values) of one cell in every sweep, so a CTA has n^2 * CB threads.
+// pencil (a 1D line of n values) of one cell -- of two cells for f2 -- in every sweep, so a
+// CTA has n^2 * CB threads.
 // Launch configurations of the apply kernels, chosen per operator by the autotuner
 // (mf_operator_autotune): variant 0 = CB0 cells per CTA with registers capped for 2 resident
 // CTAs per SM; variant 1 = CB0/2 cells per CTA, capped for 3 resident CTAs per SM;
