@@ -667,8 +667,6 @@ static mf_status launch_cg_p(const mf_operator* op, int elem, const void* r, voi
                              cudaStream_t s) {
   MF_SWITCH_N(op->n, cg_p_e, op, elem, r, p, dinv, st, s);
 }
-// One split-dual iteration: apply with <p, A_K p> (alpha), update (q = G G^T q~, x, r, beta),
-// then p = r + beta p -- or, with fused_p, the apply forms p = r + beta p itself at load.
 // apply with <p, A_K p> partials, then alpha
 static mf_status launch_apply_alpha(const mf_operator* op, int elem, void* p, const void* r, void* q, const SolveWs& w,
                                    CgState* st, int fused_p, cudaStream_t s) {
@@ -679,6 +677,8 @@ static mf_status launch_apply_alpha(const mf_operator* op, int elem, void* p, co
   alpha_kernel<<<1, 1024, 0, s>>>(w.apart, nb, st);
   return cuda_check(cudaGetLastError(), "alpha launch");
 }
+// One split-dual iteration: apply with <p, A_K p> (alpha), update (q = G G^T q~, x, r, beta),
+// then p = z + beta p -- or, with fused_p, the apply forms p = r + beta p itself at load.
 static mf_status launch_cg_split(const mf_operator* op, int elem, void* x, void* r, void* p, void* q, const SolveWs& w,
                                  CgState* st, double* hist, int fused_p, cudaStream_t s) {
   mf_status rc = launch_apply_alpha(op, elem, p, r, q, w, st, fused_p, s);
