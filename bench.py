@@ -604,13 +604,13 @@ def main():
     # emulated arithmetic is the FP32 issue rate / 12, in FP64-equivalent FLOP/s.
     emu_peak = pk["fp32_tflops"] / 12.0
     # DRAM bytes of this kernel (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
-    # capture of the same kernel on the curved Q4 48^3 case: 75.8 bytes per cell-wise DoF,
+    # capture of the same kernel on the curved Q4 48^3 case: 79.0 bytes per cell-wise DoF,
     # scaled here to the bench's DoFs (traffic grows in proportion to the cells).
-    traffic = 75.80 * ncw
+    traffic = 79.02 * ncw
     roof = {"bound": "alu", "achieved": flops / t_fused / 1e12, "peak": emu_peak, "unit": "TFLOP/s",
             "frac": flops / t_fused / 1e12 / emu_peak, "traffic": traffic,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of apply_general<dd,dd,5,16,2,1,0> "
-                              "on Q4 curved 48^3 (13.82 M DoFs): 1047.8 MB, scaled by DoFs",
+                              "on Q4 curved 48^3 (13.82 M DoFs): 1092.3 MB, scaled by DoFs",
             "kernel": "apply_general<double,dd,5,curved,laplace> as the split-dual CG apply "
                       "(A_K p and <p, A_K p> at the quadrature points)",
             "kernel_ms": round(t_fused * 1e3, 4),

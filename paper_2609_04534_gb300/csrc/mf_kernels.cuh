@@ -433,7 +433,6 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
   load_tile<S, T, N, CB, NT>(a, t, lane0, buf0);
   __syncthreads();
   const int c = threadIdx.x % CB, p = threadIdx.x / CB, pa = p % N, pb = p / N;
-  const auto* Dc = tab.Dc;
   { // x-sweep with S, pencil (j=pa, k=pb), in place
     T in[N], out[N];
 #pragma unroll
@@ -465,8 +464,24 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
     Fold<T, N, true>(U).apply(tab.eD, d3);
   }
   __syncthreads();
-  // Per Gauss point (pa, pb, q): reference gradient (x and y parts from buf1), metric, and the
-  // fluxes v = G grad u; v1 -> buf0, v2 -> buf2, v3 stays in registers (Helmholtz: m u too).
+  { // x- and y-derivatives by Dc, folded like the z one: x-pencil (j=pa, k=pb) of buf1 -> buf0,
+    // y-pencil (i=pa, k=pb) of buf1 -> buf2
+    T in[N], out[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) in[i] = buf1[(i + N * pa + N2 * pb) * CB + c];
+    Fold<T, N, true>(in).apply(tab.eD, out);
+#pragma unroll
+    for (int q = 0; q < N; ++q) buf0[(q + N * pa + N2 * pb) * CB + c] = out[q];
+#pragma unroll
+    for (int j = 0; j < N; ++j) in[j] = buf1[(pa + N * j + N2 * pb) * CB + c];
+    Fold<T, N, true>(in).apply(tab.eD, out);
+#pragma unroll
+    for (int q = 0; q < N; ++q) buf2[(pa + N * q + N2 * pb) * CB + c] = out[q];
+  }
+  __syncthreads();
+  // Per Gauss point (pa, pb, q): reference gradient (d1 from buf0, d2 from buf2, d3 in
+  // registers), metric, and the fluxes v = G grad u, each written over its own derivative:
+  // v1 -> buf0, v2 -> buf2, v3 -> d3 (Helmholtz: m u too).
   // A fused CG step also sums grad u . v (+ m u^2): p_K^T A_K p_K of this pencil's points,
   // equal to the pairing of p with the split product written below (Lemma 1).
   const long long gbase = (t * NC * (long long)N3) * BL + lane0 + c * CellsPer<T>::value;
@@ -497,14 +512,7 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
 #pragma unroll
   for (int q = 0; q < N; ++q) {
     const int l = pa + N * pb + N2 * q;
-    T s1 = mul0(Dc[pa * N], buf1[(N * pb + N2 * q) * CB + c]);
-    T s2 = mul0(Dc[pb * N], buf1[(pa + N2 * q) * CB + c]);
-#pragma unroll
-    for (int r = 1; r < N; ++r) {
-      s1 = fma(Dc[pa * N + r], buf1[(r + N * pb + N2 * q) * CB + c], s1);
-      s2 = fma(Dc[pb * N + r], buf1[(pa + N * r + N2 * q) * CB + c], s2);
-    }
-    const T d1 = finish(s1), d2 = finish(s2);
+    const T d1 = buf0[l * CB + c], d2 = buf2[l * CB + c];
     T g0, g1, g2, g3, g4, g5, m = T(0);
     if constexpr (CURVED && IsF32<T>::value) {
       float gg[CPL][7];
@@ -543,19 +551,29 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
     if (HELM) U[q] = m * U[q];
   }
   __syncthreads();
+  { // Dc^T along x of v1: x-pencil (j=pa, k=pb) of buf0 -> buf1 (U there is no longer read);
+    // Dc^T along y of v2: y-pencil (i=pa, k=pb) of buf2, in place
+    T in[N], out[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) in[q] = buf0[(q + N * pa + N2 * pb) * CB + c];
+    Fold<T, N, true>(in).apply(tab.eDt, out);
+#pragma unroll
+    for (int i = 0; i < N; ++i) buf1[(i + N * pa + N2 * pb) * CB + c] = out[i];
+#pragma unroll
+    for (int q = 0; q < N; ++q) in[q] = buf2[(pa + N * q + N2 * pb) * CB + c];
+    Fold<T, N, true>(in).apply(tab.eDt, out);
+#pragma unroll
+    for (int j = 0; j < N; ++j) buf2[(pa + N * j + N2 * pb) * CB + c] = out[j];
+  }
+  __syncthreads();
   // t = Dc^T_x v1 + Dc^T_y v2 + Dc^T_z v3 (+ m u) at points (pa, pb, q), then S^T along z
   {
     T tq[N];
     Fold<T, N, true>(d3).apply(tab.eDt, tq); // Dc^T_z v3 along this pencil
 #pragma unroll
     for (int q = 0; q < N; ++q) {
-      T s = mul0(Dc[pa], buf0[(N * pb + N2 * q) * CB + c]);
-      s = fma(Dc[pb], buf2[(pa + N2 * q) * CB + c], s);
-#pragma unroll
-      for (int r = 1; r < N; ++r) {
-        s = fma(Dc[r * N + pa], buf0[(r + N * pb + N2 * q) * CB + c], s);
-        s = fma(Dc[r * N + pb], buf2[(pa + N * r + N2 * q) * CB + c], s);
-      }
+      const int l = pa + N * pb + N2 * q;
+      T s = add_lazy(buf1[l * CB + c], buf2[l * CB + c]);
       s = add_lazy(s, tq[q]);
       if (HELM) s = add_lazy(s, U[q]);
       tq[q] = finish(s);
