@@ -196,6 +196,20 @@ def time_kernels(mf, torch, op, x, y, stream_obj, reps):
     return ta / reps, td / reps
 
 
+def time_twin(mf, torch, op, x, y, stream_obj, reps):
+    """Device time of the apply kernel's stream twin: its grid and global loads and stores,
+    none of its arithmetic (the access pattern's ceiling)."""
+    s = stream_obj.cuda_stream
+    mf.mf_apply_stream_twin(op, x.data_ptr(), y.data_ptr(), s)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record(stream_obj)
+    for _ in range(reps):
+        mf.mf_apply_stream_twin(op, x.data_ptr(), y.data_ptr(), s)
+    e[1].record(stream_obj)
+    e[1].synchronize()
+    return e[0].elapsed_time(e[1]) / 1e3 / reps
+
+
 def cpu_baseline(N, k, curved, kind_helm, target_s=12.0):
     """The FP64 oracle (as it stands) on a bounded sample of cells of the same mesh, all
     host threads; reports cell-wise DoF/s of its apply."""
@@ -592,6 +606,7 @@ def main():
     # iteration launched kernel by kernel with CUDA events on the bench stream (both forms)
     t_apply = time_apply(mf, torch, op, b, y, stream, 20, 3)
     t_split, t_dss = time_kernels(mf, torch, op, b, y, stream, 10)
+    t_twin = time_twin(mf, torch, op, b, y, stream, 20)
     prof = {}
     for form, nm in ((mf.MF_CG_SPLIT_DUAL, "split_dual"), (mf.MF_CG_SPLIT_DUAL_FUSED, "split_dual_fused_p"),
                      (mf.MF_CG_ASSEMBLED, "assembled")):
@@ -662,10 +677,12 @@ def main():
             autotune(mf, torch, op, xx, s)
             t = time_apply(mf, torch, op, xx, yy, stream, 20, 3)
             ta, td = time_kernels(mf, torch, op, xx, yy, stream, 5)
+            tt = time_twin(mf, torch, op, xx, yy, stream, 20)
             gd = info["n_cellwise"] / t / 1e9
             applies[f"Q{kk}_{nm}"] = {"gdofs": round(gd, 3),
                                       "hbm_frac": round(info["algorithmic_bytes_per_apply"] / t / 1e9 / pk["hbm_gbs"], 4),
-                                      "apply_kernel_ms": round(ta * 1e3, 4), "dss_kernel_ms": round(td * 1e3, 4)}
+                                      "apply_kernel_ms": round(ta * 1e3, 4), "dss_kernel_ms": round(td * 1e3, 4),
+                                      "twin_kernel_ms": round(tt * 1e3, 4), "apply_over_twin": round(ta / tt, 3)}
             mf.mf_operator_destroy(op)
             mf.mf_mesh_destroy(mesh)
             del ws, xx, yy
@@ -707,7 +724,10 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(ncw, world),
             "apply_only": {"gdofs": round(ncw / t_apply / 1e9, 4), "hbm_frac_of_measured": round(hbm_frac_apply, 4),
-                           "apply_kernel_ms": round(t_split * 1e3, 4), "dss_kernel_ms": round(t_dss * 1e3, 4)},
+                           "apply_kernel_ms": round(t_split * 1e3, 4), "dss_kernel_ms": round(t_dss * 1e3, 4),
+                           # the same accesses without arithmetic (mf_apply_stream_twin)
+                           "twin_kernel_ms": round(t_twin * 1e3, 4),
+                           "twin_hbm_frac_of_measured": round(alg_bytes / t_twin / 1e9 / pk["hbm_gbs"], 4)},
             "cg_iteration_kernels_ms": {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in prof.items()},
             "roofline": roof,
             "apply_variant": variant,

@@ -149,6 +149,18 @@ mf_status mf_dss(const mf_operator* op, void* y_dev, void* stream);
  * bytes, 256-byte aligned), then every copy reads the sum back.  Consistent, but the order of
  * the atomic additions -- hence the last bits of the sums -- is not reproducible.  Same
  * precision as the operator's vectors; P y for Dirichlet. */
+size_t mf_dss_atomic_workspace_bytes(const mf_operator* op);
+mf_status mf_dss_atomic(const mf_operator* op, void* y_dev, void* scratch_dev, size_t scratch_bytes, void* stream);
+/* Stream twin of the apply kernel (a measurement entry: the paper times kernels that keep a
+ * kernel's memory accesses and drop its arithmetic, Sec. 6, as the ceiling of its access
+ * pattern).  One launch with the apply's grid and cells per CTA (the operator's launch
+ * variant) and its global accesses: the cell-wise x tile of every CTA is read; for a curved
+ * mesh in an FP64 precision the per-point metric (6 words per point, 7 for Helmholtz, 8 bytes
+ * each) is read as the apply streams it; y is written by x-pencils.  No contraction and no
+ * duplicate summation.  y_dev receives a bit-copy of x_dev, not an operator result.
+ * x_dev, y_dev: device, n_native elements of the operator's vector precision, caller-owned,
+ * distinct.  Errors: MF_ERR_ARG (NULL or equal vectors, operator not ready), MF_ERR_CUDA. */
+mf_status mf_apply_stream_twin(const mf_operator* op, const void* x_dev, void* y_dev, void* stream);
 /* The assembled diagonal of the operator (P A P for Dirichlet: 0 on constrained nodes), as a
  * consistent native vector of FP32 values (n_native floats), computed from the same
  * quadrature and metric as the apply, for Jacobi preconditioning of CG (the paper's smoother,
@@ -156,8 +168,6 @@ mf_status mf_dss(const mf_operator* op, void* y_dev, void* stream);
  * mf_diagonal_workspace_bytes() device bytes. */
 size_t mf_diagonal_workspace_bytes(const mf_operator* op);
 mf_status mf_diagonal(const mf_operator* op, float* diag_dev, void* scratch_dev, size_t scratch_bytes, void* stream);
-size_t mf_dss_atomic_workspace_bytes(const mf_operator* op);
-mf_status mf_dss_atomic(const mf_operator* op, void* y_dev, void* scratch_dev, size_t scratch_bytes, void* stream);
 /* End to end from host memory: copies canonical x_host to the device, applies, copies the
  * canonical result to y_host and synchronises `stream`.  Uses the caller's device
  * workspace of >= mf_apply_host_workspace_bytes() bytes. */

@@ -100,7 +100,7 @@ def lib() -> C.CDLL:
     L.mf_operator_info.argtypes = [vp, C.POINTER(mf_info)]
     L.mf_operator_setup.argtypes = [vp, vp, sz, vp]
     for nm in ("mf_to_native", "mf_from_native", "mf_scatter_unique", "mf_gather_unique", "mf_apply",
-               "mf_apply_split"):
+               "mf_apply_split", "mf_apply_stream_twin"):
         getattr(L, nm).argtypes = [vp, vp, vp, vp]
     L.mf_dss.argtypes = [vp, vp, vp]
     L.mf_apply_host_workspace_bytes.argtypes = [vp]
@@ -226,6 +226,11 @@ def mf_apply(op, x_ptr: int, y_ptr: int, stream: int = 0) -> None:
 
 def mf_apply_split(op, x_ptr: int, y_ptr: int, stream: int = 0) -> None:
     _check(lib().mf_apply_split(op, x_ptr, y_ptr, stream or None))
+
+
+def mf_apply_stream_twin(op, x_ptr: int, y_ptr: int, stream: int = 0) -> None:
+    """The apply kernel's memory accesses without its arithmetic; y receives a copy of x."""
+    _check(lib().mf_apply_stream_twin(op, x_ptr, y_ptr, stream or None))
 
 
 def mf_dss(op, y_ptr: int, stream: int = 0) -> None:

@@ -305,6 +305,16 @@ mf_status mf_dss_atomic(const mf_operator* op, void* y_dev, void* scratch_dev, s
   MF_DISPATCH_N(op->n, dss_atomic_n, op, elem_of(op), y_dev, scratch_dev, static_cast<cudaStream_t>(stream));
 }
 
+mf_status mf_apply_stream_twin(const mf_operator* op, const void* x_dev, void* y_dev, void* stream) {
+  mf_status st = check_ready(op, "mf_apply_stream_twin");
+  if (st) return st;
+  if (!x_dev || !y_dev || x_dev == y_dev) return set_error(MF_ERR_ARG, "mf_apply_stream_twin: bad vectors");
+  const int vk = view_of_elem(op, elem_of(op));
+  const void* geom = (vk != VK_F32 && op->path == PATH_CURVED) ? op->v64.geom : nullptr;
+  const int nc = geom ? geom_comps(op) : 0;
+  MF_DISPATCH_N(op->n, stream_twin_n, op, vk, x_dev, y_dev, geom, nc, static_cast<cudaStream_t>(stream));
+}
+
 mf_status mf_apply(const mf_operator* op, const void* x_dev, void* y_dev, void* stream) {
   mf_status st = mf_apply_split(op, x_dev, y_dev, stream);
   if (st) return st;

@@ -208,6 +208,9 @@ mf_status dss_n(const mf_operator* op, int elem, void* y, cudaStream_t s);
 template <int N>
 mf_status dss_atomic_n(const mf_operator* op, int elem, void* y, void* acc, cudaStream_t s);
 template <int N>
+mf_status stream_twin_n(const mf_operator* op, int vk, const void* x, void* y, const void* geom, int nc,
+                        cudaStream_t s);
+template <int N>
 mf_status diagonal_n(const mf_operator* op, float* diag, float* gtab, cudaStream_t s);
 // assembled diagonal (FP32, consistent, 0 on Dirichlet nodes); gtab: diag_table_bytes(op) bytes
 mf_status launch_diagonal(const mf_operator* op, float* diag, float* gtab, cudaStream_t s);

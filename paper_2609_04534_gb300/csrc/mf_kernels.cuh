@@ -772,6 +772,81 @@ mf_status dss_atomic_n(const mf_operator* op, int elem, void* y, void* acc, cuda
 }
 
 // ---------------------------------------------------------------------------------------
+// Stream twin of the apply (Sec. 6 times such memory-only kernels as the ceiling of an access
+// pattern): the apply's grid and cells per CTA (CC) and its global accesses -- the x tile read
+// into shared memory, the NC metric words of every point of the thread's z pencil read as the
+// streamed geometry, y written by x-pencils -- and none of the contractions.  y is a bit-copy
+// of x: the metric words are folded by XOR and tested against a mask that the host passes as
+// zero, which keeps their loads live without changing y.
+// ---------------------------------------------------------------------------------------
+template <typename E, int N, int CC, int NC>
+__global__ void __launch_bounds__(N * N * CC) stream_twin_kernel(const E* __restrict__ x, E* __restrict__ y,
+                                                                  const unsigned long long* __restrict__ geom,
+                                                                  unsigned long long mask) {
+  constexpr int N2 = N * N, N3 = N2 * N, NT = N2 * CC, GPT = BL / CC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  E* buf = reinterpret_cast<E*>(smem_raw);
+  const long long t = blockIdx.x / GPT;
+  const int lane0 = (int)(blockIdx.x % GPT) * CC;
+  const long long base = t * (long long)N3 * BL + lane0;
+  for (int idx = threadIdx.x; idx < N3 * CC; idx += NT) {
+    const int l = idx / CC, c = idx - l * CC;
+    buf[idx] = x[base + (long long)l * BL + c];
+  }
+  __syncthreads();
+  const int c = threadIdx.x % CC, p = threadIdx.x / CC, pa = p % N, pb = p / N;
+  if constexpr (NC > 0) {
+    const unsigned long long* gp = geom + t * (long long)NC * N3 * BL + lane0 + c;
+    unsigned long long acc = 0;
+#pragma unroll
+    for (int q = 0; q < N; ++q)
+#pragma unroll
+      for (int m = 0; m < NC; ++m) acc ^= gp[(long long)(m * N3 + pa + N * pb + N2 * q) * BL];
+    if ((acc & mask) != 0) buf[(pa + N * pb) * CC + c] = E(0);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const int l = i + N * pa + N2 * pb;
+    y[base + (long long)l * BL + c] = buf[l * CC + c];
+  }
+}
+template <typename E, int N, int CC>
+static mf_status stream_twin_cc(const mf_operator* op, const void* x, void* y, const void* geom, int nc,
+                                cudaStream_t s) {
+  constexpr int NT = N * N * CC;
+  const long long blocks = op->g.ntiles * (BL / CC);
+  const size_t smem = sizeof(E) * N * N * N * CC;
+  if (blocks <= 0) return MF_OK;
+  void (*k)(const E*, E*, const unsigned long long*, unsigned long long) =
+      nc == 7 ? stream_twin_kernel<E, N, CC, 7> : (nc == 6 ? stream_twin_kernel<E, N, CC, 6> : stream_twin_kernel<E, N, CC, 0>);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(stream twin)");
+  }
+  k<<<(unsigned)blocks, NT, smem, s>>>(static_cast<const E*>(x), static_cast<E*>(y),
+                                       static_cast<const unsigned long long*>(geom), 0ull);
+  return cuda_check(cudaGetLastError(), "stream twin launch");
+}
+// vk: the view mf_apply uses; geom / nc: the streamed metric (nullptr / 0 when there is none).
+// Cells per CTA follow the view's compute type and the operator's launch variant.
+template <int N>
+mf_status stream_twin_n(const mf_operator* op, int vk, const void* x, void* y, const void* geom, int nc,
+                        cudaStream_t s) {
+  const bool half = op->variant[vk == VK_DDS ? VK_DD : vk] != 0;
+  if (vk == VK_F32) {
+    using C0 = Cfg<FP32C, N, 0>;
+    using CH = Cfg<FP32C, N, 1>;
+    return half ? stream_twin_cc<unsigned, N, CH::CB * CH::CPL>(op, x, y, nullptr, 0, s)
+                : stream_twin_cc<unsigned, N, C0::CB * C0::CPL>(op, x, y, nullptr, 0, s);
+  }
+  using D0 = Cfg<dd, N, 0>;
+  using DH = Cfg<dd, N, 1>;
+  return half ? stream_twin_cc<unsigned long long, N, DH::CB>(op, x, y, geom, nc, s)
+              : stream_twin_cc<unsigned long long, N, D0::CB>(op, x, y, geom, nc, s);
+}
+
+// ---------------------------------------------------------------------------------------
 // Per-point geometry of the curved map (Sec. 2: six metric entries plus det J per point):
 // G = w |det J| J^-1 J^-T (xx,xy,xz,yy,yz,zz) and, for Helmholtz, m = w |det J| c_m, computed
 // in FP64 from the analytic Jacobian and stored in T, layout [tile][comp][l][lane].
@@ -1307,6 +1382,8 @@ mf_status layout_n(const mf_operator* op, int elem, int mode, const void* in, vo
                                     int, long long*, cudaStream_t);                                     \
   template mf_status dss_n<NN>(const mf_operator*, int, void*, cudaStream_t);                           \
   template mf_status dss_atomic_n<NN>(const mf_operator*, int, void*, void*, cudaStream_t);              \
+  template mf_status stream_twin_n<NN>(const mf_operator*, int, const void*, void*, const void*, int,    \
+                                       cudaStream_t);                                                   \
   template mf_status diagonal_n<NN>(const mf_operator*, float*, float*, cudaStream_t);                   \
   template mf_status apply_batch_fill_n<NN>(const BatchMember*, int, int, void*, long long*);            \
   template mf_status apply_batch_launch_n<NN>(const mf_operator*, int, const void*, const long long*, int,  \

@@ -287,3 +287,32 @@ def test_atomic_dss_ablation_matches_sweep_dss(prec, dims, k, bc):
     torch.cuda.synchronize()
     assert torch.equal(back, y_atomic)
     d.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("geom,kind,prec,k,dims", [
+    ("curved", mf.MF_LAPLACE, mf.MF_FP64, 4, (5, 6, 3)),
+    ("curved", mf.MF_HELMHOLTZ, mf.MF_FP64, 1, (9, 5, 3)),
+    ("curved", mf.MF_LAPLACE, mf.MF_FP64, 8, (5, 2, 3)),
+    ("curved", mf.MF_HELMHOLTZ, mf.MF_FP64_DFMA, 2, (5, 6, 3)),
+    ("curved", mf.MF_LAPLACE, mf.MF_MIXED, 3, (5, 6, 3)),
+    ("curved", mf.MF_LAPLACE, mf.MF_FP32, 3, (5, 6, 3)),
+    ("curved", mf.MF_HELMHOLTZ, mf.MF_FP32, 8, (5, 2, 3)),
+    ("cart", mf.MF_HELMHOLTZ, mf.MF_FP64, 5, (5, 6, 3)),
+    ("shear", mf.MF_LAPLACE, mf.MF_FP32, 6, (5, 2, 3)),
+])
+def test_stream_twin_copies_x(geom, kind, prec, k, dims, variant):
+    """The stream twin (the apply's accesses without its arithmetic) writes every native
+    element, padding lanes included, as a bit-copy of x, for every view and launch variant."""
+    d = DevOp(*dims, k, geom, kind, 1.0, prec, 0)
+    mf.mf_operator_set_variant(d.op, variant)
+    g = torch.Generator(device="cuda").manual_seed(11)
+    x = torch.randn(d.n_native, dtype=d.dtype, device="cuda", generator=g)
+    y = torch.full_like(x, float("nan"))
+    mf.mf_apply_stream_twin(d.op, x.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    ib = torch.int64 if d.dtype == torch.float64 else torch.int32
+    assert torch.equal(y.view(ib), x.view(ib))
+    with pytest.raises(mf.MfError):
+        mf.mf_apply_stream_twin(d.op, x.data_ptr(), x.data_ptr())
+    d.close()
