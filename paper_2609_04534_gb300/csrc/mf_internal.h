@@ -48,9 +48,10 @@ struct EoTab {
   static constexpr int H = N / 2, HE = (N + 1) / 2;
   T F[H * HE], G[H * H > 0 ? H * H : 1], Mid[HE];
 };
+// What the apply kernels read: the Gauss weights and every 1D matrix in even-odd form.
 template <typename T, int N>
 struct Tab {
-  T S[N * N], Dc[N * N], W[N], M[N * N], K[N * N];
+  T W[N];
   EoTab<T, N> eS, eSt, eD, eDt, eM, eK; // S, S^T, Dc, Dc^T, M, K
 };
 

@@ -1127,15 +1127,7 @@ static void fill_tab(const mf_operator* op, Tab<T, N>& tab) {
   fill_eo<T, N>(h.Dc, true, tab.eDt);
   fill_eo<T, N>(h.M, false, tab.eM);
   fill_eo<T, N>(h.K, false, tab.eK);
-  for (int q = 0; q < N; ++q) {
-    tab.W[q] = host_from_double<T>(h.qw[q]);
-    for (int i = 0; i < N; ++i) {
-      tab.S[q * N + i] = host_from_double<T>(h.S[q * MAXN + i]);
-      tab.Dc[q * N + i] = host_from_double<T>(h.Dc[q * MAXN + i]);
-      tab.M[q * N + i] = host_from_double<T>(h.M[q * MAXN + i]);
-      tab.K[q * N + i] = host_from_double<T>(h.K[q * MAXN + i]);
-    }
-  }
+  for (int q = 0; q < N; ++q) tab.W[q] = host_from_double<T>(h.qw[q]);
 }
 
 // L2 prefetch distance of an apply launch: MF_PREFETCH_WAVES waves of resident CTAs, in
