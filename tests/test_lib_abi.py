@@ -72,10 +72,11 @@ def test_operator_argument_validation_and_info(L):
     # FP64 view streams 7 values per point; the FP32 view keeps sin/cos tables per cell layer
     assert info["geom_bytes"] == 7 * info["n_native"] * 8 + 4 * 2 * (5 + 6 + 3) * 5
     assert info["algorithmic_bytes_per_apply"] == (16 + 7 * 8) * info["n_cellwise"]
-    # not set up yet: apply must refuse without touching the GPU
-    with pytest.raises(mf.MfError) as e:
-        mf.mf_apply(op, 16, 32)
-    assert e.value.code == mf.MF_ERR_ARG
+    # not set up yet: apply and its stream twin must refuse without touching the GPU
+    for fn in (mf.mf_apply, mf.mf_apply_stream_twin):
+        with pytest.raises(mf.MfError) as e:
+            fn(op, 16, 32)
+        assert e.value.code == mf.MF_ERR_ARG
     # workspace too small
     with pytest.raises(mf.MfError) as e:
         mf.mf_operator_setup(op, 256, 1024)
@@ -96,6 +97,13 @@ def test_operator_argument_validation_and_info(L):
     mf.mf_operator_destroy(op)
     mf.mf_mesh_destroy(mc)
     mf.mf_mesh_destroy(m)
+
+
+def test_stream_twin_argument_validation(L):
+    with pytest.raises(mf.MfError) as e:
+        mf.mf_apply_stream_twin(None, 16, 32)
+    assert e.value.code == mf.MF_ERR_ARG
+    assert "NULL operator" in mf.last_error()
 
 
 def test_sheared_affine_selects_general_path(L):
