@@ -635,6 +635,8 @@ def main():
     alg_bytes = info["algorithmic_bytes_per_apply"]
     hbm_frac_apply = alg_bytes / t_apply / 1e9 / pk["hbm_gbs"]
     roof["hbm_frac_of_measured"] = alg_bytes / t_fused / 1e9 / pk["hbm_gbs"]
+    # achieved bandwidth both ways: algorithmic bytes / time (above) and ncu DRAM bytes / time
+    roof["dram_gbs_from_traffic"] = traffic / t_fused / 1e9
 
     # e2e through the public API from host memory: pinned b in, x out, K CG iterations
     e2e = None
