@@ -143,6 +143,16 @@ mf_status mf_apply(const mf_operator* op, const void* x_dev, void* y_dev, void* 
 mf_status mf_apply_split(const mf_operator* op, const void* x_dev, void* y_dev, void* stream);
 /* In-place duplicate summation y <- G G^T y (and P y for Dirichlet). */
 mf_status mf_dss(const mf_operator* op, void* y_dev, void* stream);
+/* In place: every copy of a shared node is replaced by the average of that node's copies,
+ * y <- G diag(1/m) G^T y with m the multiplicity (1, 2, 4 or 8 copies), i.e. the assembly
+ * G^T of Sec. 4, Eq. (shadow_assembly), divided by the number of cells sharing the node,
+ * then the gather G of Eq. (shadow_gather).  Turns any cell-wise vector into a consistent
+ * one (a projection: consistent vectors are left unchanged).  The copies are summed in the
+ * canonical order of mf_dss and scaled by 1/m (exact), so all copies come out bitwise equal.
+ * No Dirichlet mask is applied.  y_dev: native vector of the operator's element type,
+ * caller-owned; padding lanes are left as they are.  Errors: MF_ERR_ARG (NULL argument),
+ * MF_ERR_CUDA. */
+mf_status mf_make_consistent(const mf_operator* op, void* y_dev, void* stream);
 /* Ablation of the duplicate summation (a measurement entry; the paper compares its layer-
  * disjoint sweeps against an atomic variant in Sec. 6): every copy atomically adds its value
  * into an accumulator over unique nodes (scratch: mf_dss_atomic_workspace_bytes() device
@@ -206,9 +216,13 @@ mf_status mf_dot(const mf_operator* op, const void* a_dev, const void* b_dev, in
  * mf_dot within rounding (same weights, FP64 accumulation, fixed order; a different CTA
  * split).  Its scratch is a 512 KiB static device array inside libmf (held by every GPU
  * that loads the library until exit): vectors with n_native > 134,217,728 elements are
- * rejected with MF_ERR_ARG.  The first call on a device looks up that array's address with
- * the device current; make it before any stream capture.  All calls share the array:
- * calls that overlap on the GPU race, so serialise them.  Calls no allocating routine. */
+ * rejected with MF_ERR_ARG, as is an operator that has not been set up (mf_operator_setup),
+ * both before any CUDA call.  The first successful call on a device looks up that array's
+ * address with the device current and caches it per device for the life of the process
+ * (a failed lookup is not cached: the next call retries); make that first call before any
+ * stream capture.  The cached address is invalid after cudaDeviceReset.  All calls share the
+ * array: calls that overlap on the GPU race, so serialise them.  Calls no allocating
+ * routine. */
 mf_status mf_dot_noalloc(const mf_operator* op, const void* a_dev, const void* b_dev, int split, double* result_dev,
                          void* stream);
 

@@ -103,6 +103,7 @@ def lib() -> C.CDLL:
                "mf_apply_split", "mf_apply_stream_twin"):
         getattr(L, nm).argtypes = [vp, vp, vp, vp]
     L.mf_dss.argtypes = [vp, vp, vp]
+    L.mf_make_consistent.argtypes = [vp, vp, vp]
     L.mf_apply_host_workspace_bytes.argtypes = [vp]
     L.mf_apply_host_workspace_bytes.restype = sz
     L.mf_apply_host.argtypes = [vp, vp, vp, vp, sz, vp]
@@ -218,6 +219,11 @@ def mf_scatter_unique(op, unique_ptr: int, native_ptr: int, stream: int = 0) -> 
 
 def mf_gather_unique(op, native_ptr: int, unique_ptr: int, stream: int = 0) -> None:
     _check(lib().mf_gather_unique(op, native_ptr, unique_ptr, stream or None))
+
+
+def mf_make_consistent(op, native_ptr: int, stream: int = 0) -> None:
+    """In place: every copy of a shared node becomes the average of its copies."""
+    _check(lib().mf_make_consistent(op, native_ptr, stream or None))
 
 
 def mf_apply(op, x_ptr: int, y_ptr: int, stream: int = 0) -> None:

@@ -283,6 +283,11 @@ mf_status mf_dss(const mf_operator* op, void* y_dev, void* stream) {
   return launch_dss(op, elem_of(op), y_dev, static_cast<cudaStream_t>(stream));
 }
 
+mf_status mf_make_consistent(const mf_operator* op, void* y_dev, void* stream) {
+  if (!op || !y_dev) return set_error(MF_ERR_ARG, "mf_make_consistent: NULL argument");
+  MF_DISPATCH_N(op->n, make_consistent_n, op, elem_of(op), y_dev, static_cast<cudaStream_t>(stream));
+}
+
 size_t mf_diagonal_workspace_bytes(const mf_operator* op) { return op ? diag_table_bytes(op) : 0; }
 
 mf_status mf_diagonal(const mf_operator* op, float* diag_dev, void* scratch_dev, size_t scratch_bytes, void* stream) {

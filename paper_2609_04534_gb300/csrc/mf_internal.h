@@ -207,6 +207,8 @@ mf_status apply_cg_n(const mf_operator* op, int vk, void* p, const void* r, void
 template <int N>
 mf_status dss_n(const mf_operator* op, int elem, void* y, cudaStream_t s);
 template <int N>
+mf_status make_consistent_n(const mf_operator* op, int elem, void* y, cudaStream_t s);
+template <int N>
 mf_status dss_atomic_n(const mf_operator* op, int elem, void* y, void* acc, cudaStream_t s);
 template <int N>
 mf_status stream_twin_n(const mf_operator* op, int vk, const void* x, void* y, const void* geom, int nc,

@@ -680,8 +680,11 @@ __device__ __forceinline__ int copies_1d(long long I, int ncell, int k, int* cel
   return 1;
 }
 
+// avg = 1: the average of the copies instead of their sum (mf_make_consistent): the sum in
+// the same canonical order times 1/multiplicity (a power of two, so exact), and no Dirichlet
+// mask.
 template <typename T, int N>
-__global__ void dss_kernel(T* __restrict__ y, GridInfo g) {
+__global__ void dss_kernel(T* __restrict__ y, GridInfo g, int avg) {
   constexpr int K = N - 1, N2 = N * N, N3 = N2 * N;
   const long long NX = (long long)g.nx * K + 1, NY = (long long)g.ny * K + 1, NZ = (long long)g.nz * K + 1;
   const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -691,7 +694,7 @@ __global__ void dss_kernel(T* __restrict__ y, GridInfo g) {
   const int mx = copies_1d(I, g.nx, K, cx, ix);
   const int my = copies_1d(J, g.ny, K, cy, iy);
   const int mz = copies_1d(L, g.nz, K, cz, iz);
-  const bool bnd = g.bc && (I == 0 || I == NX - 1 || J == 0 || J == NY - 1 || L == 0 || L == NZ - 1);
+  const bool bnd = !avg && g.bc && (I == 0 || I == NX - 1 || J == 0 || J == NY - 1 || L == 0 || L == NZ - 1);
   if (mx * my * mz == 1 && !bnd) return;
   long long addr[8];
   T s = T(0);
@@ -711,6 +714,7 @@ __global__ void dss_kernel(T* __restrict__ y, GridInfo g) {
     sz[zz] = (my == 2) ? sy[0] + sy[1] : sy[0];
   }
   s = (mz == 2) ? sz[0] + sz[1] : sz[0];
+  if (avg) s = s * (T(1) / T(mx * my * mz));
   if (bnd) s = T(0);
   for (int zz = 0; zz < mz; ++zz)
     for (int yy = 0; yy < my; ++yy)
@@ -1321,13 +1325,21 @@ mf_status apply_batch_launch_n(const mf_operator* op0, int vk, const void* jobs_
   return batch_launch_t<double, double, N>(op0, v, jobs_dev, block0_dev, njobs, blocks, s);
 }
 template <int N>
-mf_status dss_n(const mf_operator* op, int elem, void* y, cudaStream_t s) {
+static mf_status dss_mode(const mf_operator* op, int elem, void* y, int avg, cudaStream_t s) {
   const long long total = op->n_unique;
   const int thr = 256;
   const long long blocks = (total + thr - 1) / thr;
-  if (elem == 8) dss_kernel<double, N><<<(unsigned)blocks, thr, 0, s>>>(static_cast<double*>(y), op->g);
-  else dss_kernel<float, N><<<(unsigned)blocks, thr, 0, s>>>(static_cast<float*>(y), op->g);
+  if (elem == 8) dss_kernel<double, N><<<(unsigned)blocks, thr, 0, s>>>(static_cast<double*>(y), op->g, avg);
+  else dss_kernel<float, N><<<(unsigned)blocks, thr, 0, s>>>(static_cast<float*>(y), op->g, avg);
   return cuda_check(cudaGetLastError(), "dss launch");
+}
+template <int N>
+mf_status dss_n(const mf_operator* op, int elem, void* y, cudaStream_t s) {
+  return dss_mode<N>(op, elem, y, 0, s);
+}
+template <int N>
+mf_status make_consistent_n(const mf_operator* op, int elem, void* y, cudaStream_t s) {
+  return dss_mode<N>(op, elem, y, 1, s);
 }
 
 template <int N>
@@ -1373,6 +1385,7 @@ mf_status layout_n(const mf_operator* op, int elem, int mode, const void* in, vo
   template mf_status apply_cg_n<NN>(const mf_operator*, int, void*, const void*, void*, CgState*, double*, \
                                     int, long long*, cudaStream_t);                                     \
   template mf_status dss_n<NN>(const mf_operator*, int, void*, cudaStream_t);                           \
+  template mf_status make_consistent_n<NN>(const mf_operator*, int, void*, cudaStream_t);               \
   template mf_status dss_atomic_n<NN>(const mf_operator*, int, void*, void*, cudaStream_t);              \
   template mf_status stream_twin_n<NN>(const mf_operator*, int, const void*, void*, const void*, int,    \
                                        cudaStream_t);                                                   \

@@ -13,9 +13,13 @@
 //    ceil(n_native / 2048) partials; the static array holds 65536 of them (512 KiB + 256 B,
 //    held by every GPU that loads the library until the process exits).  Vectors longer than
 //    65536 * 2048 = 134,217,728 elements are rejected with MF_ERR_ARG before any GPU work.
-//  - The first call on each device resolves the array's device address with
-//    cudaGetSymbolAddress while that device is current; later calls on that device reuse it.
-//    Make that first call before any stream capture.
+//  - An operator that has not been set up is rejected (after the size check, before any
+//    CUDA call), so a call with a bad operator never reaches a launch.
+//  - The first successful call on each device resolves the array's device address with
+//    cudaGetSymbolAddress while that device is current and caches it per device; later calls
+//    on that device reuse it.  A failed lookup is not cached: the next call retries it.  Make
+//    that first call before any stream capture.  The cached address is invalid after
+//    cudaDeviceReset (the module, and with it the array, is reloaded).
 //  - Every call shares the one array: the done-counter is cleared (cudaMemsetAsync) at the
 //    start of each call, and the partials are rewritten before they are read.  Calls whose
 //    executions overlap on the GPU (on different streams, or on different host threads)
@@ -42,9 +46,23 @@ struct NoAllocScratch {
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
 constexpr int NA_MAX_DEVICES = 64;
-NoAllocScratch* g_scratch_ptr[NA_MAX_DEVICES];
-cudaError_t g_scratch_err[NA_MAX_DEVICES];
-std::once_flag g_scratch_once[NA_MAX_DEVICES];
+NoAllocScratch* g_scratch_ptr[NA_MAX_DEVICES]; // resolved addresses (null: not resolved yet)
+std::mutex g_scratch_mu;
+
+// The array's device address on the current device `dev`, resolved on first use; only a
+// successful lookup is cached.
+cudaError_t scratch_address(int dev, NoAllocScratch** out) {
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    if (!p) return cudaErrorInvalidSymbol;
+    g_scratch_ptr[dev] = static_cast<NoAllocScratch*>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return cudaSuccess;
+}
 
 // Weight of native element e in the assembled pairing: 1/multiplicity of its node (exact,
 // a power of two), 1 for every real copy when split, 0 for padding lanes.
@@ -141,20 +159,14 @@ extern "C" mf_status mf_dot_noalloc(const mf_operator* op, const void* a_dev, co
                      "reduction scratch (use mf_dot with caller scratch)",
                      op->n_native, (long long)NA_MAX_PARTIALS * NA_CHUNK);
   if (blocks == 0) return set_error(MF_ERR_ARG, "mf_dot_noalloc: empty vector");
+  if (!op->ready) return set_error(MF_ERR_ARG, "mf_dot_noalloc: operator not set up (mf_operator_setup)");
   int dev = -1;
   mf_status st = cuda_check(cudaGetDevice(&dev), "mf_dot_noalloc: cudaGetDevice");
   if (st) return st;
   if (dev < 0 || dev >= NA_MAX_DEVICES) return set_error(MF_ERR_ARG, "mf_dot_noalloc: device %d not supported", dev);
-  std::call_once(g_scratch_once[dev], [dev]() {
-    void* p = nullptr;
-    g_scratch_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    g_scratch_ptr[dev] = static_cast<NoAllocScratch*>(p);
-  });
-  if (g_scratch_err[dev] != cudaSuccess || !g_scratch_ptr[dev])
-    return cuda_check(g_scratch_err[dev] != cudaSuccess ? g_scratch_err[dev] : cudaErrorInvalidSymbol,
-                      "mf_dot_noalloc: cudaGetSymbolAddress");
+  NoAllocScratch* sc = nullptr;
+  if ((st = cuda_check(scratch_address(dev, &sc), "mf_dot_noalloc: cudaGetSymbolAddress"))) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  NoAllocScratch* sc = g_scratch_ptr[dev];
   if ((st = cuda_check(cudaMemsetAsync(&sc->counter, 0, sizeof(unsigned int), s), "mf_dot_noalloc: clear counter")))
     return st;
   const int elem = op->precision == MF_FP32 ? 4 : 8;

@@ -120,6 +120,37 @@ def test_layout_round_trip():
     d.close()
 
 
+@pytest.mark.parametrize("prec,bc", [(mf.MF_FP64, 0), (mf.MF_FP32, 0), (mf.MF_FP64, 1)])
+@pytest.mark.parametrize("k,dims", [(1, (5, 6, 3)), (3, (5, 6, 3)), (6, (5, 2, 3))])
+def test_make_consistent_is_average_of_copies(oracle, prec, bc, k, dims):
+    """mf_make_consistent against the oracle's assembly G^T divided by the multiplicity
+    (assemble(1)), gathered back to every copy (Sec. 4, Eqs. (shadow_gather),
+    (shadow_assembly)); no Dirichlet mask.  All copies bitwise equal; a consistent vector
+    is left unchanged."""
+    d = DevOp(*dims, k, "cart", mf.MF_LAPLACE, 1.0, prec, bc)
+    o = oracle_op(oracle, *dims, k, "cart", 0.0, bc)
+    rng = np.random.default_rng(7)
+    ycw = rng.uniform(-1.0, 1.0, d.n_cw)  # independent copies: not consistent
+    if prec == mf.MF_FP32:
+        ycw = ycw.astype(np.float32).astype(np.float64)
+    dt = torch.float32 if prec == mf.MF_FP32 else torch.float64
+    can = torch.as_tensor(ycw, dtype=dt, device="cuda")
+    nat = torch.empty(d.n_native, dtype=dt, device="cuda")
+    mf.mf_to_native(d.op, can.data_ptr(), nat.data_ptr())
+    mf.mf_make_consistent(d.op, nat.data_ptr())
+    got = d.canonical_from_native(nat)
+    ref = o.scatter(o.assemble(ycw) / o.assemble(np.ones(d.n_cw)))
+    assert rel_max(got, ref) <= (1e-6 if prec == mf.MF_FP32 else 1e-15)
+    # every copy of a node equal: gathering one copy and scattering it back changes nothing
+    back = d.native_from_unique(d.unique_from_native(nat))
+    assert torch.equal(back, nat)
+    # idempotent (a projection onto consistent vectors)
+    again = nat.clone()
+    mf.mf_make_consistent(d.op, again.data_ptr())
+    assert torch.equal(again, nat)
+    d.close()
+
+
 @pytest.mark.parametrize("prec", [mf.MF_FP64, mf.MF_FP32])
 def test_dot_products(oracle, prec):
     """Assembled dot over unique nodes (1/multiplicity weights) and the Lemma 1 pairing of a

@@ -106,6 +106,36 @@ def test_stream_twin_argument_validation(L):
     assert "NULL operator" in mf.last_error()
 
 
+def test_noalloc_dot_rejects_on_the_host(L):
+    """mf_dot_noalloc refuses on the host, before any CUDA call: a vector longer than its
+    static scratch (134,217,728 native elements), then an operator that was never set up.
+    The pointers are never dereferenced: no operator here is set up, so even a regressed
+    size check stops at the set-up check."""
+    mesh = mf.mf_mesh_create(256, 256, 128)
+    op = mf.mf_operator_create(mesh, 3)
+    assert mf.mf_operator_info(op)["n_native"] > 134_217_728
+    with pytest.raises(mf.MfError) as e:
+        mf.mf_dot_noalloc(op, 256, 512, 1024)
+    assert e.value.code == mf.MF_ERR_ARG
+    assert "limit" in str(e.value)
+    mf.mf_operator_destroy(op)
+    mf.mf_mesh_destroy(mesh)
+    mesh = mf.mf_mesh_create(4, 4, 4)
+    op = mf.mf_operator_create(mesh, 3)
+    with pytest.raises(mf.MfError) as e:
+        mf.mf_dot_noalloc(op, 256, 512, 1024)
+    assert e.value.code == mf.MF_ERR_ARG
+    assert "not set up" in str(e.value)
+    mf.mf_operator_destroy(op)
+    mf.mf_mesh_destroy(mesh)
+
+
+def test_make_consistent_argument_validation(L):
+    with pytest.raises(mf.MfError) as e:
+        mf.mf_make_consistent(None, 16)
+    assert e.value.code == mf.MF_ERR_ARG
+
+
 def test_sheared_affine_selects_general_path(L):
     m = mf.mf_mesh_create(2, 2, 2, mf.MF_AFFINE, [1, 0.3, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0])
     op = mf.mf_operator_create(m, 2)
