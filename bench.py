@@ -300,11 +300,16 @@ def profile_apply(args):
     with torch.cuda.stream(stream):
         x = random_native(mf, torch, op, info, N, k, 1, dt, s)
         y = torch.empty_like(x)
-    for v in ([args.variant] if args.variant >= 0 else [0, 1, 2]):
+    tensor = mf.mf_operator_get_variant(op) == mf.MF_VARIANT_TENSOR
+    for v in ([args.variant] if args.variant >= 0 else [0, 1, 2] + ([mf.MF_VARIANT_TENSOR] if tensor else [])):
         mf.mf_operator_set_variant(op, v)
         t = time_apply(mf, torch, op, x, y, stream, args.reps, 1)
+        ta, td = time_kernels(mf, torch, op, x, y, stream, args.reps)
         print(json.dumps({"case": args.profile_apply, "variant": v, "n_cellwise": info["n_cellwise"],
-                          "ms": round(t * 1e3, 4), "gdofs": round(info["n_cellwise"] / t / 1e9, 3)}), flush=True)
+                          "ms": round(t * 1e3, 4), "gdofs": round(info["n_cellwise"] / t / 1e9, 3),
+                          "apply_kernel_ms": round(ta * 1e3, 4), "dss_kernel_ms": round(td * 1e3, 4),
+                          "apply_kernel_hbm_frac": round(info["algorithmic_bytes_per_apply"] / ta / 1e9 / peaks()["hbm_gbs"], 4)}),
+              flush=True)
     mf.mf_operator_destroy(op)
     mf.mf_mesh_destroy(mesh)
 

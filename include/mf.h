@@ -109,17 +109,38 @@ mf_status mf_operator_setup(mf_operator* op, void* workspace_dev, size_t bytes, 
 
 /* Autotuner: times each launch configuration of the apply kernel (variant 0: n^2 x CB
  * threads per CTA, registers capped for two CTAs per SM; variant 1: half the cells per CTA,
- * capped for three; variant 2: half the cells per CTA, no register cap)
- * with `reps` applies of x_dev into y_dev (both native vectors of this operator; y is
- * overwritten) and keeps the fastest.  The choice is cached per (device, degree, path,
- * kind, precision) for the life of the process, so later operators of the same class reuse
- * it without timing.  Synchronises `stream`.  Results do not depend on the variant (each
- * thread runs the same arithmetic), only speed does. */
+ * capped for three; variant 2: half the cells per CTA, no register cap; variant 3, for
+ * MF_FP64 operators on an axis-aligned affine mesh of degree 1..3 only: the tensor-core
+ * apply, see MF_VARIANT_TENSOR) with `reps` applies of x_dev into y_dev (both native vectors
+ * of this operator; y is overwritten) and keeps the fastest.  The choice is cached per
+ * (device, degree, path, kind, precision) for the life of the process, so later operators of
+ * the same class reuse it without timing.  Synchronises `stream`.  Variants 0-2 run the same
+ * per-thread arithmetic and give bitwise equal results; variant 3 rounds differently (same
+ * accuracy class), so its results agree with theirs within 1e-12 relative max-norm. */
 mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, int reps, void* stream);
-/* Forces a launch variant (0, 1 or 2) for every precision view; returns MF_ERR_ARG otherwise. */
+/* The tensor-core apply of the FP64 Cartesian operator (degree 1..3; the default launch
+ * variant of such operators).  All cells of an axis-aligned uniform mesh share one element
+ * matrix A_e (the seven-contraction form of Sec. 3.1, Eq. (eval_pipeline), assembled per
+ * element), so the local apply of 128 cells is the product X[128, n^3] A_e^T.  It runs on the
+ * FP16 tensor cores (tcgen05) exactly: every value is cut into six balanced 8-bit integer
+ * digits relative to its cell's (data) or row's (table) largest exponent, the 21 digit
+ * products up to significance level 5 accumulate as exact integers in FP32, and the levels
+ * are combined in 64-bit integers and rounded once to double (error-free splitting of
+ * Ozaki et al., Numer. Algorithms 59, 2012).  Accuracy: a few 2^-48 relative to |A_e| |x|
+ * per value.  A non-finite input value makes its cell's outputs NaN.  Needs
+ * mf_operator_setup (the digit table lives in the operator workspace, at most 48 KB). */
+#define MF_VARIANT_TENSOR 3
+/* Forces a launch variant (0, 1 or 2) for every precision view, or MF_VARIANT_TENSOR for
+ * the FP64 view (MF_ERR_UNSUPPORTED for an operator it does not cover); MF_ERR_ARG for any
+ * other value. */
 mf_status mf_operator_set_variant(mf_operator* op, int variant);
 /* Variant in use for the operator's main precision view (-1 for a NULL operator). */
 int mf_operator_get_variant(const mf_operator* op);
+
+/* The library's device error word: nonzero when a bounded wait inside one of its kernels
+ * (an mbarrier wait of the tensor-core apply) gave up; that kernel then left its outputs
+ * incomplete.  Synchronous (reads device memory); reset != 0 clears the word. */
+int mf_device_error(int reset);
 
 /* ------------------------------------------------------------------ layout helpers */
 /* canonical cell-wise -> native and back (device pointers, operator element type). */

@@ -23,6 +23,7 @@ MF_FP64, MF_FP32, MF_MIXED, MF_FP64_DFMA = 0, 1, 2, 3
 MF_BC_NONE, MF_BC_DIRICHLET0 = 0, 1
 MF_CG_DEFAULT, MF_CG_SPLIT_DUAL, MF_CG_ASSEMBLED, MF_CG_SPLIT_DUAL_FUSED = 0, 1, 2, 3
 MF_PRECOND_NONE, MF_PRECOND_JACOBI = 0, 1
+MF_VARIANT_TENSOR = 3
 
 _STATUS = {0: "MF_OK", -1: "MF_ERR_ARG", -2: "MF_ERR_OOM", -3: "MF_ERR_CUDA", -4: "MF_ERR_NOT_CONVERGED",
            -5: "MF_ERR_BREAKDOWN", -6: "MF_ERR_TIMEOUT", -7: "MF_ERR_BUSY", -8: "MF_ERR_UNSUPPORTED",
@@ -115,6 +116,8 @@ def lib() -> C.CDLL:
     L.mf_operator_set_variant.argtypes = [vp, i32]
     L.mf_operator_get_variant.argtypes = [vp]
     L.mf_operator_get_variant.restype = i32
+    L.mf_device_error.argtypes = [i32]
+    L.mf_device_error.restype = i32
     L.mf_manufactured_workspace_bytes.argtypes = [vp]
     L.mf_manufactured_workspace_bytes.restype = sz
     L.mf_rhs_manufactured.argtypes = [vp, d, vp, vp, sz, vp]
@@ -198,6 +201,11 @@ def mf_operator_autotune(op, x_ptr: int, y_ptr: int, reps: int = 3, stream: int 
 
 def mf_operator_set_variant(op, variant: int) -> None:
     _check(lib().mf_operator_set_variant(op, variant))
+
+
+def mf_device_error(reset: bool = True) -> int:
+    """The library's device error word (nonzero: a bounded wait in a kernel gave up)."""
+    return int(lib().mf_device_error(1 if reset else 0))
 
 
 def mf_operator_get_variant(op) -> int:

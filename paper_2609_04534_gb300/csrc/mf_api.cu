@@ -196,6 +196,8 @@ mf_status mf_operator_create(const mf_mesh* mesh, int degree, int kind, double m
     const size_t tab = sizeof(float) * 2 * (size_t)(g.nx + g.ny + g.nz) * op->n;
     op->v32.geom_bytes = (precision == MF_FP64 || precision == MF_FP64_DFMA) ? 0 : tab;
   }
+  // the FP64 view of a Cartesian operator of degree 1..3 applies on the tensor cores
+  if (tc_eligible(op)) op->variant[VK_DD] = MF_VARIANT_TENSOR;
   *out = op;
   return MF_OK;
 }
@@ -214,7 +216,7 @@ mf_status mf_operator_info(const mf_operator* op, mf_info* info) {
   info->elem_bytes = (op->precision == MF_FP32) ? 4 : 8;
   info->path = op->path;
   info->geom_bytes = op->v64.geom_bytes + op->v32.geom_bytes;
-  info->workspace_bytes = align256(op->v64.geom_bytes) + align256(op->v32.geom_bytes) + 256;
+  info->workspace_bytes = align256(op->v64.geom_bytes) + align256(op->v32.geom_bytes) + align256(tc_table_bytes(op)) + 256;
   const double e = info->elem_bytes;
   double per_dof = 2.0 * e;
   if (op->path == PATH_CURVED && op->precision != MF_FP32) per_dof += geom_comps(op) * e; // FP32: no stream
@@ -236,6 +238,12 @@ mf_status mf_operator_setup(mf_operator* op, void* workspace_dev, size_t bytes, 
   op->v32.geom = nullptr;
   if (op->v64.geom_bytes) { op->v64.geom = w; w += align256(op->v64.geom_bytes); }
   if (op->v32.geom_bytes) { op->v32.geom = w; w += align256(op->v32.geom_bytes); }
+  op->tc_table = nullptr;
+  if (tc_table_bytes(op)) {
+    mf_status st = tc_setup(op, w, s);
+    if (st) return st;
+    w += align256(tc_table_bytes(op));
+  }
   op->workspace = workspace_dev;
   op->workspace_bytes = bytes;
   if (op->path == PATH_CURVED) {
@@ -380,7 +388,8 @@ mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, 
   if ((st = cuda_check(cudaEventCreate(&e1), "event"))) { cudaEventDestroy(e0); return st; }
   float best = 1e30f;
   int best_v = 0;
-  for (int v = 0; v < 3 && st == MF_OK; ++v) {
+  const int nvar = (vk == VK_DD && tc_eligible(op)) ? 4 : 3; // variant 3: the tensor-core apply
+  for (int v = 0; v < nvar && st == MF_OK; ++v) {
     op->variant[vk] = v;
     st = launch_apply_split(op, vk, x_dev, y_dev, s); // warm-up
     if (st) break;
@@ -403,10 +412,19 @@ mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, 
 }
 
 mf_status mf_operator_set_variant(mf_operator* op, int variant) {
-  if (!op || variant < 0 || variant > 2) return set_error(MF_ERR_ARG, "mf_operator_set_variant: bad argument");
+  if (!op || variant < 0 || variant > MF_VARIANT_TENSOR) return set_error(MF_ERR_ARG, "mf_operator_set_variant: bad argument");
+  if (variant == MF_VARIANT_TENSOR) {
+    if (!tc_eligible(op))
+      return set_error(MF_ERR_UNSUPPORTED, "mf_operator_set_variant: the tensor-core apply covers FP64 Cartesian "
+                                           "operators of degree 1..3");
+    op->variant[VK_DD] = MF_VARIANT_TENSOR;
+    return MF_OK;
+  }
   op->variant[VK_F64] = op->variant[VK_DD] = op->variant[VK_F32] = variant;
   return MF_OK;
 }
+
+int mf_device_error(int reset) { return tc_read_error(reset); }
 
 int mf_operator_get_variant(const mf_operator* op) {
   return op ? op->variant[view_of_elem(op, elem_of(op))] : -1;

@@ -8,6 +8,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/mf.h"
@@ -176,7 +177,12 @@ struct mf_operator {
   void* workspace = nullptr;
   size_t workspace_bytes = 0;
   bool ready = false;
-  int variant[3] = {0, 0, 0}; // apply launch variant per ViewKind (autotuned)
+  // apply launch variant per ViewKind (autotuned); MF_VARIANT_TENSOR for the FP64 view of an
+  // eligible Cartesian operator selects the tensor-core apply (mf_tc.cu)
+  int variant[3] = {0, 0, 0};
+  void* tc_table = nullptr;             // device: digit slices of the element matrix (workspace)
+  int tc_fexp[64] = {0};                // per output row: biased exponent bound of its entries
+  std::vector<unsigned short> tc_host;  // host copy of the digit slices (upload source)
 };
 
 namespace mf {
@@ -234,6 +240,14 @@ template <int N>
 mf_status geometry_n(const mf_operator* op, int vk, void* geom, cudaStream_t s);
 template <int N>
 mf_status layout_n(const mf_operator* op, int elem, int mode, const void* in, void* out, cudaStream_t s);
+
+// Tensor-core apply of the FP64 Cartesian operator (mf_tc.cu), degrees 1..3: launch variant
+// MF_VARIANT_TENSOR (include/mf.h).
+bool tc_eligible(const mf_operator* op);
+size_t tc_table_bytes(const mf_operator* op);              // device bytes of its digit table
+mf_status tc_setup(mf_operator* op, void* table_dev, cudaStream_t s); // builds and uploads it
+mf_status tc_apply(const mf_operator* op, const void* x, void* y, cudaStream_t s);
+int tc_read_error(int reset);                              // device error word (synchronous)
 
 // layout modes
 enum { LAYOUT_TO_NATIVE = 0, LAYOUT_FROM_NATIVE = 1, LAYOUT_SCATTER_UNIQUE = 2, LAYOUT_GATHER_UNIQUE = 3 };

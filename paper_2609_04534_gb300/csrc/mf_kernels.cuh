@@ -837,7 +837,8 @@ static mf_status stream_twin_cc(const mf_operator* op, const void* x, void* y, c
 template <int N>
 mf_status stream_twin_n(const mf_operator* op, int vk, const void* x, void* y, const void* geom, int nc,
                         cudaStream_t s) {
-  const bool half = op->variant[vk == VK_DDS ? VK_DD : vk] != 0;
+  const int var = op->variant[vk == VK_DDS ? VK_DD : vk];
+  const bool half = var == 1 || var == 2;
   if (vk == VK_F32) {
     using C0 = Cfg<FP32C, N, 0>;
     using CH = Cfg<FP32C, N, 1>;
@@ -1212,6 +1213,9 @@ static mf_status apply_split_t(const mf_operator* op, int variant, const void* x
 template <int N>
 mf_status apply_split_n(const mf_operator* op, int vk, const void* x, void* y, cudaStream_t s) {
   const int v = op->variant[vk == VK_DDS ? VK_DD : vk];
+  // the tensor-core apply stages x with 16-byte bulk copies; other x take the variant-0 kernel
+  if (vk == VK_DD && v == MF_VARIANT_TENSOR && (reinterpret_cast<uintptr_t>(x) & 15) == 0)
+    return tc_apply(op, x, y, s);
   if (vk == VK_F64) return apply_split_t<double, double, N>(op, v, x, y, op->v64.geom, CgFuse<double>{}, nullptr, s);
   if (vk == VK_DD) return apply_split_t<double, dd, N>(op, v, x, y, op->v64.geom, CgFuse<double>{}, nullptr, s);
   if (vk == VK_DDS) return apply_split_t<dd, dd, N>(op, v, x, y, op->v64.geom, CgFuse<dd>{}, nullptr, s);

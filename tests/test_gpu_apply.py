@@ -289,8 +289,14 @@ def test_launch_variants_agree_bitwise_and_autotune(k, geom, prec):
         assert torch.equal(y0, y1), v
     scratch = torch.empty_like(xn)
     v = mf.mf_operator_autotune(d.op, xn.data_ptr(), scratch.data_ptr(), 2)
-    assert v in (0, 1, 2)
-    assert torch.equal(d.apply(xn), y0)
+    if v == mf.MF_VARIANT_TENSOR:  # the tensor-core apply rounds differently (same accuracy)
+        assert geom == "cart" and prec == mf.MF_FP64 and k <= 3
+        y3 = d.apply(xn)
+        torch.cuda.synchronize()
+        assert float((y3 - y0).abs().max() / y0.abs().max()) <= 1e-12
+    else:
+        assert v in (0, 1, 2)
+        assert torch.equal(d.apply(xn), y0)
     d.close()
 
 

@@ -128,6 +128,12 @@ def test_split_dual_matches_assembled_iteration(oracle, dims, k, geom, kind, pre
     bitwise, and the split-dual solution satisfies the oracle's equations."""
     nx, ny, nz = dims
     d = DevOp(nx, ny, nz, k, geom, kind, 1.0, prec, bc)
+    # both forms on the same apply arithmetic (the assembled form would otherwise take the
+    # tensor-core apply of a Cartesian FP64 operator, which rounds differently; CG amplifies
+    # such 2^-48 differences to ~1e-8 after 25 iterations): this compares the iterations
+    tensor = mf.mf_operator_get_variant(d.op) == mf.MF_VARIANT_TENSOR
+    if tensor:
+        mf.mf_operator_set_variant(d.op, 0)
     bu = inputs.random_unique(nx, ny, nz, k, 11)
     b = d.native_from_unique(bu)
     its = 25
@@ -142,11 +148,16 @@ def test_split_dual_matches_assembled_iteration(oracle, dims, k, geom, kind, pre
         assert rel_max(d.unique_from_native(xs), d.unique_from_native(xa)) <= tol
     if prec != mf.MF_FP32:
         o = oracle_op(oracle, nx, ny, nz, k, geom, 1.0 if kind == mf.MF_HELMHOLTZ else 0.0, bc)
-        x1, st1, _ = solve(d, b, 1e-11, 20000, 0)
-        assert st1["code"] == mf.MF_OK
         bm = np.where(o.boundary_mask(), 0.0, bu) if bc else bu
-        res = np.linalg.norm(bm - o.apply(d.unique_from_native(x1))) / np.linalg.norm(bm)
-        assert res <= 2e-11, res
+        forms = [mf.MF_CG_DEFAULT]
+        if tensor:  # the assembled iteration on the tensor-core apply solves the same equations
+            mf.mf_operator_set_variant(d.op, mf.MF_VARIANT_TENSOR)
+            forms.append(mf.MF_CG_ASSEMBLED)
+        for form in forms:
+            x1, st1, _ = solve(d, b, 1e-11, 20000, 0, cg_form=form)
+            assert st1["code"] == mf.MF_OK
+            res = np.linalg.norm(bm - o.apply(d.unique_from_native(x1))) / np.linalg.norm(bm)
+            assert res <= 2e-11, (form, res)
     d.close()
 
 
