@@ -119,7 +119,7 @@ mf_status mf_operator_setup(mf_operator* op, void* workspace_dev, size_t bytes, 
  * accuracy class), so its results agree with theirs within 1e-12 relative max-norm. */
 mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, int reps, void* stream);
 /* The tensor-core apply of the FP64 Cartesian operator (degree 1..3; the default launch
- * variant of such operators).  All cells of an axis-aligned uniform mesh share one element
+ * variant of such operators of degree 2 and 3).  All cells of an axis-aligned uniform mesh share one element
  * matrix A_e (the seven-contraction form of Sec. 3.1, Eq. (eval_pipeline), assembled per
  * element), so the local apply of 128 cells is the product X[128, n^3] A_e^T.  It runs on the
  * FP16 tensor cores (tcgen05) exactly: every value is cut into six balanced 8-bit integer

@@ -196,8 +196,9 @@ mf_status mf_operator_create(const mf_mesh* mesh, int degree, int kind, double m
     const size_t tab = sizeof(float) * 2 * (size_t)(g.nx + g.ny + g.nz) * op->n;
     op->v32.geom_bytes = (precision == MF_FP64 || precision == MF_FP64_DFMA) ? 0 : tab;
   }
-  // the FP64 view of a Cartesian operator of degree 1..3 applies on the tensor cores
-  if (tc_eligible(op)) op->variant[VK_DD] = MF_VARIANT_TENSOR;
+  // the FP64 view of a Cartesian operator of degree 2 or 3 applies on the tensor cores by
+  // default (at degree 1 the double-float kernel is faster; the autotuner can still pick it)
+  if (tc_eligible(op) && op->n >= 3) op->variant[VK_DD] = MF_VARIANT_TENSOR;
   *out = op;
   return MF_OK;
 }

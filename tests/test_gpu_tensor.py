@@ -19,7 +19,9 @@ DIMS = [(5, 6, 3), (9, 6, 5), (1, 1, 1), (4, 4, 2)]
 
 def tc_op(dims, k, kind, bc, mass=1.0):
     d = DevOp(*dims, k, "cart", kind, mass, mf.MF_FP64, bc)
-    assert mf.mf_operator_get_variant(d.op) == mf.MF_VARIANT_TENSOR
+    # the default from degree 2; selectable at degree 1
+    assert (mf.mf_operator_get_variant(d.op) == mf.MF_VARIANT_TENSOR) == (k >= 2)
+    mf.mf_operator_set_variant(d.op, mf.MF_VARIANT_TENSOR)
     return d
 
 
