@@ -4,11 +4,15 @@ Workload (N=1): Q4 Laplace on the curved 64^3 mesh of the unit cube (x + 0.1 sin
 sin(pi y) sin(pi z) on every coordinate, per-Gauss-point Jacobians), FP64, homogeneous
 Dirichlet.  A step is one CG iteration: q = P A P p (sum-factorised apply + deterministic
 duplicate summation + mask) and the fused CG vector updates with their dot products.
-value = cell-wise DoFs per step / step time.  Extra fields: the apply alone for Q3/Q4 in
-FP64 and FP32, the Helmholtz degree sweep at ~50M cell-wise DoFs, the end-to-end apply from
-host memory, and the CPU oracle baseline.
+value = cell-wise DoFs per step / step time; roofline = the CG apply's algorithmic bytes over
+its time against the measured HBM bandwidth; e2e = the same K iterations through the C-ABI
+host-buffer solve.  Extra fields: the applies of the curved 64^3 config (Q3/Q4, FP64 / FP64
+on the native FP64 pipe / FP32), the Helmholtz degree sweep at ~50M cell-wise DoFs with the
+per-degree HBM fractions, the 96^3 mixed-precision solve against plain FP64 CG, a burst of the
+serving stream, and the CPU oracle baseline.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-sweep] [--solve]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-sweep]
+                  [--no-solve] [--serve-burst NREQ] [--solve] [--serve NREQ --rate R]
 """
 from __future__ import annotations
 
@@ -38,19 +42,7 @@ def peaks():
         p = {"hbm_gbs": float(j["hbm_gbs"]), "source": "measured"}
     except Exception:
         pass
-    # FP64 FMA pipe of GB300: nominal 1.25 TFLOP/s dense at the 2070 MHz maximum clock,
-    # i.e. 2 FP64 FMA / clock / SM x 152 SMs x 2 FLOP.
-    p["fp64_tflops"] = 2 * 2 * 152 * 2.070e9 / 1e12
-    # FP32 FMA pipe: 128 lanes / SM
-    p["fp32_tflops"] = 128 * 2 * 152 * 2.070e9 / 1e12
     return p
-
-
-def flops_per_dof(path: int, n: int, helm: bool) -> float:
-    """Algorithmic FLOPs per cell-wise DoF of one apply (FMA = 2)."""
-    if path == 0:
-        return 14.0 * n
-    return 24.0 * n + 15.0 + (2.0 if helm else 0.0)
 
 
 class Clocks:
@@ -390,15 +382,16 @@ def dss_ablation(args):
         torch.cuda.empty_cache()
 
 
-def solve_run(args):
-    """Mixed-precision Poisson solve: Q4 on the curved N^3 mesh (default 96^3), manufactured
+def solve_compare(N=96, inner=(1e-3,), extra=True):
+    """Mixed-precision Poisson solve: Q4 on the curved N^3 mesh (96^3 is the config), manufactured
     u = sin(2 pi x) sin(2 pi y) sin(2 pi z), FP32 apply inside FP64 defect correction to
-    relative residual 1e-10, against plain FP64 CG (double-float apply) on the same problem."""
+    relative residual 1e-10, against plain FP64 CG (double-float apply) on the same problem.
+    extra adds the Jacobi-preconditioned runs."""
     import torch
 
     import paper_2609_04534_gb300 as mf
 
-    N, k = args.solve_n, 4
+    k = 4
     stream = torch.cuda.Stream()
     s = stream.cuda_stream
     out = {"metric": "solved DoF/s at relative residual 1e-10", "workload":
@@ -416,7 +409,9 @@ def solve_run(args):
     autotune(mf, torch, op, b, s)
     autotune(mf, torch, op64, b, s)
     l2 = torch.zeros(1, dtype=torch.float64, device="cuda")
-    runs = [(1, t, 0) for t in args.inner_rtol] + [(0, 0.0, 0), (1, args.inner_rtol[0], 1), (0, 0.0, 1)]
+    runs = [(1, t, 0) for t in inner] + [(0, 0.0, 0)]
+    if extra:
+        runs += [(1, inner[0], 1), (0, 0.0, 1)]
     for mixed, itol, pre in runs:
         sop = op if mixed else op64
         cws = torch.empty(mf.mf_cg_workspace_bytes(sop, mixed), dtype=torch.uint8, device="cuda")
@@ -441,36 +436,39 @@ def solve_run(args):
     best = min((v["seconds"], kk) for kk, v in out.items() if kk.startswith("mixed_inner") and "jacobi" not in kk)
     out["best_mixed"] = best[1]
     out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / best[0]
-    print(json.dumps(out), flush=True)
     mf.mf_operator_destroy(op)
     mf.mf_mesh_destroy(mesh)
     mf.mf_operator_destroy(op64)
     mf.mf_mesh_destroy(mesh64)
+    del ws, ws64, b, x, sc
+    torch.cuda.empty_cache()
+    return out
 
 
-def serve_run(args):
-    """Serving stream: NREQ Poisson CG solve requests, mesh N^3 with N log-uniform in [4, 64],
+def solve_run(args):
+    print(json.dumps(solve_compare(args.solve_n, tuple(args.inner_rtol), True)), flush=True)
+
+
+def serve_stream(n, rate=0.0, single=False, no_batching=False, arena_gb=120):
+    """Serving stream: n Poisson CG solve requests, mesh N^3 with N log-uniform in [4, 64],
     degree uniform in {2..6}, affine or curved 50/50, manufactured right-hand side, FP32 apply
     in FP64 refinement to 1e-10; seed 4.  Reports p50/p99 latency (submit -> result) and
-    solved DoF/s over the makespan."""
+    solved DoF/s over the makespan.  rate 0: all requests at t = 0 (a closed burst)."""
     import torch
 
     import paper_2609_04534_gb300 as mf
 
     rng = np.random.default_rng(4)
-    n = args.serve
     Ns = np.rint(np.exp(rng.uniform(np.log(4), np.log(64), n))).astype(int)
     ks = rng.integers(2, 7, n)
     geo = rng.integers(0, 2, n)
-    arena = torch.empty(int(120 * 2**30), dtype=torch.uint8, device="cuda")
-    # --fp64-single: the baseline of the same stream, the plain FP64 solver one request at a time
-    single = args.fp64_single
+    arena = torch.empty(int(arena_gb * 2**30), dtype=torch.uint8, device="cuda")
+    # single: the baseline of the same stream, the plain FP64 solver one request at a time
     sv = mf.mf_server_create(arena.data_ptr(), arena.numel(), max_slots=1 if single else 64, autotune=1,
-                             batching=-1 if (args.no_batching or single) else 0)
+                             batching=-1 if (no_batching or single) else 0)
     reqs = [mf.make_request(int(N), int(N), int(N), int(k), geometry=mf.MF_CURVED_SIN if g else mf.MF_AFFINE,
                             rhs=mf.MF_RHS_MANUFACTURED, rtol=1e-10, maxit=400000, mixed=0 if single else 1)
             for N, k, g in zip(Ns, ks, geo)]
-    rate = args.rate
     gaps = rng.exponential(1.0 / rate, n) if rate > 0 else np.zeros(n)
     t0 = time.perf_counter()
     tickets, results = [], {}
@@ -504,10 +502,16 @@ def serve_run(args):
            "failed": [dict(N=int(Ns[i]), k=int(ks[i]), curved=int(geo[i]), status=int(rs[i]["status"]),
                            iterations=int(rs[i]["iterations"]), outer=int(rs[i]["outer_iterations"]),
                            rel=float(rs[i]["rel_residual"])) for i in range(n) if rs[i]["status"] != 0][:10],
-           "batching": not (args.no_batching or single),
+           "batching": not (no_batching or single),
            "solver": "plain FP64 CG, one request at a time" if single else "mixed precision, 64 slots",
            "arena_peak_gb": st["arena_peak"] / 2**30, "slots": 1 if single else 64}
-    print(json.dumps(out), flush=True)
+    del arena
+    torch.cuda.empty_cache()
+    return out
+
+
+def serve_run(args):
+    print(json.dumps(serve_stream(args.serve, args.rate, args.fp64_single, args.no_batching)), flush=True)
 
 
 def main():
@@ -518,6 +522,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-solve", action="store_true", help="skip the 96^3 mixed vs FP64 solve of the default line")
+    ap.add_argument("--serve-burst", type=int, default=100,
+                    help="requests of the serving burst in the default line (0: skip)")
     ap.add_argument("--solve", action="store_true")
     ap.add_argument("--profile-apply", default=None, metavar="N,k,geom,prec,kind",
                     help="only run a few applies of one case (for ncu), e.g. 32,4,curved,fp64,laplace")
@@ -617,53 +624,55 @@ def main():
                      (mf.MF_CG_ASSEMBLED, "assembled")):
         prof[nm] = mf.mf_cg_profile(op, b.data_ptr(), x.data_ptr(), 20, form, cws.data_ptr(), cws.numel(), s)
     t_fused = prof["split_dual"]["apply_ms"] / 1e3
-    fpd = flops_per_dof(info["path"], info["n"], False)
-    flops = fpd * ncw
-    # The FP64 apply computes in double-float on the FP32 pipe: each algorithmic FP64 FMA
-    # costs 12 FP32 instructions (TwoProd 4 + TwoSum 6 + 2 adds), so the ALU roof of the
-    # emulated arithmetic is the FP32 issue rate / 12, in FP64-equivalent FLOP/s.
-    emu_peak = pk["fp32_tflops"] / 12.0
-    # DRAM bytes of this kernel (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
-    # capture of the same kernel on the curved Q4 48^3 case: 79.0 bytes per cell-wise DoF,
-    # scaled here to the bench's DoFs (traffic grows in proportion to the cells).
+    alg_bytes = info["algorithmic_bytes_per_apply"]
+    # Byte roofline of the step's dominant kernel, the CG apply (A_K p and <p, A_K p>): the
+    # algorithmic bytes of one apply (x 8 + y 8 + 6 metric words x 8 = 64 B per cell-wise DoF
+    # for the curved FP64 Laplace operator) over its CUDA-event time, against the measured HBM
+    # copy bandwidth.  traffic: DRAM bytes of this kernel from one ncu capture of the same kernel
+    # on the curved Q4 48^3 case, 79.0 B per cell-wise DoF, scaled to the bench's DoFs.
     traffic = 79.02 * ncw
-    roof = {"bound": "alu", "achieved": flops / t_fused / 1e12, "peak": emu_peak, "unit": "TFLOP/s",
-            "frac": flops / t_fused / 1e12 / emu_peak, "traffic": traffic,
+    roof = {"bound": "hbm", "achieved": alg_bytes / t_fused / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": alg_bytes / t_fused / 1e9 / pk["hbm_gbs"], "traffic": traffic,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy kernel), of measured" if pk["source"] == "measured"
+            else "fallback 6800 GB/s",
+            "algorithmic_bytes_per_dof": alg_bytes / ncw,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of apply_general<dd,dd,5,16,2,1,0> "
                               "on Q4 curved 48^3 (13.82 M DoFs): 1092.3 MB, scaled by DoFs",
-            "kernel": "apply_general<double,dd,5,curved,laplace> as the split-dual CG apply "
+            "kernel": "apply_general<dd,dd,5,curved,laplace> as the split-dual CG apply "
                       "(A_K p and <p, A_K p> at the quadrature points)",
             "kernel_ms": round(t_fused * 1e3, 4),
-            "peak_source": "derived: FP32 pipe 128 lanes/SM x 152 SMs x 2070 MHz x 2 FLOP, / 12 FP32 "
-                           "instructions per emulated FP64 FMA (FP64-equivalent FLOP/s)",
-            "hbm_frac_of_measured": None}
-    alg_bytes = info["algorithmic_bytes_per_apply"]
+            "dram_gbs_from_traffic": traffic / t_fused / 1e9,
+            # the same accesses without the arithmetic (mf_apply_stream_twin): the layout's ceiling
+            "twin_frac": alg_bytes / t_twin / 1e9 / pk["hbm_gbs"]}
     hbm_frac_apply = alg_bytes / t_apply / 1e9 / pk["hbm_gbs"]
-    roof["hbm_frac_of_measured"] = alg_bytes / t_fused / 1e9 / pk["hbm_gbs"]
-    # achieved bandwidth both ways: algorithmic bytes / time (above) and ncu DRAM bytes / time
-    roof["dram_gbs_from_traffic"] = traffic / t_fused / 1e9
 
-    # e2e through the public API from host memory: pinned b in, x out, K CG iterations
+    # e2e through the C ABI from host buffers: mf_cg_solve_host copies the canonical b from
+    # pinned host memory, runs the same K iterations and copies the canonical x back, all
+    # inside the timed call
     e2e = None
     try:
-        hb = torch.empty(info["n_native"], dtype=torch.float64, pin_memory=True)
-        hb.copy_(b.cpu())
-        hx = torch.empty_like(hb).pin_memory()
-        db = torch.empty_like(b)
+        ncan = info["n_cellwise"]
+        can = torch.empty(ncan, dtype=torch.float64, device="cuda")
+        mf.mf_from_native(op, b.data_ptr(), can.data_ptr(), s)
+        hb = torch.empty(ncan, dtype=torch.float64, pin_memory=True)
+        hb.copy_(can.cpu())
+        hx = torch.empty(ncan, dtype=torch.float64, pin_memory=True)
+        hws = torch.empty(mf.mf_cg_solve_host_workspace_bytes(op, 0), dtype=torch.uint8, device="cuda")
+        del can
+        mf.mf_cg_solve_host(op, hb.data_ptr(), hx.data_ptr(), 0.0, args.warmup, 0, hws.data_ptr(), hws.numel(), s,
+                            allow_not_converged=True)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with torch.cuda.stream(stream):
-            db.copy_(hb, non_blocking=True)
-        st2 = mf.mf_cg_solve(op, db.data_ptr(), x.data_ptr(), 0.0, args.steps, 0, cws.data_ptr(), cws.numel(), s,
-                             allow_not_converged=True)
-        with torch.cuda.stream(stream):
-            hx.copy_(x, non_blocking=True)
-        stream.synchronize()
+        st2 = mf.mf_cg_solve_host(op, hb.data_ptr(), hx.data_ptr(), 0.0, args.steps, 0, hws.data_ptr(), hws.numel(),
+                                  s, allow_not_converged=True)
         te = time.perf_counter() - t0
+        its2 = max(st2["iterations"], 1)
         e2e = {"value": world * ncw * st2["iterations"] / te / 1e9, "unit": "GDoF/s",
-               "h2d_bytes_per_step": info["n_native"] * 8 / max(st2["iterations"], 1),
-               "d2h_bytes_per_step": info["n_native"] * 8 / max(st2["iterations"], 1),
-               "note": "mf_cg_solve of K iterations from pinned host b to host x; copies amortised per step"}
+               "h2d_bytes_per_step": ncan * 8 / its2, "d2h_bytes_per_step": ncan * 8 / its2,
+               "note": "one mf_cg_solve_host call (C ABI, pinned host buffers in canonical layout): H2D of b, "
+                       "layout conversion, K CG iterations, conversion back, D2H of x, synchronise; copies "
+                       "amortised per step"}
+        del hws, hb, hx
     except Exception as exc:  # keep the line even if pinned memory is unavailable
         e2e = {"value": None, "unit": "GDoF/s", "error": str(exc)[:200]}
     del cws
@@ -696,7 +705,10 @@ def main():
             torch.cuda.empty_cache()
 
     # ------------------------------------------------------------ degree sweep (Helmholtz, ~50M)
+    # mf_apply (local apply + duplicate summation) per degree with the autotuned launch variant
+    # (variant 3: the tensor-core apply of degrees 1..3), against 16 B per cell-wise DoF
     sweep = {}
+    frac_deg, kfrac_deg = {}, {}
     if not args.no_sweep:
         for kk, NN in SWEEP_N.items():
             ent = {"N": NN}
@@ -705,17 +717,48 @@ def main():
                 with torch.cuda.stream(stream):
                     xx = random_native(mf, torch, op, info, NN, kk, 2, torch.float64, s)
                     yy = torch.empty_like(xx)
-                autotune(mf, torch, op, xx, s)
+                v = autotune(mf, torch, op, xx, s)
                 t = time_apply(mf, torch, op, xx, yy, stream, 10, 3)
+                ta, td = time_kernels(mf, torch, op, xx, yy, stream, 5)
                 gd = info["n_cellwise"] / t / 1e9
+                ab = info["algorithmic_bytes_per_apply"]
                 ent["n_cellwise"] = info["n_cellwise"]
-                ent[nm] = {"gdofs": round(gd, 3),
-                           "hbm_frac": round(info["algorithmic_bytes_per_apply"] / t / 1e9 / pk["hbm_gbs"], 4)}
+                ent[nm] = {"gdofs": round(gd, 3), "hbm_frac": round(ab / t / 1e9 / pk["hbm_gbs"], 4),
+                           "apply_kernel_ms": round(ta * 1e3, 4), "dss_kernel_ms": round(td * 1e3, 4),
+                           "apply_kernel_hbm_frac": round(ab / ta / 1e9 / pk["hbm_gbs"], 4), "variant": v}
+                if nm == "fp64":
+                    frac_deg[f"k{kk}"] = ent[nm]["hbm_frac"]
+                    kfrac_deg[f"k{kk}"] = ent[nm]["apply_kernel_hbm_frac"]
                 mf.mf_operator_destroy(op)
                 mf.mf_mesh_destroy(mesh)
                 del ws, xx, yy
                 torch.cuda.empty_cache()
             sweep[f"k{kk}"] = ent
+
+    # ------------------------------------------------------------ the metric's second half
+    # config 4: the mixed-precision solve against plain FP64 CG, to 1e-10 (each with its clocks)
+    solve = None
+    if rank == 0 and not args.no_solve:
+        try:
+            with Clocks(local) as sclk:
+                sclk.mark_start()
+                solve = solve_compare(args.solve_n, (1e-3,), False)
+                sclk.mark_end()
+            solve["clocks"] = sclk.summary()
+        except Exception as exc:
+            solve = {"error": str(exc)[:200]}
+    # config 5 (shortened): a burst of requests of the serving stream through the batched
+    # mixed-precision server
+    serve = None
+    if rank == 0 and args.serve_burst > 0:
+        try:
+            with Clocks(local) as vclk:
+                vclk.mark_start()
+                serve = serve_stream(args.serve_burst, 0.0, False, False, arena_gb=60)
+                vclk.mark_end()
+            serve["clocks"] = vclk.summary()
+        except Exception as exc:
+            serve = {"error": str(exc)[:200]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -728,18 +771,24 @@ def main():
         line = {
             "metric": METRIC, "value": round(value, 4), "unit": "GDoF/s", "n_gpus": world, "steps": its,
             "warmup": args.warmup, "ms_per_step": round(t_it * 1e3, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 (double-float arithmetic on the FP32 pipe, ~2^-48; config-3 degrees 2-3: exact "
+                     "integer digits on the FP16 tensor cores)",
+            "data": "synthetic",
             "config": workload_config(ncw, world),
+            "roofline": roof,
+            "apply_hbm_frac_per_degree": frac_deg,
+            "apply_kernel_hbm_frac_per_degree": kfrac_deg,
             "apply_only": {"gdofs": round(ncw / t_apply / 1e9, 4), "hbm_frac_of_measured": round(hbm_frac_apply, 4),
                            "apply_kernel_ms": round(t_split * 1e3, 4), "dss_kernel_ms": round(t_dss * 1e3, 4),
-                           # the same accesses without arithmetic (mf_apply_stream_twin)
                            "twin_kernel_ms": round(t_twin * 1e3, 4),
                            "twin_hbm_frac_of_measured": round(alg_bytes / t_twin / 1e9 / pk["hbm_gbs"], 4)},
             "cg_iteration_kernels_ms": {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in prof.items()},
-            "roofline": roof,
             "apply_variant": variant,
             "applies_64cubed_curved": applies,
             "helmholtz_sweep_50M": sweep,
+            "solve_96cubed": solve,
+            "serve_burst": serve,
             "cpu_baseline": cpu,
             "e2e": e2e,
             # mask, max|b|, zero x, scale b, copy p, <r,r>, state; then 4 kernels per iteration

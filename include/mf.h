@@ -269,6 +269,17 @@ typedef struct {
 size_t mf_cg_workspace_bytes(const mf_operator* op, int mixed);
 mf_status mf_cg_solve(const mf_operator* op, const void* b_dev, void* x_dev, double rtol, int maxit, int mixed,
                       mf_solve_stats* stats, void* workspace_dev, size_t bytes, void* stream);
+/* End to end from host memory: copies the canonical cell-wise right-hand side b_host
+ * (n_cellwise elements of the operator's element type, consistent) to the device, converts
+ * it to the native layout, runs mf_cg_solve from x = 0, and copies the canonical solution
+ * to x_host; synchronises `stream` before it returns.  Host buffers are the caller's (pinned
+ * memory makes the copies asynchronous DMA; pageable memory works, more slowly).  Device
+ * workspace: mf_cg_solve_host_workspace_bytes(op, mixed) bytes, 256-byte aligned.  Returns
+ * what mf_cg_solve returns (x_host is written for MF_ERR_NOT_CONVERGED and MF_ERR_BREAKDOWN
+ * too), or MF_ERR_ARG / MF_ERR_OOM / MF_ERR_CUDA. */
+size_t mf_cg_solve_host_workspace_bytes(const mf_operator* op, int mixed);
+mf_status mf_cg_solve_host(const mf_operator* op, const void* b_host, void* x_host, double rtol, int maxit, int mixed,
+                           mf_solve_stats* stats, void* workspace_dev, size_t bytes, void* stream);
 /* mf_cg_solve with options (0 fields keep the defaults): inner_rtol of the FP32 CG in
  * defect correction (default 1e-3), CG iterations per graph launch (default 20), cap on
  * defect-correction steps (default 60), and the form of the CG iteration:

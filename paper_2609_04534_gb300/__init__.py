@@ -128,6 +128,9 @@ def lib() -> C.CDLL:
     L.mf_cg_record_history.argtypes = [vp, i32]
     L.mf_cg_solve_ex.argtypes = [vp, vp, vp, d, i32, i32, C.POINTER(mf_solve_options), C.POINTER(mf_solve_stats),
                                  vp, sz, vp]
+    L.mf_cg_solve_host_workspace_bytes.argtypes = [vp, i32]
+    L.mf_cg_solve_host_workspace_bytes.restype = sz
+    L.mf_cg_solve_host.argtypes = [vp, vp, vp, d, i32, i32, C.POINTER(mf_solve_stats), vp, sz, vp]
     L.mf_diagonal_workspace_bytes.argtypes = [vp]
     L.mf_diagonal_workspace_bytes.restype = sz
     L.mf_diagonal.argtypes = [vp, vp, vp, sz, vp]
@@ -297,6 +300,23 @@ def mf_cg_solve(op, b_ptr: int, x_ptr: int, rtol: float, maxit: int, mixed: int,
     opts = mf_solve_options(inner_rtol, chunk_iterations, max_outer, cg_form, precond)
     code = lib().mf_cg_solve_ex(op, b_ptr, x_ptr, rtol, maxit, mixed, C.byref(opts), C.byref(st), workspace_ptr,
                                 nbytes, stream or None)
+    if not (code == MF_OK or (allow_not_converged and code == MF_ERR_NOT_CONVERGED)):
+        _check(code)
+    out = {f: getattr(st, f) for f, _ in mf_solve_stats._fields_}
+    out["code"] = code
+    return out
+
+
+def mf_cg_solve_host_workspace_bytes(op, mixed: int = 0) -> int:
+    return int(lib().mf_cg_solve_host_workspace_bytes(op, mixed))
+
+
+def mf_cg_solve_host(op, b_host_ptr: int, x_host_ptr: int, rtol: float, maxit: int, mixed: int, workspace_ptr: int,
+                     nbytes: int, stream: int = 0, allow_not_converged: bool = False) -> dict:
+    """CG from host memory: canonical b in, canonical x out (see include/mf.h)."""
+    st = mf_solve_stats()
+    code = lib().mf_cg_solve_host(op, b_host_ptr, x_host_ptr, rtol, maxit, mixed, C.byref(st), workspace_ptr, nbytes,
+                                  stream or None)
     if not (code == MF_OK or (allow_not_converged and code == MF_ERR_NOT_CONVERGED)):
         _check(code)
     out = {f: getattr(st, f) for f, _ in mf_solve_stats._fields_}

@@ -1124,6 +1124,43 @@ mf_status mf_cg_solve(const mf_operator* op, const void* b_dev, void* x_dev, dou
   return mf_cg_solve_ex(op, b_dev, x_dev, rtol, maxit, mixed, nullptr, stats, workspace_dev, bytes, stream);
 }
 
+static size_t host_align(size_t b) { return (b + 255) & ~size_t(255); }
+
+size_t mf_cg_solve_host_workspace_bytes(const mf_operator* op, int mixed) {
+  if (!op) return 0;
+  const size_t e = op->precision == MF_FP32 ? 4 : 8;
+  return host_align(mf_cg_workspace_bytes(op, mixed)) + 2 * host_align((size_t)op->n_native * e) +
+         host_align((size_t)op->n_cellwise * e);
+}
+
+mf_status mf_cg_solve_host(const mf_operator* op, const void* b_host, void* x_host, double rtol, int maxit, int mixed,
+                           mf_solve_stats* stats, void* workspace_dev, size_t bytes, void* stream) {
+  if (!op || !b_host || !x_host) return set_error(MF_ERR_ARG, "mf_cg_solve_host: NULL argument");
+  if (!op->ready) return set_error(MF_ERR_ARG, "mf_cg_solve_host: operator not set up");
+  const size_t need = mf_cg_solve_host_workspace_bytes(op, mixed);
+  if (!workspace_dev || bytes < need) return set_error(MF_ERR_OOM, "mf_cg_solve_host: workspace %zu < %zu", bytes, need);
+  if (reinterpret_cast<uintptr_t>(workspace_dev) & 255)
+    return set_error(MF_ERR_ARG, "mf_cg_solve_host: workspace alignment");
+  const size_t e = op->precision == MF_FP32 ? 4 : 8;
+  const size_t cgb = host_align(mf_cg_workspace_bytes(op, mixed)), nb = host_align((size_t)op->n_native * e);
+  char* w = static_cast<char*>(workspace_dev);
+  void* bn = w + cgb;
+  void* xn = w + cgb + nb;
+  void* can = w + cgb + 2 * nb;
+  const size_t cbytes = (size_t)op->n_cellwise * e;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  mf_status st = cuda_check(cudaMemcpyAsync(can, b_host, cbytes, cudaMemcpyHostToDevice, s), "mf_cg_solve_host H2D");
+  if (st) return st;
+  if ((st = mf_to_native(op, can, bn, stream))) return st;
+  const mf_status solve = mf_cg_solve_ex(op, bn, xn, rtol, maxit, mixed, nullptr, stats, w, cgb, stream);
+  if (solve != MF_OK && solve != MF_ERR_NOT_CONVERGED && solve != MF_ERR_BREAKDOWN) return solve;
+  if ((st = mf_from_native(op, xn, can, stream))) return st;
+  if ((st = cuda_check(cudaMemcpyAsync(x_host, can, cbytes, cudaMemcpyDeviceToHost, s), "mf_cg_solve_host D2H")))
+    return st;
+  if ((st = cuda_check(cudaStreamSynchronize(s), "mf_cg_solve_host sync"))) return st;
+  return solve;
+}
+
 mf_status mf_cg_solve_ex(const mf_operator* op, const void* b_dev, void* x_dev, double rtol, int maxit, int mixed,
                          const mf_solve_options* opts, mf_solve_stats* stats, void* workspace_dev, size_t bytes,
                          void* stream) {

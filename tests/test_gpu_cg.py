@@ -232,3 +232,23 @@ def test_jacobi_pcg_converges_with_fewer_iterations(oracle, geom, k, prec, mixed
     assert res <= 2e-10, res
     assert rel_max(xg, d.unique_from_native(x0)) <= 1e-7
     d.close()
+
+
+@pytest.mark.parametrize("geom,k,prec", [("curved", 4, mf.MF_FP64), ("cart", 3, mf.MF_FP64), ("curved", 2, mf.MF_FP32)])
+def test_cg_solve_host_matches_device_solve(geom, k, prec):
+    """mf_cg_solve_host (canonical host b in, canonical host x out) runs the same solve as
+    mf_cg_solve on native device vectors: bitwise equal solution and statistics."""
+    dims = (5, 6, 3)
+    d = DevOp(*dims, k, geom, mf.MF_LAPLACE, 1.0, prec, 1)
+    bu = inputs.random_unique(*dims, k, 17)
+    b = d.native_from_unique(bu)
+    x, st, _ = solve(d, b, 1e-9, 2000, 0)
+    xc = d.canonical_from_native(x)
+    bh = torch.empty(d.n_cw, dtype=d.dtype, pin_memory=True)
+    bh.copy_(torch.as_tensor(d.canonical_from_native(b), dtype=d.dtype))
+    xh = torch.full((d.n_cw,), float("nan"), dtype=d.dtype).pin_memory()
+    ws = torch.empty(mf.mf_cg_solve_host_workspace_bytes(d.op, 0), dtype=torch.uint8, device="cuda")
+    sth = mf.mf_cg_solve_host(d.op, bh.data_ptr(), xh.data_ptr(), 1e-9, 2000, 0, ws.data_ptr(), ws.numel())
+    assert sth["iterations"] == st["iterations"] and sth["rel_residual"] == st["rel_residual"]
+    assert np.array_equal(xh.double().numpy(), xc)
+    d.close()

@@ -130,6 +130,20 @@ def test_noalloc_dot_rejects_on_the_host(L):
     mf.mf_mesh_destroy(mesh)
 
 
+def test_cg_solve_host_argument_validation(L):
+    mesh = mf.mf_mesh_create(4, 4, 4)
+    op = mf.mf_operator_create(mesh, 2)
+    with pytest.raises(mf.MfError) as e:
+        mf.mf_cg_solve_host(op, 16, 32, 1e-8, 10, 0, 256, 1 << 20)
+    assert e.value.code == mf.MF_ERR_ARG and "not set up" in str(e.value)
+    with pytest.raises(mf.MfError) as e:
+        mf.mf_cg_solve_host(None, 16, 32, 1e-8, 10, 0, 256, 1 << 20)
+    assert e.value.code == mf.MF_ERR_ARG
+    assert mf.mf_cg_solve_host_workspace_bytes(op, 0) > mf.mf_cg_workspace_bytes(op, 0)
+    mf.mf_operator_destroy(op)
+    mf.mf_mesh_destroy(mesh)
+
+
 def test_make_consistent_argument_validation(L):
     with pytest.raises(mf.MfError) as e:
         mf.mf_make_consistent(None, 16)
