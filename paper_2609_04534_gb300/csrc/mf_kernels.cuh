@@ -721,6 +721,66 @@ __global__ void dss_kernel(T* __restrict__ y, GridInfo g, int avg) {
       for (int xx = 0; xx < mx; ++xx) y[addr[xx + 2 * (yy + 2 * zz)]] = s;
 }
 
+// The same duplicate summation with the global nodes of (J, L) rows per block and the cells
+// fastest across threads: thread (i, cx) takes node I = cx k + i (for i = 0 the extra column
+// cx = nx takes the row's last node I = nx k), so for one i consecutive threads read
+// consecutive lanes of a tile (whole 32-byte sectors); J and L come from the grid and a
+// block loops over DSS_ROWS_Y-strided rows (no division per thread, few blocks).  Same sums
+// in the same canonical order as dss_kernel, so bitwise equal.
+constexpr int DSS_ROW_THREADS = 128, DSS_ROWS_Y = 32;
+template <typename T, int N>
+__global__ void __launch_bounds__(DSS_ROW_THREADS) dss_row_kernel(T* __restrict__ y, GridInfo g, int avg, int cxb) {
+  constexpr int K = N - 1, N2 = N * N, N3 = N2 * N;
+  const int i = blockIdx.x / cxb;                                       // local x index
+  const int cxs = (blockIdx.x - i * cxb) * DSS_ROW_THREADS + threadIdx.x; // cell column
+  if (cxs > g.nx || (i > 0 && cxs == g.nx)) return;
+  const int NYn = g.ny * K + 1, NZn = g.nz * K + 1;
+  int cx[2], ix[2];
+  int mx;
+  if (cxs == g.nx) { mx = 1; cx[0] = g.nx - 1; ix[0] = K; }            // I = nx k, the last node
+  else if (i == 0 && cxs > 0) { mx = 2; cx[0] = cxs - 1; ix[0] = K; cx[1] = cxs; ix[1] = 0; }
+  else { mx = 1; cx[0] = cxs; ix[0] = i; }
+  const bool bx = (i == 0 && cxs == 0) || cxs == g.nx; // on the x = 0 or x = 1 face
+  for (int L = blockIdx.z; L < NZn; L += gridDim.z) {
+    int cz[2], iz[2];
+    const int mz = copies_1d(L, g.nz, K, cz, iz);
+    for (int J = blockIdx.y; J < NYn; J += gridDim.y) {
+      int cy[2], iy[2];
+      const int my = copies_1d(J, g.ny, K, cy, iy);
+      const bool bnd = !avg && g.bc && (bx || J == 0 || J == NYn - 1 || L == 0 || L == NZn - 1);
+      if (mx * my * mz == 1 && !bnd) continue;
+      long long addr[8];
+      T sz[2];
+#pragma unroll
+      for (int zz = 0; zz < 2; ++zz) {
+        if (zz >= mz) break;
+        T sy[2];
+#pragma unroll
+        for (int yy = 0; yy < 2; ++yy) {
+          if (yy >= my) break;
+          T sx = T(0);
+#pragma unroll
+          for (int xx = 0; xx < 2; ++xx) {
+            if (xx >= mx) break;
+            const long long ad = native_index(g, N3, cx[xx], cy[yy], cz[zz], ix[xx] + N * iy[yy] + N2 * iz[zz]);
+            addr[xx + 2 * (yy + 2 * zz)] = ad;
+            const T v = y[ad];
+            sx = (xx == 0) ? v : sx + v;
+          }
+          sy[yy] = sx;
+        }
+        sz[zz] = (my == 2) ? sy[0] + sy[1] : sy[0];
+      }
+      T s = (mz == 2) ? sz[0] + sz[1] : sz[0];
+      if (avg) s = s * (T(1) / T(mx * my * mz));
+      if (bnd) s = T(0);
+      for (int zz = 0; zz < mz; ++zz)
+        for (int yy = 0; yy < my; ++yy)
+          for (int xx = 0; xx < mx; ++xx) y[addr[xx + 2 * (yy + 2 * zz)]] = s;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // Atomic duplicate summation (ablation of dss_kernel): pass 1 adds every copy into its
 // unique node's accumulator with atomicAdd; pass 2 writes the accumulated sum (zero on the
@@ -1328,8 +1388,25 @@ mf_status apply_batch_launch_n(const mf_operator* op0, int vk, const void* jobs_
   if (vk == VK_DD) return batch_launch_t<double, dd, N>(op0, v, jobs_dev, block0_dev, njobs, blocks, s);
   return batch_launch_t<double, double, N>(op0, v, jobs_dev, block0_dev, njobs, blocks, s);
 }
+// The row kernel from degree 2 (measured: k = 3, 92^3: 0.204 ms against 0.277 ms); degree 1,
+// whose rows hold a single local index, keeps the lexicographic one (0.159 against 0.179 ms).
+// MF_DSS_ROWS=0 selects the lexicographic kernel everywhere (same sums, bitwise).
+#ifndef MF_DSS_ROWS
+#define MF_DSS_ROWS 1
+#endif
 template <int N>
 static mf_status dss_mode(const mf_operator* op, int elem, void* y, int avg, cudaStream_t s) {
+  if (MF_DSS_ROWS && N > 2) {
+    const int cxb = (op->g.nx + 1 + DSS_ROW_THREADS - 1) / DSS_ROW_THREADS; // nx + 1 columns at i = 0
+    const long long NYn = (long long)op->g.ny * (N - 1) + 1, NZn = (long long)op->g.nz * (N - 1) + 1;
+    const dim3 grid((unsigned)((N - 1) * cxb), (unsigned)(NYn < DSS_ROWS_Y ? NYn : DSS_ROWS_Y),
+                    (unsigned)(NZn < 65535 ? NZn : 65535));
+    if (elem == 8)
+      dss_row_kernel<double, N><<<grid, DSS_ROW_THREADS, 0, s>>>(static_cast<double*>(y), op->g, avg, cxb);
+    else
+      dss_row_kernel<float, N><<<grid, DSS_ROW_THREADS, 0, s>>>(static_cast<float*>(y), op->g, avg, cxb);
+    return cuda_check(cudaGetLastError(), "dss launch");
+  }
   const long long total = op->n_unique;
   const int thr = 256;
   const long long blocks = (total + thr - 1) / thr;
