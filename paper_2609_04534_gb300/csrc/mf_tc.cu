@@ -162,24 +162,23 @@ __device__ __forceinline__ uint64_t fixed_offset(double x, int emax) {
   return ((X ^ neg) - neg) + 0x808080808080ull;
 }
 
-// An exact integer held in a float (|v| < 2^22) as int: two full-rate instructions.
+// An exact integer held in a float (|v| <= 2^22) as int: two full-rate instructions.
 __device__ __forceinline__ int small_float_int(float v) {
   return __float_as_int(v + 12582912.0f) - 0x4B400000;
 }
 
 // double nearest below |Y| 2^p with the sign of Y (truncated: the value already carries the
-// ~2^-48 error of the digit products); underflow to 0, overflow to inf.
+// ~2^-48 error of the digit products); 0 for Y = 0; underflow to 0, overflow to inf.
 __device__ __forceinline__ double scaled_to_double(long long Y, int p) {
   const unsigned long long neg = (unsigned long long)(Y >> 63);
   unsigned long long U = ((unsigned long long)Y ^ neg) - neg;
-  if (U == 0) return 0.0;
-  const int lz = __clzll(U);
-  U <<= lz;                                  // leading one at bit 63
+  const int lz = __clzll(U);                 // 64 for U = 0
+  U <<= (lz & 63);                           // leading one at bit 63
   const int e = p + 1086 - lz;               // Y 2^p = (U >> 11) 2^(e - 1075)
-  const unsigned long long sign = neg << 63;
-  if (e <= 0) return __longlong_as_double((long long)sign);
-  if (e >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
-  return __longlong_as_double((long long)(sign | ((unsigned long long)e << 52) | ((U >> 11) & 0xFFFFFFFFFFFFFull)));
+  unsigned long long bits = (neg << 63) | ((unsigned long long)(unsigned)e << 52) + ((U >> 11) & 0xFFFFFFFFFFFFFull);
+  if ((unsigned)(e - 1) >= 2046u || U == 0) // rare: zero, underflow or overflow
+    bits = (neg << 63) | (U == 0 || e <= 0 ? 0ull : 0x7FF0000000000000ull);
+  return __longlong_as_double((long long)bits);
 }
 
 // The tile and cell coordinates of cell c of group grp; valid = a real cell of the mesh.
@@ -229,16 +228,16 @@ __global__ void __launch_bounds__(TC_NT, 1) apply_cartesian_tc(const __grid_cons
   long long g = blockIdx.x;
   if (tid == 0) tc_stage_x<N>(a, g, sX, xbar_a); // the grid never exceeds the number of groups
 
-  // Combine the six levels of group gp (cell exponent emc) for this thread's outputs: Y =
-  // sum_t C_t 256^(5-t) in 64-bit integers (C_0 256 + C_1 fills the high word), y = Y 2^(E_c +
-  // F_i - 54); stores them (0 for padding cells of real tiles, nothing for missing tiles).
-  auto combine = [&](long long gp, int emc) {
+  // Combine the six levels of group gp (cell exponent emc) for CH of this thread's outputs
+  // from i0: Y = sum_t C_t 256^(5-t) in 64-bit integers (C_0 256 + C_1 fills the high word),
+  // y = Y 2^(E_c + F_i - 54); stores them (0 for padding cells of real tiles, nothing for
+  // missing tiles).
+  auto combine = [&](long long gp, int emc, int i0) {
     long long t;
     int cx, cy, cz;
     const bool valid = tc_cell(a.g, gp, c, t, cx, cy, cz);
     double* __restrict__ yp = a.y + t * (long long)NN * BL + (c & 31);
-#pragma unroll
-    for (int i0 = q * VPT; i0 < (q + 1) * VPT; i0 += CH) {
+    {
       uint32_t r[TC_S][CH];
 #pragma unroll
       for (int lv = 0; lv < TC_S; ++lv) {
@@ -254,18 +253,18 @@ __global__ void __launch_bounds__(TC_NT, 1) apply_cartesian_tc(const __grid_cons
                        : "r"(ta));
       }
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (t >= a.g.ntiles) continue;
+      if (t >= a.g.ntiles) return;
 #pragma unroll
       for (int j = 0; j < CH; ++j) {
         const int i = i0 + j;
         if (i >= NN) continue;
         double yv = 0.0;
         if (valid) {
-          // |C_0..C_2| <= 3 n^3 2^14 < 2^22; C_3..C_5 up to 6 n^3 2^14 take the conversion unit
+          // |C_0..C_3| <= 4 n^3 2^14 <= 2^22; C_4, C_5 up to 6 n^3 2^14 take the conversion unit
           const int c0 = small_float_int(__uint_as_float(r[0][j]));
           const int c1 = small_float_int(__uint_as_float(r[1][j]));
           const int c2 = small_float_int(__uint_as_float(r[2][j]));
-          const int c3 = __float2int_rn(__uint_as_float(r[3][j]));
+          const int c3 = small_float_int(__uint_as_float(r[3][j]));
           const int c4 = __float2int_rn(__uint_as_float(r[4][j]));
           const int c5 = __float2int_rn(__uint_as_float(r[5][j]));
           const long long L = (long long)c5 + (long long)c4 * 256LL + (long long)c3 * 65536LL + (long long)c2 * 16777216LL;
@@ -283,16 +282,10 @@ __global__ void __launch_bounds__(TC_NT, 1) apply_cartesian_tc(const __grid_cons
   int it = 0;
   int abort_all = 0;
   for (; g < a.ngroups; g += gridDim.x, ++it) {
-    // (1) the previous group's products, its combine and stores
-    int bad = 0;
-    if (it > 0) {
-      bad = !mbar_wait(mbar_a, (uint32_t)((it - 1) & 1));
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (!bad) combine(gprev, emc_s[(it - 1) & 1][c]);
-    }
-    // (2) this group's x (staged one phase earlier), masked, and its quarter's largest biased
-    // exponent (2047 marks a non-finite value)
-    bad |= !mbar_wait(xbar_a, (uint32_t)(it & 1));
+    // (1) this group's x from the staging buffer (copied one phase earlier), masked, and its
+    // quarter's largest biased exponent (2047 marks a non-finite value); the previous group's
+    // products are still running meanwhile
+    int bad = !mbar_wait(xbar_a, (uint32_t)(it & 1));
     double xv[VPT];
     {
       long long t;
@@ -324,9 +317,20 @@ __global__ void __launch_bounds__(TC_NT, 1) apply_cartesian_tc(const __grid_cons
     }
     const int emc = max(max(emax_s[0][c], emax_s[1][c]), max(emax_s[2][c], emax_s[3][c]));
     if (q == 0) emc_s[it & 1][c] = emc;
-    // (3) this group's digits, CH consecutive values of a slice per store
+    // (2) the previous group's products; the tensor memory and the digit buffer are free
+    // once they have landed
+    if (it > 0) {
+      bad = !mbar_wait(mbar_a, (uint32_t)((it - 1) & 1));
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      abort_all = __syncthreads_or(bad);
+      if (abort_all) break;
+    }
+    // (3) chunk by chunk: combine and store CH outputs of the previous group, and write the
+    // digits of CH values of this group (two independent instruction streams per thread)
+    const int emp = it > 0 ? emc_s[(it - 1) & 1][c] : 0;
 #pragma unroll
     for (int k0 = 0; k0 < VPT; k0 += CH) {
+      if (it > 0) combine(gprev, emp, q * VPT + k0);
       uint64_t X[CH];
 #pragma unroll
       for (int j = 0; j < CH; ++j) X[j] = fixed_offset(xv[k0 + j], emc);
@@ -386,7 +390,9 @@ __global__ void __launch_bounds__(TC_NT, 1) apply_cartesian_tc(const __grid_cons
   if (!abort_all && it > 0) {
     const int bad = !mbar_wait(mbar_a, (uint32_t)((it - 1) & 1));
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!bad) combine(gprev, emc_s[(it - 1) & 1][c]);
+    if (!bad)
+#pragma unroll
+      for (int i0 = q * VPT; i0 < (q + 1) * VPT; i0 += CH) combine(gprev, emc_s[(it - 1) & 1][c], i0);
     abort_all = __syncthreads_or(bad);
   }
   if (abort_all) {
