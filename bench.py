@@ -409,31 +409,36 @@ def solve_compare(N=96, inner=(1e-3,), extra=True):
     autotune(mf, torch, op, b, s)
     autotune(mf, torch, op64, b, s)
     l2 = torch.zeros(1, dtype=torch.float64, device="cuda")
-    runs = [(1, t, 0) for t in inner] + [(0, 0.0, 0)]
+    # (mixed, inner tolerance, preconditioner, Chebyshev interval ratio b / a)
+    runs = [(1, t, 0, 0.0) for t in inner] + [(0, 0.0, 0, 0.0)]
     if extra:
-        runs += [(1, inner[0], 1), (0, 0.0, 1)]
-    for mixed, itol, pre in runs:
+        runs += [(1, inner[0], mf.MF_PRECOND_JACOBI, 0.0), (0, 0.0, mf.MF_PRECOND_JACOBI, 0.0)]
+        runs += [(0, 0.0, mf.MF_PRECOND_CHEBYSHEV, r) for r in (10.0, 30.0, 100.0)]
+    for mixed, itol, pre, ratio in runs:
         sop = op if mixed else op64
-        cws = torch.empty(mf.mf_cg_workspace_bytes(sop, mixed), dtype=torch.uint8, device="cuda")
+        cws = torch.empty(mf.mf_cg_workspace_bytes_ex(sop, mixed, pre), dtype=torch.uint8, device="cuda")
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         ev[0].record(stream)
         st = mf.mf_cg_solve(sop, b.data_ptr(), x.data_ptr(), 1e-10, 400000, mixed, cws.data_ptr(), cws.numel(), s,
-                            allow_not_converged=True, inner_rtol=itol,
-                            precond=mf.MF_PRECOND_JACOBI if pre else mf.MF_PRECOND_NONE)
+                            allow_not_converged=True, inner_rtol=itol, precond=pre, cheb_ratio=ratio)
         ev[1].record(stream)
         ev[1].synchronize()
         t = ev[0].elapsed_time(ev[1]) / 1e3
         mf.mf_error_manufactured(op, 2.0, x.data_ptr(), l2.data_ptr(), sc.data_ptr(), sc.numel(), s)
         stream.synchronize()
-        out[(f"mixed_inner{itol:g}" if mixed else "fp64") + ("_jacobi" if pre else "")] = {
+        tag = {mf.MF_PRECOND_NONE: "", mf.MF_PRECOND_JACOBI: "_jacobi",
+               mf.MF_PRECOND_CHEBYSHEV: f"_chebyshev{ratio:g}"}[pre]
+        out[(f"mixed_inner{itol:g}" if mixed else "fp64") + tag] = {
             "status": st["code"], "iterations": st["iterations"], "outer": st["outer_iterations"],
             "rel_residual": st["rel_residual"], "seconds": t,
+            "applies": st["iterations"] * (3 if pre == mf.MF_PRECOND_CHEBYSHEV else 1),
             "solved_gdofs_cellwise": info["n_cellwise"] / t / 1e9, "solved_gdofs_unique": info["n_unique"] / t / 1e9,
             "l2_error": float(l2.item()) ** 0.5}
         del cws
         torch.cuda.empty_cache()
     out["n_cellwise"], out["n_unique"] = info["n_cellwise"], info["n_unique"]
-    best = min((v["seconds"], kk) for kk, v in out.items() if kk.startswith("mixed_inner") and "jacobi" not in kk)
+    best = min((v["seconds"], kk) for kk, v in out.items()
+               if kk.startswith("mixed_inner") and "jacobi" not in kk and "chebyshev" not in kk)
     out["best_mixed"] = best[1]
     out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / best[0]
     mf.mf_operator_destroy(op)

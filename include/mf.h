@@ -294,17 +294,27 @@ mf_status mf_cg_solve_host(const mf_operator* op, const void* b_host, void* x_ho
  *     load (three kernels per iteration).
  * All compute the same iterates up to rounding (only <p, A p> is summed differently). */
 enum { MF_CG_DEFAULT = 0, MF_CG_SPLIT_DUAL = 1, MF_CG_ASSEMBLED = 2, MF_CG_SPLIT_DUAL_FUSED = 3 };
-/* Preconditioner (mf_solve_options.precond): none (default), or Jacobi -- z = r / diag(P A P)
- * with the assembled diagonal of mf_diagonal (0 on Dirichlet nodes); split-dual form only.
- * The convergence test stays ||r|| <= rtol ||b||; alpha and beta use <r, z>. */
-enum { MF_PRECOND_NONE = 0, MF_PRECOND_JACOBI = 1 };
+/* Preconditioner (mf_solve_options.precond): none (default), Jacobi -- z = r / diag(P A P)
+ * with the assembled diagonal of mf_diagonal (0 on Dirichlet nodes); split-dual form only --
+ * or the degree-3 Chebyshev-accelerated Jacobi method of Sec. 5.2 (the paper's smoother as a
+ * CG preconditioner): z = M^-1 r is three Richardson updates z <- z + w_j D^-1 (r - A z) from
+ * z = 0 with the weights of Eq. (chebyshev_weights) on [b / cheb_ratio, b], b = 1.1 times a
+ * 12-step power-iteration estimate of the largest eigenvalue of D^-1 A; M is symmetric positive
+ * definite.  Each CG iteration then applies the operator three times (iterations in
+ * mf_solve_stats are CG iterations); assembled vectors of the operator's element type, MF_FP64
+ * and MF_FP32 operators, mixed = 0 only; workspace mf_cg_workspace_bytes_ex().  The
+ * convergence test stays ||r|| <= rtol ||b||; alpha and beta use <r, z>. */
+enum { MF_PRECOND_NONE = 0, MF_PRECOND_JACOBI = 1, MF_PRECOND_CHEBYSHEV = 2 };
 typedef struct {
   double inner_rtol;
   int32_t chunk_iterations;
   int32_t max_outer;
   int32_t cg_form; /* MF_CG_* */
   int32_t precond; /* MF_PRECOND_* */
+  double cheb_ratio; /* MF_PRECOND_CHEBYSHEV: b / a of the target interval (0: 30) */
 } mf_solve_options;
+/* Workspace of mf_cg_solve_ex with these options (opts may be NULL: mf_cg_workspace_bytes). */
+size_t mf_cg_workspace_bytes_ex(const mf_operator* op, int mixed, const mf_solve_options* opts);
 mf_status mf_cg_solve_ex(const mf_operator* op, const void* b_dev, void* x_dev, double rtol, int maxit, int mixed,
                          const mf_solve_options* opts, mf_solve_stats* stats, void* workspace_dev, size_t bytes,
                          void* stream);

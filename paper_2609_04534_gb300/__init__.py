@@ -22,7 +22,7 @@ MF_LAPLACE, MF_HELMHOLTZ = 0, 1
 MF_FP64, MF_FP32, MF_MIXED, MF_FP64_DFMA = 0, 1, 2, 3
 MF_BC_NONE, MF_BC_DIRICHLET0 = 0, 1
 MF_CG_DEFAULT, MF_CG_SPLIT_DUAL, MF_CG_ASSEMBLED, MF_CG_SPLIT_DUAL_FUSED = 0, 1, 2, 3
-MF_PRECOND_NONE, MF_PRECOND_JACOBI = 0, 1
+MF_PRECOND_NONE, MF_PRECOND_JACOBI, MF_PRECOND_CHEBYSHEV = 0, 1, 2
 MF_VARIANT_TENSOR = 3
 
 _STATUS = {0: "MF_OK", -1: "MF_ERR_ARG", -2: "MF_ERR_OOM", -3: "MF_ERR_CUDA", -4: "MF_ERR_NOT_CONVERGED",
@@ -50,7 +50,7 @@ class mf_solve_stats(C.Structure):
 
 class mf_solve_options(C.Structure):
     _fields_ = [("inner_rtol", C.c_double), ("chunk_iterations", C.c_int32), ("max_outer", C.c_int32),
-                ("cg_form", C.c_int32), ("precond", C.c_int32)]
+                ("cg_form", C.c_int32), ("precond", C.c_int32), ("cheb_ratio", C.c_double)]
 
 
 class mf_server_config(C.Structure):
@@ -128,6 +128,8 @@ def lib() -> C.CDLL:
     L.mf_cg_record_history.argtypes = [vp, i32]
     L.mf_cg_solve_ex.argtypes = [vp, vp, vp, d, i32, i32, C.POINTER(mf_solve_options), C.POINTER(mf_solve_stats),
                                  vp, sz, vp]
+    L.mf_cg_workspace_bytes_ex.argtypes = [vp, i32, C.POINTER(mf_solve_options)]
+    L.mf_cg_workspace_bytes_ex.restype = sz
     L.mf_cg_solve_host_workspace_bytes.argtypes = [vp, i32]
     L.mf_cg_solve_host_workspace_bytes.restype = sz
     L.mf_cg_solve_host.argtypes = [vp, vp, vp, d, i32, i32, C.POINTER(mf_solve_stats), vp, sz, vp]
@@ -293,11 +295,17 @@ def mf_cg_workspace_bytes(op, mixed: int = 0) -> int:
     return int(lib().mf_cg_workspace_bytes(op, mixed))
 
 
+def mf_cg_workspace_bytes_ex(op, mixed: int = 0, precond: int = 0) -> int:
+    opts = mf_solve_options(0.0, 0, 0, 0, precond, 0.0)
+    return int(lib().mf_cg_workspace_bytes_ex(op, mixed, C.byref(opts)))
+
+
 def mf_cg_solve(op, b_ptr: int, x_ptr: int, rtol: float, maxit: int, mixed: int, workspace_ptr: int,
                 nbytes: int, stream: int = 0, allow_not_converged: bool = False, inner_rtol: float = 0.0,
-                chunk_iterations: int = 0, max_outer: int = 0, cg_form: int = 0, precond: int = 0) -> dict:
+                chunk_iterations: int = 0, max_outer: int = 0, cg_form: int = 0, precond: int = 0,
+                cheb_ratio: float = 0.0) -> dict:
     st = mf_solve_stats()
-    opts = mf_solve_options(inner_rtol, chunk_iterations, max_outer, cg_form, precond)
+    opts = mf_solve_options(inner_rtol, chunk_iterations, max_outer, cg_form, precond, cheb_ratio)
     code = lib().mf_cg_solve_ex(op, b_ptr, x_ptr, rtol, maxit, mixed, C.byref(opts), C.byref(st), workspace_ptr,
                                 nbytes, stream or None)
     if not (code == MF_OK or (allow_not_converged and code == MF_ERR_NOT_CONVERGED)):

@@ -1119,6 +1119,12 @@ size_t mf_cg_workspace_bytes(const mf_operator* op, int mixed) {
   return solve_ws_layout(op, mixed ? 1 : 0, nullptr, nullptr);
 }
 
+size_t mf_cg_workspace_bytes_ex(const mf_operator* op, int mixed, const mf_solve_options* opts) {
+  if (!op) return 0;
+  if (opts && opts->precond == MF_PRECOND_CHEBYSHEV) return cheb_workspace_bytes(op);
+  return mf_cg_workspace_bytes(op, mixed);
+}
+
 mf_status mf_cg_solve(const mf_operator* op, const void* b_dev, void* x_dev, double rtol, int maxit, int mixed,
                       mf_solve_stats* stats, void* workspace_dev, size_t bytes, void* stream) {
   return mf_cg_solve_ex(op, b_dev, x_dev, rtol, maxit, mixed, nullptr, stats, workspace_dev, bytes, stream);
@@ -1167,12 +1173,26 @@ mf_status mf_cg_solve_ex(const mf_operator* op, const void* b_dev, void* x_dev, 
   if (!op || !b_dev || !x_dev) return set_error(MF_ERR_ARG, "mf_cg_solve: NULL argument");
   if (opts && ((opts->inner_rtol != 0.0 && !(opts->inner_rtol > 0.0 && opts->inner_rtol < 1.0)) ||
                opts->chunk_iterations < 0 || opts->max_outer < 0 || opts->cg_form < 0 ||
-               opts->cg_form > MF_CG_SPLIT_DUAL_FUSED || opts->precond < 0 || opts->precond > MF_PRECOND_JACOBI ||
-               (opts->precond == MF_PRECOND_JACOBI && opts->cg_form > MF_CG_SPLIT_DUAL)))
+               opts->cg_form > MF_CG_SPLIT_DUAL_FUSED || opts->precond < 0 || opts->precond > MF_PRECOND_CHEBYSHEV ||
+               (opts->precond == MF_PRECOND_JACOBI && opts->cg_form > MF_CG_SPLIT_DUAL) ||
+               (opts->precond == MF_PRECOND_CHEBYSHEV && (mixed || opts->cheb_ratio < 0.0 ||
+                                                         (opts->cheb_ratio != 0.0 && !(opts->cheb_ratio > 1.0))))))
     return set_error(MF_ERR_ARG, "mf_cg_solve_ex: bad options");
   if (!op->ready) return set_error(MF_ERR_ARG, "mf_cg_solve: operator not set up");
   if (maxit < 0 || !(rtol >= 0.0)) return set_error(MF_ERR_ARG, "mf_cg_solve: bad rtol/maxit");
   if (mixed && op->precision != MF_MIXED) return set_error(MF_ERR_ARG, "mf_cg_solve: mixed needs an MF_MIXED operator");
+  if (opts && opts->precond == MF_PRECOND_CHEBYSHEV) {
+    if (!workspace_dev || (reinterpret_cast<uintptr_t>(workspace_dev) & 255))
+      return set_error(MF_ERR_ARG, "mf_cg_solve: workspace NULL or not 256-byte aligned");
+    const auto t0 = std::chrono::steady_clock::now();
+    mf_solve_stats local;
+    mf_solve_stats* sp = stats ? stats : &local;
+    std::memset(sp, 0, sizeof(*sp));
+    mf_status rc = cheb_solve(op, b_dev, x_dev, rtol, maxit, opts->cheb_ratio, sp, workspace_dev, bytes,
+                              static_cast<cudaStream_t>(stream));
+    sp->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+  }
   const size_t need = mf_cg_workspace_bytes(op, mixed);
   if (!workspace_dev || bytes < need) return set_error(MF_ERR_OOM, "mf_cg_solve: workspace %zu < %zu", bytes, need);
   if (reinterpret_cast<uintptr_t>(workspace_dev) & 255) return set_error(MF_ERR_ARG, "mf_cg_solve: workspace alignment");

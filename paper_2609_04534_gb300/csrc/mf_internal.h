@@ -249,6 +249,11 @@ mf_status tc_setup(mf_operator* op, void* table_dev, cudaStream_t s); // builds 
 mf_status tc_apply(const mf_operator* op, const void* x, void* y, cudaStream_t s);
 int tc_read_error(int reset);                              // device error word (synchronous)
 
+// CG preconditioned by degree-3 Chebyshev-accelerated Jacobi (mf_cheb.cu)
+size_t cheb_workspace_bytes(const mf_operator* op);
+mf_status cheb_solve(const mf_operator* op, const void* b, void* x, double rtol, int maxit, double ratio,
+                     mf_solve_stats* stats, void* ws, size_t bytes, cudaStream_t s);
+
 // layout modes
 enum { LAYOUT_TO_NATIVE = 0, LAYOUT_FROM_NATIVE = 1, LAYOUT_SCATTER_UNIQUE = 2, LAYOUT_GATHER_UNIQUE = 3 };
 

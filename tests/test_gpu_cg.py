@@ -252,3 +252,33 @@ def test_cg_solve_host_matches_device_solve(geom, k, prec):
     assert sth["iterations"] == st["iterations"] and sth["rel_residual"] == st["rel_residual"]
     assert np.array_equal(xh.double().numpy(), xc)
     d.close()
+
+
+@pytest.mark.parametrize("dims,k,geom,kind,prec,bc,ratio", [
+    ((7, 6, 5), 3, "curved", mf.MF_LAPLACE, mf.MF_FP64, 1, 0.0),
+    ((9, 5, 3), 2, "cart", mf.MF_HELMHOLTZ, mf.MF_FP64, 0, 10.0),
+    ((6, 5, 4), 4, "shear", mf.MF_LAPLACE, mf.MF_FP64, 1, 100.0),
+    ((7, 6, 5), 3, "curved", mf.MF_LAPLACE, mf.MF_FP32, 1, 0.0),
+])
+def test_chebyshev_jacobi_pcg_solves_oracle_equations(oracle, dims, k, geom, kind, prec, bc, ratio):
+    """CG preconditioned by the degree-3 Chebyshev-accelerated Jacobi method (Sec. 5.2,
+    Eqs. (chebyshev_weights), (chebyshev_richardson)): the solution satisfies the oracle's
+    equations, and it takes fewer CG iterations than the unpreconditioned solver."""
+    d = DevOp(*dims, k, geom, kind, 1.0, prec, bc)
+    bu = inputs.random_unique(*dims, k, 19)
+    b = d.native_from_unique(bu)
+    rtol = 1e-5 if prec == mf.MF_FP32 else 1e-11
+    x = torch.zeros(d.n_native, dtype=d.dtype, device="cuda")
+    ws = torch.empty(mf.mf_cg_workspace_bytes_ex(d.op, 0, mf.MF_PRECOND_CHEBYSHEV), dtype=torch.uint8, device="cuda")
+    st = mf.mf_cg_solve(d.op, b.data_ptr(), x.data_ptr(), rtol, 5000, 0, ws.data_ptr(), ws.numel(),
+                        precond=mf.MF_PRECOND_CHEBYSHEV, cheb_ratio=ratio)
+    assert st["code"] == mf.MF_OK and st["rel_residual"] <= rtol
+    o = oracle_op(oracle, *dims, k, geom, 1.0 if kind == mf.MF_HELMHOLTZ else 0.0, bc)
+    bm = np.where(o.boundary_mask(), 0.0, bu) if bc else bu
+    if prec == mf.MF_FP32:
+        bm = np.where(o.boundary_mask(), 0.0, bu.astype(np.float32).astype(np.float64)) if bc else bu
+    res = np.linalg.norm(bm - o.apply(d.unique_from_native(x))) / np.linalg.norm(bm)
+    assert res <= (1e-4 if prec == mf.MF_FP32 else 2e-11), res
+    _, st0, _ = solve(d, b, rtol, 5000, 0)
+    assert st["iterations"] < st0["iterations"], (st["iterations"], st0["iterations"])
+    d.close()
