@@ -114,7 +114,10 @@ mf_status mf_operator_setup(mf_operator* op, void* workspace_dev, size_t bytes, 
  * apply, see MF_VARIANT_TENSOR) with `reps` applies of x_dev into y_dev (both native vectors
  * of this operator; y is overwritten) and keeps the fastest.  The choice is cached per
  * (device, degree, path, kind, precision) for the life of the process, so later operators of
- * the same class reuse it without timing.  Synchronises `stream`.  Variants 0-2 run the same
+ * the same class reuse it without timing, and persisted across processes in a JSON file keyed
+ * by the GPU's name (MF_AUTOTUNE_CACHE, else $XDG_CACHE_HOME/libmf/autotune.json or
+ * $HOME/.cache/libmf/autotune.json; MF_AUTOTUNE_CACHE=off disables the file): a stored choice
+ * is used without timing.  Synchronises `stream` when it times.  Variants 0-2 run the same
  * per-thread arithmetic and give bitwise equal results; variant 3 rounds differently (same
  * accuracy class), so its results agree with theirs within 1e-12 relative max-norm. */
 mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, int reps, void* stream);

@@ -2,11 +2,16 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <new>
+#include <string>
 #include <tuple>
+
+#include <sys/stat.h>
+#include <unistd.h>
 
 #include "mf_dd.cuh"
 #include "mf_internal.h"
@@ -366,6 +371,78 @@ mf_status mf_apply_host(const mf_operator* op, const void* x_host, void* y_host,
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int, int, int, int, int>, int> g_tune_cache; // (device, n, path, kind, view) -> variant
 
+// The autotuner's choices persist across processes in a JSON object of "key": variant
+// entries, one per line, with key "<GPU name>|lib=2|n=<n>|path=<p>|kind=<k>|view=<v>".  The
+// file is MF_AUTOTUNE_CACHE if set ("off" disables it), else $XDG_CACHE_HOME/libmf/
+// autotune.json or $HOME/.cache/libmf/autotune.json.  It is read once per process (entries of
+// other GPUs are kept and written back) and rewritten through a temporary file after each new
+// choice; a missing or unreadable file only means the variants are timed again.
+static std::map<std::string, int> g_tune_file;
+static bool g_tune_file_loaded = false;
+
+static std::string tune_file_path() {
+  const char* e = std::getenv("MF_AUTOTUNE_CACHE");
+  if (e && *e) return std::strcmp(e, "off") == 0 ? std::string() : std::string(e);
+  const char* x = std::getenv("XDG_CACHE_HOME");
+  if (x && *x) return std::string(x) + "/libmf/autotune.json";
+  const char* h = std::getenv("HOME");
+  if (h && *h) return std::string(h) + "/.cache/libmf/autotune.json";
+  return std::string();
+}
+
+static void tune_file_load(const std::string& path) {
+  g_tune_file_loaded = true;
+  if (path.empty()) return;
+  FILE* f = std::fopen(path.c_str(), "r");
+  if (!f) return;
+  char line[1024];
+  while (std::fgets(line, sizeof(line), f)) {
+    const char* q0 = std::strchr(line, '"');
+    if (!q0) continue;
+    const char* q1 = std::strchr(q0 + 1, '"');
+    if (!q1) continue;
+    const char* colon = std::strchr(q1, ':');
+    if (!colon) continue;
+    int v = -1;
+    if (std::sscanf(colon + 1, " %d", &v) == 1 && v >= 0 && v <= MF_VARIANT_TENSOR)
+      g_tune_file[std::string(q0 + 1, q1)] = v;
+  }
+  std::fclose(f);
+}
+
+static void tune_file_store(const std::string& path) {
+  if (path.empty()) return;
+  const std::string dir = path.substr(0, path.find_last_of('/'));
+  if (!dir.empty() && dir != path) {
+    // create the directory chain (best effort)
+    for (size_t i = 1; i <= dir.size(); ++i)
+      if (i == dir.size() || dir[i] == '/') mkdir(dir.substr(0, i).c_str(), 0755);
+  }
+  const std::string tmp = path + "." + std::to_string((long long)getpid()) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return;
+  std::fprintf(f, "{\n");
+  size_t i = 0;
+  for (const auto& kv : g_tune_file) {
+    std::string k;
+    for (char ch : kv.first) k += (ch == '"' || ch == '\\') ? '_' : ch;
+    std::fprintf(f, "  \"%s\": %d%s\n", k.c_str(), kv.second, ++i < g_tune_file.size() ? "," : "");
+  }
+  std::fprintf(f, "}\n");
+  const bool ok = std::fclose(f) == 0;
+  if (ok) std::rename(tmp.c_str(), path.c_str());
+  else std::remove(tmp.c_str());
+}
+
+static std::string tune_key(int dev, const mf_operator* op, int vk) {
+  cudaDeviceProp prop;
+  std::string name = "unknown";
+  if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+  char buf[160];
+  std::snprintf(buf, sizeof(buf), "|lib=2|n=%d|path=%d|kind=%d|view=%d", op->n, op->path, op->kind, vk);
+  return name + buf;
+}
+
 mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, int reps, void* stream) {
   mf_status st = check_ready(op, "mf_operator_autotune");
   if (st) return st;
@@ -376,11 +453,22 @@ mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, 
   if ((st = cuda_check(cudaGetDevice(&dev), "cudaGetDevice"))) return st;
   const int vk = view_of_elem(op, elem_of(op));
   const auto key = std::make_tuple(dev, op->n, op->path, op->kind, vk);
+  const std::string fkey = tune_key(dev, op, vk);
+  const std::string fpath = tune_file_path();
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
       op->variant[vk] = it->second;
+      return MF_OK;
+    }
+    if (!g_tune_file_loaded) tune_file_load(fpath);
+    auto ft = g_tune_file.find(fkey);
+    // a stored choice is used if it is valid for this operator (the tensor-core variant only
+    // where it is built)
+    if (ft != g_tune_file.end() && (ft->second < MF_VARIANT_TENSOR || (vk == VK_DD && tc_eligible(op)))) {
+      op->variant[vk] = ft->second;
+      g_tune_cache[key] = ft->second;
       return MF_OK;
     }
   }
@@ -409,6 +497,8 @@ mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, 
   if (st) return st;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune_cache[key] = best_v;
+  g_tune_file[fkey] = best_v;
+  tune_file_store(fpath);
   return MF_OK;
 }
 

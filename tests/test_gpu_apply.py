@@ -3,6 +3,8 @@
 Tolerances (relative max-norm max|y - y_ref| / max|y_ref|): FP64 1e-12, FP32 1e-5.
 Meshes span several 4x4x2 tiles with ragged tails in every direction.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -353,3 +355,35 @@ def test_stream_twin_copies_x(geom, kind, prec, k, dims, variant):
     with pytest.raises(mf.MfError):
         mf.mf_apply_stream_twin(d.op, x.data_ptr(), x.data_ptr())
     d.close()
+
+
+def test_autotune_choice_persists_in_json_file(tmp_path):
+    """The autotuner writes its choice to the JSON cache keyed by the GPU's name, and a fresh
+    process takes a stored choice from the file instead of timing (a planted entry wins)."""
+    import json
+    import subprocess
+    import sys
+
+    cache = tmp_path / "autotune.json"
+    code = (
+        "import sys, torch; sys.path.insert(0, %r)\n"
+        "import paper_2609_04534_gb300 as mf\n"
+        "from paper_2609_04534_gb300 import inputs\n"
+        "from tests._gpu import DevOp\n"
+        "d = DevOp(5, 6, 3, 4, 'curved', mf.MF_LAPLACE, 1.0, mf.MF_FP64, 0)\n"
+        "x = d.native_from_unique(inputs.random_unique(5, 6, 3, 4, 3)); y = torch.empty_like(x)\n"
+        "print(mf.mf_operator_autotune(d.op, x.data_ptr(), y.data_ptr(), 2))\n"
+    ) % (os.path.dirname(os.path.dirname(os.path.abspath(__file__))),)
+    env = dict(os.environ, MF_AUTOTUNE_CACHE=str(cache))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    v = int(r.stdout.strip().splitlines()[-1])
+    entries = json.loads(cache.read_text())
+    keys = [k for k in entries if "|n=5|path=2|" in k]
+    assert len(keys) == 1 and entries[keys[0]] == v and torch.cuda.get_device_name(0) in keys[0]
+    planted = (v + 1) % 3
+    entries[keys[0]] = planted
+    cache.write_text(json.dumps(entries))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert int(r.stdout.strip().splitlines()[-1]) == planted
