@@ -49,11 +49,23 @@ struct EoTab {
   static constexpr int H = N / 2, HE = (N + 1) / 2;
   T F[H * HE], G[H * H > 0 ? H * H : 1], Mid[HE];
 };
+// Fast diagonalisation of the 1D pencil (K, M): W = M V with V^T M V = I, V^T K V = diag(lam),
+// so M = W W^T and K = W diag(lam) W^T.  Both matrices are centro-symmetric, so every column
+// of W (mode) is symmetric or antisymmetric; the modes are stored with the HE symmetric ones
+// first.  Forward z = W^T x on a folded pencil: z_s = Ff e (HE x HE), z_a = Gf o (H x H);
+// backward y = W z: U = Fb z_s (HE outputs), V = Gb z_a (H outputs), y_j = U_j + V_j,
+// y_(n-1-j) = U_j - V_j.  lam in the same mode order.
+template <typename T, int N>
+struct FdTab {
+  static constexpr int H = N / 2, HE = (N + 1) / 2;
+  T Ff[HE * HE], Gf[H * H > 0 ? H * H : 1], Fb[HE * HE], Gb[H * H > 0 ? H * H : 1], lam[N];
+};
 // What the apply kernels read: the Gauss weights and every 1D matrix in even-odd form.
 template <typename T, int N>
 struct Tab {
   T W[N];
   EoTab<T, N> eS, eSt, eD, eDt, eM, eK; // S, S^T, Dc, Dc^T, M, K
+  FdTab<T, N> fd;                       // the Cartesian form's modes (fast diagonalisation)
 };
 
 // Precision views of an operator: storage type of the vectors / compute type of the apply.
@@ -147,6 +159,9 @@ struct HostTables {
   int n;
   double nodes[MAXN], qx[MAXN], qw[MAXN];
   double S[MAXN * MAXN], D[MAXN * MAXN], Dc[MAXN * MAXN], M[MAXN * MAXN], K[MAXN * MAXN];
+  // fast diagonalisation of (K, M): Wfd[j * MAXN + m] = W_jm for mode m (symmetric modes
+  // first, each group by increasing eigenvalue), lam[m] its eigenvalue
+  double Wfd[MAXN * MAXN], lam[MAXN];
 };
 int make_host_tables(int degree, HostTables* t);
 

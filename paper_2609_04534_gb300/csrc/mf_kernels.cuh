@@ -381,6 +381,120 @@ __device__ __forceinline__ void cartesian_body(const ApplyJob<S, T>& a, const Ta
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Cartesian cells in fast-diagonalised form: with W = M V (V^T M V = I, V^T K V = diag(lam)),
+// M = W W^T and K = W diag(lam) W^T, so the seven-contraction operator of Eq. (eval_pipeline)
+// is A_e = (W(x)W(x)W) diag(d) (W(x)W(x)W)^T with d(i,j,k) = gx lam_i + gy lam_j + gz lam_k
+// [+ c]: three forward sweeps W^T, a pointwise scale, three backward sweeps W.  Six
+// single-input contractions (folded: every mode is symmetric or antisymmetric) instead of
+// seven, and the pointwise scale replaces the combination of the contractions.
+// ---------------------------------------------------------------------------------------
+// forward: modes of a pencil (symmetric first), from its folded sums and differences
+template <typename C, typename T, int N>
+__device__ __forceinline__ void fd_forward(const FdTab<C, N>& t, const T* in, T* out) {
+  constexpr int H = N / 2, HE = (N + 1) / 2;
+  const Fold<T, N, false> f(in);
+#pragma unroll
+  for (int m = 0; m < HE; ++m) out[m] = finish(chain<C, T, HE>(t.Ff + m * HE, f.e));
+#pragma unroll
+  for (int m = 0; m < H; ++m) out[HE + m] = finish(chain<C, T, H>(t.Gf + m * H, f.o));
+}
+// backward: nodal values of a pencil from its modes
+template <typename C, typename T, int N>
+__device__ __forceinline__ void fd_backward(const FdTab<C, N>& t, const T* z, T* out) {
+  constexpr int H = N / 2, HE = (N + 1) / 2;
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    const T u = chain<C, T, HE>(t.Fb + j * HE, z);
+    const T v = chain<C, T, H>(t.Gb + j * H, z + HE);
+    out[j] = finish(add_lazy(u, v));
+    out[N - 1 - j] = finish(sub_lazy(u, v));
+  }
+  if (N % 2) out[H] = finish(chain<C, T, HE>(t.Fb + H * HE, z));
+}
+
+template <typename S, typename T, int N, int CB, bool HELM>
+__device__ __forceinline__ void cartesian_fd_body(const ApplyJob<S, T>& a, const Tab<typename CoefOf<T>::type, N>& tab,
+                                                  long long t, int lane0, long long cta) {
+  using C = typename CoefOf<T>::type;
+  constexpr int N2 = N * N, N3 = N2 * N, NT = N2 * CB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* buf0 = reinterpret_cast<T*>(smem_raw);
+  if (a.cg.st != nullptr && a.cg.st->flag != 0) return; // CG step after convergence: no work
+  prefetch_next_wave<S, T, N, 0>(a, t, lane0);
+  load_tile<S, T, N, CB, NT>(a, t, lane0, buf0);
+  __syncthreads();
+  const int c = threadIdx.x % CB, p = threadIdx.x / CB, pa = p % N, pb = p / N;
+  const FdTab<C, N>& fd = tab.fd;
+  { // forward x: pencil (j=pa, k=pb)
+    T in[N], out[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) in[i] = buf0[(i + N * pa + N2 * pb) * CB + c];
+    fd_forward<C, T, N>(fd, in, out);
+#pragma unroll
+    for (int i = 0; i < N; ++i) buf0[(i + N * pa + N2 * pb) * CB + c] = out[i];
+  }
+  __syncthreads();
+  { // forward y: pencil (i=pa, k=pb)
+    T in[N], out[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) in[j] = buf0[(pa + N * j + N2 * pb) * CB + c];
+    fd_forward<C, T, N>(fd, in, out);
+#pragma unroll
+    for (int j = 0; j < N; ++j) buf0[(pa + N * j + N2 * pb) * CB + c] = out[j];
+  }
+  __syncthreads();
+  { // forward z, scale by d = gx lam_pa + gy lam_pb + gz lam_k (+ c), backward z: pencil (i=pa, j=pb)
+    T in[N], z[N], out[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) in[k] = buf0[(pa + N * pb + N2 * k) * CB + c];
+    fd_forward<C, T, N>(fd, in, z);
+    T dxy = fma(fd.lam[pb], a.gy, mul0(fd.lam[pa], a.gx));
+    if (HELM) dxy = add_lazy(dxy, a.cmass);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const T dk = finish(fma(fd.lam[k], a.gz, dxy));
+      z[k] = finish(mul0(dk, z[k]));
+    }
+    fd_backward<C, T, N>(fd, z, out);
+#pragma unroll
+    for (int k = 0; k < N; ++k) buf0[(pa + N * pb + N2 * k) * CB + c] = out[k];
+  }
+  __syncthreads();
+  { // backward y: pencil (i=pa, k=pb)
+    T z[N], out[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) z[j] = buf0[(pa + N * j + N2 * pb) * CB + c];
+    fd_backward<C, T, N>(fd, z, out);
+#pragma unroll
+    for (int j = 0; j < N; ++j) buf0[(pa + N * j + N2 * pb) * CB + c] = out[j];
+  }
+  __syncthreads();
+  PairAcc<S> acc;
+  { // backward x: pencil (j=pa, k=pb) -> global (a fused CG step pairs each stored value with p)
+    constexpr int CPL = CellsPer<T>::value;
+    S pv[N * CPL];
+    if (a.cg.st != nullptr) {
+      const S* __restrict__ pg = (a.cg.update_p ? a.cg.p : a.x) + t * (long long)N3 * BL + lane0 + c * CPL;
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) pv[i * CPL + j] = pg[(long long)(i + N * pa + N2 * pb) * BL + j];
+    }
+    T z[N], o[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) z[i] = buf0[(i + N * pa + N2 * pb) * CB + c];
+    fd_backward<C, T, N>(fd, z, o);
+    store_xpencil<S, T, N, CB>(a, t, lane0, c, pa, pb, o, acc, pv);
+  }
+  if (a.cg.st != nullptr) {
+    __shared__ double red[NT];
+    red[threadIdx.x] = acc.value();
+    __syncthreads();
+    cta_partial_after_barrier<NT>(red, a.cg.partials, cta);
+  }
+}
+
 // The metric of the FP32 curved view at one Gauss point of one cell, computed from the sin
 // and cos of pi xh per direction: the map x = xh + amp s(xh) (1,1,1) has J = (I + u v^T) D
 // with u = amp (1,1,1), v = grad s, D = diag(h); Sherman-Morrison gives J^-1 = D^-1 (I - u v^T
@@ -612,10 +726,20 @@ __device__ __forceinline__ void general_body(const ApplyJob<S, T>& a, const Tab<
 // Kernels: one operator per launch (CTA b = cells (b % GPT) * CB .. of tile b / GPT), or a
 // batch of operators of one degree (see ApplyBatch): the CTA finds its job by binary search
 // over the block offsets and copies the job's description into shared memory.
+// MF_CART_FD=0 selects the seven-contraction Cartesian body instead of the fast-diagonalised one
+#ifndef MF_CART_FD
+#define MF_CART_FD 1
+#endif
+template <typename S, typename T, int N, int CB, bool HELM>
+__device__ __forceinline__ void cartesian_apply(const ApplyJob<S, T>& a, const Tab<typename CoefOf<T>::type, N>& tab,
+                                                long long t, int lane0, long long cta) {
+  if (MF_CART_FD) cartesian_fd_body<S, T, N, CB, HELM>(a, tab, t, lane0, cta);
+  else cartesian_body<S, T, N, CB, HELM>(a, tab, t, lane0, cta);
+}
 template <typename S, typename T, int N, int CB, int MINB, bool HELM>
 __global__ void __launch_bounds__(N * N * CB, MINB) apply_cartesian(ApplyArgs<S, T, N> A) {
   constexpr int CC = CB * CellsPer<T>::value, GPT = BL / CC; // cells per CTA, CTAs per tile
-  cartesian_body<S, T, N, CB, HELM>(A.j, A.tab, blockIdx.x / GPT, (blockIdx.x % GPT) * CC, blockIdx.x);
+  cartesian_apply<S, T, N, CB, HELM>(A.j, A.tab, blockIdx.x / GPT, (blockIdx.x % GPT) * CC, blockIdx.x);
 }
 template <typename S, typename T, int N, int CB, int MINB, bool CURVED, bool HELM>
 __global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T, N> A) {
@@ -651,7 +775,7 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_cartesian_batch(ApplyB
   constexpr int CC = CB * CellsPer<T>::value, GPT = BL / CC;
   __shared__ __align__(16) ApplyJob<S, T> sj;
   const long long b = batch_job(B.jobs, B.block0, B.njobs, sj);
-  cartesian_body<S, T, N, CB, HELM>(sj, B.tab, b / GPT, (int)(b % GPT) * CC, b);
+  cartesian_apply<S, T, N, CB, HELM>(sj, B.tab, b / GPT, (int)(b % GPT) * CC, b);
 }
 template <typename S, typename T, int N, int CB, int MINB, bool CURVED, bool HELM>
 __global__ void __launch_bounds__(N * N * CB, MINB) apply_general_batch(ApplyBatch<S, T, N> B) {
@@ -1193,6 +1317,20 @@ static void fill_tab(const mf_operator* op, Tab<T, N>& tab) {
   fill_eo<T, N>(h.M, false, tab.eM);
   fill_eo<T, N>(h.K, false, tab.eK);
   for (int q = 0; q < N; ++q) tab.W[q] = host_from_double<T>(h.qw[q]);
+  // fast diagonalisation (modes: HE symmetric, then H antisymmetric)
+  constexpr int H = N / 2, HE = (N + 1) / 2;
+  auto Wm = [&](int j, int m) { return h.Wfd[j * MAXN + m]; };
+  for (int m = 0; m < HE; ++m) {
+    for (int j = 0; j < H; ++j) tab.fd.Ff[m * HE + j] = host_from_double<T>(Wm(j, m));
+    if (N % 2) tab.fd.Ff[m * HE + H] = host_from_double<T>(Wm(H, m));
+  }
+  for (int m = 0; m < H; ++m)
+    for (int j = 0; j < H; ++j) tab.fd.Gf[m * H + j] = host_from_double<T>(Wm(j, HE + m));
+  for (int j = 0; j < HE; ++j)
+    for (int m = 0; m < HE; ++m) tab.fd.Fb[j * HE + m] = host_from_double<T>(Wm(j, m));
+  for (int j = 0; j < H; ++j)
+    for (int m = 0; m < H; ++m) tab.fd.Gb[j * H + m] = host_from_double<T>(Wm(j, HE + m));
+  for (int m = 0; m < N; ++m) tab.fd.lam[m] = host_from_double<T>(h.lam[m]);
 }
 
 // L2 prefetch distance of an apply launch: MF_PREFETCH_WAVES waves of resident CTAs, in
@@ -1236,7 +1374,8 @@ static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, co
   a.j.y = static_cast<S*>(y);
   a.j.geom = static_cast<const T*>(geom);
   const bool helm = op->kind == MF_HELMHOLTZ;
-  const size_t smem = (op->path == PATH_CARTESIAN ? 2 : 3) * sizeof(T) * N * N * N * C::CB;
+  // buffers of n^3 values per cell: Cartesian 1 (fast-diagonalised) or 2, general 3
+  const size_t smem = (op->path == PATH_CARTESIAN ? (MF_CART_FD ? 1 : 2) : 3) * sizeof(T) * N * N * N * C::CB;
   const long long blocks = op->g.ntiles * (BL / (C::CB * C::CPL));
   if (nblocks) *nblocks = blocks;
   if (blocks <= 0) return MF_OK;
@@ -1336,7 +1475,7 @@ static mf_status batch_launch_v(const mf_operator* op0, const void* jobs_dev, co
   B.block0 = block0_dev;
   B.njobs = njobs;
   const bool helm = op0->kind == MF_HELMHOLTZ;
-  const size_t smem = (op0->path == PATH_CARTESIAN ? 2 : 3) * sizeof(T) * N * N * N * C::CB;
+  const size_t smem = (op0->path == PATH_CARTESIAN ? (MF_CART_FD ? 1 : 2) : 3) * sizeof(T) * N * N * N * C::CB;
   if (blocks <= 0 || njobs <= 0) return MF_OK;
   void (*k)(ApplyBatch<S, T, N>) = nullptr;
   if (op0->path == PATH_CARTESIAN)

@@ -91,6 +91,116 @@ void lagrange_at(int n, const double* xn, double s, double* v, double* d) {
   }
 }
 
+// Generalised symmetric eigenproblem K v = lam M v (M SPD) in long double: M = L L^T,
+// C = L^-1 K L^-T, cyclic Jacobi rotations C = Q diag(lam) Q^T, V = L^-T Q (V^T M V = I),
+// W = M V.  The pencil is centro-symmetric (J K J = K, J M J = M with the flip J), so every
+// mode is symmetric or antisymmetric; the parity is imposed exactly and the modes are sorted
+// symmetric first, each group by eigenvalue.
+void fast_diag(int n, const double* Mm, const double* Km, double* Wout, double* lam_out) {
+  typedef long double R;
+  R L[MAXN][MAXN] = {}, C[MAXN][MAXN], Q[MAXN][MAXN], T[MAXN][MAXN];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j <= i; ++j) {
+      R s = Mm[i * MAXN + j];
+      for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+      L[i][j] = i == j ? std::sqrt(s) : s / L[j][j];
+    }
+  // T = L^-1 K (forward substitution per column), C = T L^-T = L^-1 (L^-1 K)^T
+  for (int c = 0; c < n; ++c)
+    for (int i = 0; i < n; ++i) {
+      R s = Km[i * MAXN + c];
+      for (int k = 0; k < i; ++k) s -= L[i][k] * T[k][c];
+      T[i][c] = s / L[i][i];
+    }
+  for (int r = 0; r < n; ++r)
+    for (int i = 0; i < n; ++i) {
+      R s = T[r][i];
+      for (int k = 0; k < i; ++k) s -= L[i][k] * C[r][k];
+      C[r][i] = s / L[i][i];
+    }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Q[i][j] = i == j ? 1 : 0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    R off = 0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += C[p][q] * C[p][q];
+    if (off < 1e-60L) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        if (C[p][q] == 0) continue;
+        const R th = (C[q][q] - C[p][p]) / (2 * C[p][q]);
+        const R t = (th >= 0 ? 1 : -1) / (std::fabs(th) + std::sqrt(th * th + 1));
+        const R cs = 1 / std::sqrt(t * t + 1), sn = t * cs;
+        for (int k = 0; k < n; ++k) { // rotate columns p, q
+          const R a = C[k][p], b = C[k][q];
+          C[k][p] = cs * a - sn * b;
+          C[k][q] = sn * a + cs * b;
+        }
+        for (int k = 0; k < n; ++k) { // rotate rows p, q
+          const R a = C[p][k], b = C[q][k];
+          C[p][k] = cs * a - sn * b;
+          C[q][k] = sn * a + cs * b;
+        }
+        for (int k = 0; k < n; ++k) {
+          const R a = Q[k][p], b = Q[k][q];
+          Q[k][p] = cs * a - sn * b;
+          Q[k][q] = sn * a + cs * b;
+        }
+      }
+  }
+  // V = L^-T Q (back substitution per column), W = M V
+  R V[MAXN][MAXN], W[MAXN][MAXN];
+  for (int m = 0; m < n; ++m)
+    for (int i = n - 1; i >= 0; --i) {
+      R s = Q[i][m];
+      for (int k = i + 1; k < n; ++k) s -= L[k][i] * V[k][m];
+      V[i][m] = s / L[i][i];
+    }
+  int par[MAXN];
+  for (int m = 0; m < n; ++m) {
+    R ds = 0, da = 0;
+    for (int j = 0; j < n; ++j) {
+      ds += std::fabs(V[j][m] - V[n - 1 - j][m]);
+      da += std::fabs(V[j][m] + V[n - 1 - j][m]);
+    }
+    par[m] = da < ds ? 1 : 0; // 1: antisymmetric
+    for (int j = 0; j < (n + 1) / 2; ++j) {
+      const R a = V[j][m], b = V[n - 1 - j][m];
+      if (par[m]) { V[j][m] = (a - b) / 2; V[n - 1 - j][m] = -(a - b) / 2; }
+      else { V[j][m] = (a + b) / 2; V[n - 1 - j][m] = (a + b) / 2; }
+      if (par[m] && j == n - 1 - j) V[j][m] = 0;
+    }
+  }
+  for (int j = 0; j < n; ++j)
+    for (int m = 0; m < n; ++m) {
+      R s = 0;
+      for (int k = 0; k < n; ++k) s += (R)Mm[j * MAXN + k] * V[k][m];
+      W[j][m] = s;
+    }
+  for (int m = 0; m < n; ++m) // the parity of W's columns exactly as V's
+    for (int j = 0; j < (n + 1) / 2; ++j) {
+      const R a = W[j][m], b = W[n - 1 - j][m];
+      if (par[m]) { W[j][m] = (a - b) / 2; W[n - 1 - j][m] = -(a - b) / 2; if (j == n - 1 - j) W[j][m] = 0; }
+      else { W[j][m] = (a + b) / 2; W[n - 1 - j][m] = (a + b) / 2; }
+    }
+  // order: symmetric modes, then antisymmetric, each by eigenvalue
+  int ord[MAXN], no = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    int sel[MAXN], ns = 0;
+    for (int m = 0; m < n; ++m)
+      if (par[m] == pass) sel[ns++] = m;
+    for (int a = 0; a < ns; ++a)
+      for (int b = a + 1; b < ns; ++b)
+        if (C[sel[b]][sel[b]] < C[sel[a]][sel[a]]) { const int t = sel[a]; sel[a] = sel[b]; sel[b] = t; }
+    for (int a = 0; a < ns; ++a) ord[no++] = sel[a];
+  }
+  for (int mm = 0; mm < n; ++mm) {
+    const int m = ord[mm];
+    lam_out[mm] = (double)C[m][m];
+    for (int j = 0; j < n; ++j) Wout[j * MAXN + mm] = (double)W[j][m];
+  }
+}
+
 } // namespace
 
 int make_host_tables(int degree, HostTables* t) {
@@ -124,6 +234,7 @@ int make_host_tables(int degree, HostTables* t) {
       t->M[i * MAXN + j] = m;
       t->K[i * MAXN + j] = k;
     }
+  fast_diag(n, t->M, t->K, t->Wfd, t->lam);
   return 0;
 }
 
