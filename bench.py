@@ -132,8 +132,8 @@ def aggregate_ranks(dist, device, t_local: float, units_local: float):
     return float(tmax.item()), float(units.item()) / float(tmax.item())
 
 
-def make_op(mf, torch, N, k, geom, kind, prec, bc, stream):
-    mesh = mf.mf_mesh_create(N, N, N, geom, None, 0.1)
+def make_op(mf, torch, N, k, geom, kind, prec, bc, stream, affine=None):
+    mesh = mf.mf_mesh_create(N, N, N, geom, affine, 0.1)
     op = mf.mf_operator_create(mesh, k, kind, 1.0, prec, bc)
     info = mf.mf_operator_info(op)
     ws = torch.empty(max(info["workspace_bytes"], 256), dtype=torch.uint8, device="cuda")
@@ -288,7 +288,10 @@ def profile_apply(args):
     dt = torch.float64 if p == mf.MF_FP64 else torch.float32
     stream = torch.cuda.Stream()
     s = stream.cuda_stream
-    mesh, op, info, ws = make_op(mf, torch, N, k, g, kd, p, 0, s)
+    # geom "shear": a sheared affine map (the general path with one metric per mesh: the curved
+    # kernel's arithmetic without its per-point metric stream)
+    shear = [1.0, 0.3, 0.0, 0.1, 1.2, -0.2, 0.0, 0.25, 0.9, 0.0, 0.0, 0.0] if geom == "shear" else None
+    mesh, op, info, ws = make_op(mf, torch, N, k, g, kd, p, 0, s, affine=shear)
     with torch.cuda.stream(stream):
         x = random_native(mf, torch, op, info, N, k, 1, dt, s)
         y = torch.empty_like(x)

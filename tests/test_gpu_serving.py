@@ -158,3 +158,25 @@ def test_oversize_cancel_and_bounded_drain():
         assert r1["status"] == mf.MF_ERR_CANCELLED and r2["status"] == mf.MF_ERR_CANCELLED
     finally:
         mf.mf_server_destroy(sv)
+
+
+def test_large_curved_q6_request_reaches_1e_10():
+    """The largest kind of request of the serving stream -- curved Q6 on 60^3 cells (74 M
+    cell-wise DoFs), mixed precision -- reaches relative residual 1e-10 through the server
+    (the FP64 outer residual keeps the defect correction's true residual below the target)."""
+    sv, arena = make_server(arena_gb=40.0, slots=4)
+    try:
+        r = mf.make_request(60, 60, 60, 6, geometry=mf.MF_CURVED_SIN, rhs=mf.MF_RHS_MANUFACTURED, rtol=1e-10,
+                            maxit=400000, mixed=1)
+        t = mf.mf_batch_submit(sv, r)
+        t0 = time.time()
+        res = None
+        while res is None:
+            res = mf.mf_batch_poll(sv, t)
+            assert time.time() - t0 < 240.0, "request timed out"
+            time.sleep(0.01)
+    finally:
+        mf.mf_server_destroy(sv)
+    assert res["status"] == mf.MF_OK, res
+    assert res["rel_residual"] <= 1e-10, res
+    assert res["n_cellwise"] == 60**3 * 7**3
