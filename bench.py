@@ -412,18 +412,20 @@ def solve_compare(N=96, inner=(1e-3,), extra=True):
     autotune(mf, torch, op, b, s)
     autotune(mf, torch, op64, b, s)
     l2 = torch.zeros(1, dtype=torch.float64, device="cuda")
-    # (mixed, inner tolerance, preconditioner, Chebyshev interval ratio b / a)
-    runs = [(1, t, 0, 0.0) for t in inner] + [(0, 0.0, 0, 0.0)]
+    # (mixed, inner tolerance, preconditioner, Chebyshev interval ratio b / a, restarted inner CG)
+    runs = [(1, t, 0, 0.0, 0) for t in inner] + [(0, 0.0, 0, 0.0, 0)]
     if extra:
-        runs += [(1, inner[0], mf.MF_PRECOND_JACOBI, 0.0), (0, 0.0, mf.MF_PRECOND_JACOBI, 0.0)]
-        runs += [(0, 0.0, mf.MF_PRECOND_CHEBYSHEV, r) for r in (10.0, 30.0, 100.0)]
-    for mixed, itol, pre, ratio in runs:
+        runs += [(1, 0.0, 0, 0.0, 1)]
+        runs += [(1, 0.0, mf.MF_PRECOND_JACOBI, 0.0, 0), (0, 0.0, mf.MF_PRECOND_JACOBI, 0.0, 0)]
+        runs += [(0, 0.0, mf.MF_PRECOND_CHEBYSHEV, r, 0) for r in (10.0, 30.0, 100.0)]
+    for mixed, itol, pre, ratio, restart in runs:
         sop = op if mixed else op64
         cws = torch.empty(mf.mf_cg_workspace_bytes_ex(sop, mixed, pre), dtype=torch.uint8, device="cuda")
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         ev[0].record(stream)
         st = mf.mf_cg_solve(sop, b.data_ptr(), x.data_ptr(), 1e-10, 400000, mixed, cws.data_ptr(), cws.numel(), s,
-                            allow_not_converged=True, inner_rtol=itol, precond=pre, cheb_ratio=ratio)
+                            allow_not_converged=True, inner_rtol=itol, precond=pre, cheb_ratio=ratio,
+                            mixed_restart=restart)
         ev[1].record(stream)
         ev[1].synchronize()
         t = ev[0].elapsed_time(ev[1]) / 1e3
@@ -431,7 +433,8 @@ def solve_compare(N=96, inner=(1e-3,), extra=True):
         stream.synchronize()
         tag = {mf.MF_PRECOND_NONE: "", mf.MF_PRECOND_JACOBI: "_jacobi",
                mf.MF_PRECOND_CHEBYSHEV: f"_chebyshev{ratio:g}"}[pre]
-        out[(f"mixed_inner{itol:g}" if mixed else "fp64") + tag] = {
+        tag += "_restarted" if restart else ""
+        out[((f"mixed_inner{itol:g}" if itol else "mixed") if mixed else "fp64") + tag] = {
             "status": st["code"], "iterations": st["iterations"], "outer": st["outer_iterations"],
             "rel_residual": st["rel_residual"], "seconds": t,
             "applies": st["iterations"] * (3 if pre == mf.MF_PRECOND_CHEBYSHEV else 1),
@@ -441,7 +444,7 @@ def solve_compare(N=96, inner=(1e-3,), extra=True):
         torch.cuda.empty_cache()
     out["n_cellwise"], out["n_unique"] = info["n_cellwise"], info["n_unique"]
     best = min((v["seconds"], kk) for kk, v in out.items()
-               if kk.startswith("mixed_inner") and "jacobi" not in kk and "chebyshev" not in kk)
+               if kk.startswith("mixed") and "jacobi" not in kk and "restarted" not in kk)
     out["best_mixed"] = best[1]
     out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / best[0]
     mf.mf_operator_destroy(op)
@@ -457,7 +460,7 @@ def solve_run(args):
     print(json.dumps(solve_compare(args.solve_n, tuple(args.inner_rtol), True)), flush=True)
 
 
-def serve_stream(n, rate=0.0, single=False, no_batching=False, arena_gb=120):
+def serve_stream(n, rate=0.0, single=False, no_batching=False, arena_gb=120, mixed_restart=0):
     """Serving stream: n Poisson CG solve requests, mesh N^3 with N log-uniform in [4, 64],
     degree uniform in {2..6}, affine or curved 50/50, manufactured right-hand side, FP32 apply
     in FP64 refinement to 1e-10; seed 4.  Reports p50/p99 latency (submit -> result) and
@@ -473,7 +476,7 @@ def serve_stream(n, rate=0.0, single=False, no_batching=False, arena_gb=120):
     arena = torch.empty(int(arena_gb * 2**30), dtype=torch.uint8, device="cuda")
     # single: the baseline of the same stream, the plain FP64 solver one request at a time
     sv = mf.mf_server_create(arena.data_ptr(), arena.numel(), max_slots=1 if single else 64, autotune=1,
-                             batching=-1 if (no_batching or single) else 0)
+                             batching=-1 if (no_batching or single) else 0, mixed_restart=mixed_restart)
     reqs = [mf.make_request(int(N), int(N), int(N), int(k), geometry=mf.MF_CURVED_SIN if g else mf.MF_AFFINE,
                             rhs=mf.MF_RHS_MANUFACTURED, rtol=1e-10, maxit=400000, mixed=0 if single else 1)
             for N, k, g in zip(Ns, ks, geo)]
@@ -510,6 +513,10 @@ def serve_stream(n, rate=0.0, single=False, no_batching=False, arena_gb=120):
            "failed": [dict(N=int(Ns[i]), k=int(ks[i]), curved=int(geo[i]), status=int(rs[i]["status"]),
                            iterations=int(rs[i]["iterations"]), outer=int(rs[i]["outer_iterations"]),
                            rel=float(rs[i]["rel_residual"])) for i in range(n) if rs[i]["status"] != 0][:10],
+           "slowest": [dict(N=int(Ns[i]), k=int(ks[i]), curved=int(geo[i]), iterations=int(rs[i]["iterations"]),
+                            outer=int(rs[i]["outer_iterations"]), latency_s=round(float(lat[i]), 3))
+                       for i in np.argsort(-lat)[:5]],
+           "inner_cg": "restarted" if mixed_restart else "reliable updates",
            "batching": not (no_batching or single),
            "solver": "plain FP64 CG, one request at a time" if single else "mixed precision, 64 slots",
            "arena_peak_gb": st["arena_peak"] / 2**30, "slots": 1 if single else 64}
@@ -519,7 +526,8 @@ def serve_stream(n, rate=0.0, single=False, no_batching=False, arena_gb=120):
 
 
 def serve_run(args):
-    print(json.dumps(serve_stream(args.serve, args.rate, args.fp64_single, args.no_batching)), flush=True)
+    print(json.dumps(serve_stream(args.serve, args.rate, args.fp64_single, args.no_batching,
+                                  mixed_restart=int(args.mixed_restart))), flush=True)
 
 
 def main():
@@ -546,10 +554,13 @@ def main():
                     help="serving run: NREQ solve requests with Poisson arrivals (prints its own JSON line)")
     ap.add_argument("--rate", type=float, default=0.0, help="serving arrival rate (requests/s); 0 = measure capacity")
     ap.add_argument("--no-batching", action="store_true", help="serving: every request on its own graph chunks")
+    ap.add_argument("--mixed-restart", action="store_true",
+                    help="serving: restart the inner FP32 CG at every defect-correction step")
     ap.add_argument("--fp64-single", action="store_true",
                     help="serving baseline: the same stream through the plain FP64 solver, one request at a time")
     ap.add_argument("--solve-n", type=int, default=96, help="cells per axis of the --solve mesh")
-    ap.add_argument("--inner-rtol", type=float, nargs="+", default=[1e-3], help="inner FP32 CG tolerances to run")
+    ap.add_argument("--inner-rtol", type=float, nargs="+", default=[0.0],
+                    help="inner FP32 CG tolerances to run (0: the library default)")
     args = ap.parse_args()
     if args.profile_apply:
         profile_apply(args)
@@ -750,7 +761,7 @@ def main():
         try:
             with Clocks(local) as sclk:
                 sclk.mark_start()
-                solve = solve_compare(args.solve_n, (1e-3,), False)
+                solve = solve_compare(args.solve_n, (0.0,), False)
                 sclk.mark_end()
             solve["clocks"] = sclk.summary()
         except Exception as exc:

@@ -259,7 +259,12 @@ mf_status mf_dot_noalloc(const mf_operator* op, const void* a_dev, const void* b
  * significant bits, FP32-pipe arithmetic; b enters scaled by the power of two of max|b|, x
  * leaves scaled back), MF_FP64_DFMA keeps doubles.  mixed = 1
  * (operator MF_MIXED): FP64 defect correction -- outer residual r = b - A x, the update and
- * all dot products in FP64, inner CG with the FP32 apply.  Synchronous.  Workspace:
+ * all dot products in FP64, inner CG with the FP32 apply.  Without a preconditioner the inner
+ * CG is not restarted at a defect-correction step but continued with reliable updates (Clark
+ * et al. 2010): its residual is replaced by the FP64 one (scaled by 1/||b|| throughout), its
+ * search direction kept, p = r^ + beta p with beta = <r^, r^> / <r_k, r_k>, and its tolerance
+ * reset to inner_rtol ||r^||; mf_solve_options.mixed_restart = 1 restarts it from p = r^
+ * instead (the Jacobi-preconditioned solve always restarts).  Synchronous.  Workspace:
  * mf_cg_workspace_bytes(op, mixed) device bytes. */
 typedef struct {
   int32_t iterations;       /* total CG iterations (inner iterations for mixed) */
@@ -284,7 +289,8 @@ size_t mf_cg_solve_host_workspace_bytes(const mf_operator* op, int mixed);
 mf_status mf_cg_solve_host(const mf_operator* op, const void* b_host, void* x_host, double rtol, int maxit, int mixed,
                            mf_solve_stats* stats, void* workspace_dev, size_t bytes, void* stream);
 /* mf_cg_solve with options (0 fields keep the defaults): inner_rtol of the FP32 CG in
- * defect correction (default 1e-3), CG iterations per graph launch (default 20), cap on
+ * defect correction (default 0.1 with reliable updates -- Q4 curved 96^3: 1e-3 took 23770
+ * inner iterations, 0.1 2579 -- and 1e-3 restarted), CG iterations per graph launch (default 20), cap on
  * defect-correction steps (default 60), and the form of the CG iteration:
  *   MF_CG_SPLIT_DUAL (default) -- the Krylov loop on split data of Sec. 4: the apply leaves
  *     A p split (no duplicate summation) and forms <p, A p> -- the pairing of the consistent p
@@ -315,6 +321,8 @@ typedef struct {
   int32_t cg_form; /* MF_CG_* */
   int32_t precond; /* MF_PRECOND_* */
   double cheb_ratio; /* MF_PRECOND_CHEBYSHEV: b / a of the target interval (0: 30) */
+  int32_t mixed_restart; /* mixed, unpreconditioned: 0 reliable updates, 1 restarted inner CG */
+  int32_t reserved;      /* 0 */
 } mf_solve_options;
 /* Workspace of mf_cg_solve_ex with these options (opts may be NULL: mf_cg_workspace_bytes). */
 size_t mf_cg_workspace_bytes_ex(const mf_operator* op, int mixed, const mf_solve_options* opts);
@@ -361,9 +369,9 @@ typedef struct {
   int32_t queue_capacity;   /* pending requests before MF_ERR_BUSY (default 100000) */
   int32_t chunk_iterations; /* CG iterations per graph launch (default 20) */
   int32_t autotune;         /* 1: autotune the apply of each new operator class */
-  double inner_rtol;        /* mixed: inner FP32 CG tolerance (default 1e-3) */
+  double inner_rtol;        /* mixed: inner FP32 CG tolerance (default 0.1, reliable updates) */
   int32_t batching;         /* 0 / 1: continuous batches of CG iterations (default); -1: off */
-  int32_t reserved;
+  int32_t mixed_restart;    /* mixed: 0 reliable updates (default), 1 restarted inner CG */
 } mf_server_config;
 
 typedef struct {

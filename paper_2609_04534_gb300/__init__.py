@@ -50,13 +50,14 @@ class mf_solve_stats(C.Structure):
 
 class mf_solve_options(C.Structure):
     _fields_ = [("inner_rtol", C.c_double), ("chunk_iterations", C.c_int32), ("max_outer", C.c_int32),
-                ("cg_form", C.c_int32), ("precond", C.c_int32), ("cheb_ratio", C.c_double)]
+                ("cg_form", C.c_int32), ("precond", C.c_int32), ("cheb_ratio", C.c_double),
+                ("mixed_restart", C.c_int32), ("reserved", C.c_int32)]
 
 
 class mf_server_config(C.Structure):
     _fields_ = [("max_slots", C.c_int32), ("queue_capacity", C.c_int32), ("chunk_iterations", C.c_int32),
                 ("autotune", C.c_int32), ("inner_rtol", C.c_double), ("batching", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("mixed_restart", C.c_int32)]
 
 
 class mf_request(C.Structure):
@@ -296,16 +297,16 @@ def mf_cg_workspace_bytes(op, mixed: int = 0) -> int:
 
 
 def mf_cg_workspace_bytes_ex(op, mixed: int = 0, precond: int = 0) -> int:
-    opts = mf_solve_options(0.0, 0, 0, 0, precond, 0.0)
+    opts = mf_solve_options(0.0, 0, 0, 0, precond, 0.0, 0, 0)
     return int(lib().mf_cg_workspace_bytes_ex(op, mixed, C.byref(opts)))
 
 
 def mf_cg_solve(op, b_ptr: int, x_ptr: int, rtol: float, maxit: int, mixed: int, workspace_ptr: int,
                 nbytes: int, stream: int = 0, allow_not_converged: bool = False, inner_rtol: float = 0.0,
                 chunk_iterations: int = 0, max_outer: int = 0, cg_form: int = 0, precond: int = 0,
-                cheb_ratio: float = 0.0) -> dict:
+                cheb_ratio: float = 0.0, mixed_restart: int = 0) -> dict:
     st = mf_solve_stats()
-    opts = mf_solve_options(inner_rtol, chunk_iterations, max_outer, cg_form, precond, cheb_ratio)
+    opts = mf_solve_options(inner_rtol, chunk_iterations, max_outer, cg_form, precond, cheb_ratio, mixed_restart, 0)
     code = lib().mf_cg_solve_ex(op, b_ptr, x_ptr, rtol, maxit, mixed, C.byref(opts), C.byref(st), workspace_ptr,
                                 nbytes, stream or None)
     if not (code == MF_OK or (allow_not_converged and code == MF_ERR_NOT_CONVERGED)):
@@ -362,8 +363,9 @@ def mf_cg_record_history(hist_ptr: int | None, cap: int) -> None:
 
 # ---------------------------------------------------------------- serving
 def mf_server_create(arena_ptr: int, arena_bytes: int, max_slots: int = 32, queue_capacity: int = 0,
-                     chunk_iterations: int = 20, autotune: int = 0, inner_rtol: float = 1e-3, batching: int = 0):
-    cfg = mf_server_config(max_slots, queue_capacity, chunk_iterations, autotune, inner_rtol, batching, 0)
+                     chunk_iterations: int = 20, autotune: int = 0, inner_rtol: float = 0.0, batching: int = 0,
+                     mixed_restart: int = 0):
+    cfg = mf_server_config(max_slots, queue_capacity, chunk_iterations, autotune, inner_rtol, batching, mixed_restart)
     h = C.c_void_p()
     _check(lib().mf_server_create(C.byref(cfg), arena_ptr, arena_bytes, C.byref(h)))
     return h.value

@@ -205,9 +205,7 @@ __global__ void __launch_bounds__(RED_THREADS) cg_xr_kernel(T* __restrict__ x, T
       if (tot <= st->tol2) st->flag = 1;
       else if (!isfinite(tot)) st->flag = 2;
       else if (st->it >= st->maxit) st->flag = 3;
-    } else {
-      st->beta = 0.0;
-    }
+    } // stopped: beta stays that of the last step (a reliable update continues from it)
   }
 }
 
@@ -230,7 +228,9 @@ template <typename T>
 __device__ __forceinline__ void cg_p_body(const T* __restrict__ r, T* __restrict__ p, const float* __restrict__ dinv,
                                           long long n, const CgState* st, long long cta, long long ncta) {
   const T be = scalar_from_double<T>(st->beta);
-  if (st->flag != 0 && st->flag != 1) return;
+  // stopped (converged, broken down or at maxit): the direction stays the last one applied,
+  // which a reliable update of the mixed solver continues from
+  if (st->flag != 0) return;
   const long long nq = n / 4;
   const Quad<T>* __restrict__ rq = reinterpret_cast<const Quad<T>*>(r);
   Quad<T>* __restrict__ pq = reinterpret_cast<Quad<T>*>(p);
@@ -476,6 +476,28 @@ __global__ void sub_kernel(const double* __restrict__ b, const double* __restric
 __global__ void to32_kernel(const double* __restrict__ r, float* __restrict__ o, const double* rn2, long long n) {
   const double sc = (*rn2 > 0.0) ? 1.0 / sqrt(*rn2) : 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) o[e] = (float)(r[e] * sc);
+}
+// Reliable update of the mixed solver's inner CG (its residual r_k+1 replaced by the FP64
+// one, r^): beta = <r^, r^> / <r_k, r_k> = beta_k <r^, r^> / <r_k+1, r_k+1> (Clark et al.'s
+// reliable-update CG), the state restarted on <r^, r^>.  When the recursive residual has
+// drifted from the true one by more than RELIABLE_DRIFT ||r^||, the kept direction carries
+// little information and the CG restarts from p = r^ (beta = 0) instead.
+constexpr double RELIABLE_DRIFT = 0.1;
+__global__ void reliable_state_kernel(CgState* st, const double* rr_new, const double* cross, double inner_rtol,
+                                      int maxit) {
+  const double rr = *rr_new;
+  CgState h = *st;
+  const double drift2 = rr - 2.0 * *cross + h.rr; // ||r^ - r_k+1||^2
+  const bool keep = h.rz > 0.0 && isfinite(h.rz) && drift2 <= RELIABLE_DRIFT * RELIABLE_DRIFT * rr;
+  h.beta = keep ? h.beta * rr / h.rz : 0.0;
+  h.rr = h.rz = rr;
+  h.bnorm = sqrt(rr);
+  h.tol2 = inner_rtol * inner_rtol * rr;
+  h.pq = h.alpha = 0.0;
+  h.it = 0;
+  h.maxit = maxit;
+  h.flag = !isfinite(rr) ? 2 : ((rr == 0.0) ? 1 : (maxit <= 0 ? 3 : 0));
+  *st = h;
 }
 // x += sqrt(rn2) * d
 __global__ void axpy64_kernel(double* __restrict__ x, const float* __restrict__ d, const double* rn2, long long n) {
@@ -880,6 +902,8 @@ mf_status engine_start(SolverEngine* e) {
   // could not keep up with HBM even for the vector updates).  b is scaled by a power of two
   // near 1/||b|| on entry and x converted back on exit.
   e->w.dinv_active = nullptr;
+  if (e->precond != MF_PRECOND_NONE) e->reliable = false; // Jacobi: restarted inner CG
+  if (!(e->inner_rtol > 0.0)) e->inner_rtol = e->reliable ? 0.1 : 1e-3;
   if (e->precond == MF_PRECOND_JACOBI) {
     if ((st = launch_diagonal(e->op, e->w.dinv, e->w.dtab, e->s))) return st;
     invert_diag_kernel<<<ew_blocks(n), 256, 0, e->s>>>(e->w.dinv, n);
@@ -943,7 +967,9 @@ mf_status engine_advance(SolverEngine* e) {
       return eng_finish(e, h.flag == 3 ? MF_ERR_NOT_CONVERGED : MF_OK);
     }
     if (h.flag == 2) return eng_finish(e, set_error(MF_ERR_BREAKDOWN, "inner CG breakdown at iteration %d", h.it));
-    axpy64_kernel<<<ew_blocks(n), 256, 0, e->s>>>((double*)e->x, (const float*)e->w.d32, e->w.scal + 2, n);
+    // the inner unknowns are scaled by 1/||b|| (reliable updates) or 1/||r|| of the step
+    axpy64_kernel<<<ew_blocks(n), 256, 0, e->s>>>((double*)e->x, (const float*)e->w.d32,
+                                                  e->w.scal + (e->reliable ? 1 : 2), n);
     e->outer += 1;
     return eng_outer_residual(e, false);
   }
@@ -956,9 +982,29 @@ mf_status engine_advance(SolverEngine* e) {
     if (e->rel <= e->rtol || e->bn == 0.0) return eng_finish(e, MF_OK);
     if (e->cancel) return eng_finish(e, MF_ERR_BUSY);
     if (e->outer >= e->max_outer || e->total_it >= e->maxit) return eng_finish(e, MF_ERR_NOT_CONVERGED);
-    to32_kernel<<<ew_blocks(n), 256, 0, e->s>>>((const double*)e->w.r64, (float*)e->w.q, e->w.scal + 2, n);
+    to32_kernel<<<ew_blocks(n), 256, 0, e->s>>>((const double*)e->w.r64, (float*)e->w.q,
+                                                e->w.scal + (e->reliable ? 1 : 2), n);
     if ((st = cuda_check(cudaGetLastError(), "to32"))) return st;
-    return eng_inner_start(e, e->w.q, e->w.d32, e->inner_rtol, e->maxit - e->total_it);
+    if (!e->reliable || e->outer == 0)
+      return eng_inner_start(e, e->w.q, e->w.d32, e->inner_rtol, e->maxit - e->total_it);
+    // reliable update: <r^, r^> and <r^, r_k+1> (the drift test), then r = r^, p = r + beta p,
+    // d = 0, inner state restarted
+    if ((st = dot_launch(e->op, 4, e->w.q, e->w.q, 0, e->w.scal, e->w.sc3, e->s))) return st;
+    if ((st = dot_launch(e->op, 4, e->w.q, e->w.r, 0, e->w.scal + 6, e->w.sc3, e->s))) return st;
+    copy_kernel<float><<<ew_blocks(n), 256, 0, e->s>>>((const float*)e->w.q, (float*)e->w.r, n);
+    zero_kernel<float><<<ew_blocks(n), 256, 0, e->s>>>((float*)e->w.d32, n);
+    if ((st = cuda_check(cudaGetLastError(), "reliable update"))) return st;
+    reliable_state_kernel<<<1, 1, 0, e->s>>>(e->w.st, e->w.scal, e->w.scal + 6, e->inner_rtol,
+                                             e->maxit - e->total_it);
+    if ((st = cuda_check(cudaGetLastError(), "reliable state"))) return st;
+    if (e->form == MF_CG_SPLIT_DUAL_FUSED) {
+      // the fused apply forms p = r + beta p at its load
+    } else if ((st = launch_cg_p(e->op, 4, e->w.r, e->w.p, nullptr, e->w.st, e->s))) {
+      return st;
+    }
+    e->phase = PH_INNER;
+    return cuda_check(cudaMemcpyAsync(&e->hm->st, e->w.st, sizeof(CgState), cudaMemcpyDeviceToHost, e->s),
+                      "state D2H");
   }
   return set_error(MF_ERR_ARG, "solver engine: advance before start");
 }
@@ -1175,6 +1221,7 @@ mf_status mf_cg_solve_ex(const mf_operator* op, const void* b_dev, void* x_dev, 
                opts->chunk_iterations < 0 || opts->max_outer < 0 || opts->cg_form < 0 ||
                opts->cg_form > MF_CG_SPLIT_DUAL_FUSED || opts->precond < 0 || opts->precond > MF_PRECOND_CHEBYSHEV ||
                (opts->precond == MF_PRECOND_JACOBI && opts->cg_form > MF_CG_SPLIT_DUAL) ||
+               opts->mixed_restart < 0 || opts->mixed_restart > 1 || opts->reserved != 0 ||
                (opts->precond == MF_PRECOND_CHEBYSHEV && (mixed || opts->cheb_ratio < 0.0 ||
                                                          (opts->cheb_ratio != 0.0 && !(opts->cheb_ratio > 1.0))))))
     return set_error(MF_ERR_ARG, "mf_cg_solve_ex: bad options");
@@ -1222,6 +1269,7 @@ mf_status mf_cg_solve_ex(const mf_operator* op, const void* b_dev, void* x_dev, 
     if (opts->max_outer > 0) e.max_outer = opts->max_outer;
     if (opts->cg_form != MF_CG_DEFAULT) e.form = opts->cg_form;
     e.precond = opts->precond;
+    e.reliable = opts->mixed_restart == 0;
   }
   e.record = g_hist_host != nullptr;
   mf_status st = engine_start(&e);

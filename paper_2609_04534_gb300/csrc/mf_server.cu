@@ -231,6 +231,7 @@ mf_status job_start(mf_server* sv, Job* j, Slot& sl, HostMirror* hm) {
   engine_init(&j->eng, j->op, j->req.mixed ? 1 : 0, j->b, j->x, j->req.rtol, j->req.maxit, j->cgws, s, hm);
   if (sv->cfg.chunk_iterations > 0) j->eng.chunk = sv->cfg.chunk_iterations;
   if (sv->cfg.inner_rtol > 0) j->eng.inner_rtol = sv->cfg.inner_rtol;
+  j->eng.reliable = sv->cfg.mixed_restart == 0;
   // Inner iterations come from the class batches for requests whose apply is a few waves of
   // CTAs at most: those are launch- and latency-bound alone, and batched with others they
   // share launches.  A larger request fills the GPU by itself and runs its own graph chunks
@@ -594,6 +595,8 @@ mf_status mf_server_create(const mf_server_config* cfg, void* arena_dev, size_t 
   *out = nullptr;
   if (!arena_dev || arena_bytes < 4096) return set_error(MF_ERR_ARG, "mf_server_create: arena missing or too small");
   if (reinterpret_cast<uintptr_t>(arena_dev) & 255) return set_error(MF_ERR_ARG, "mf_server_create: arena alignment");
+  if (cfg && (cfg->mixed_restart < 0 || cfg->mixed_restart > 1 || cfg->inner_rtol < 0.0 || cfg->inner_rtol >= 1.0))
+    return set_error(MF_ERR_ARG, "mf_server_create: bad mixed_restart or inner_rtol");
   mf_server* sv = new (std::nothrow) mf_server;
   if (!sv) return set_error(MF_ERR_OOM, "mf_server_create: host allocation failed");
   if (cfg) sv->cfg = *cfg;

@@ -41,11 +41,17 @@ struct SolverEngine {
   const void* b = nullptr;
   void* x = nullptr;
   void* x_in = nullptr;
-  double rtol = 0.0, inner_rtol = 1e-3;
+  // inner_rtol 0: 0.1 with reliable updates (a residual replacement every decade, the
+  // replacement interval of Clark et al.), 1e-3 for the restarted inner CG
+  double rtol = 0.0, inner_rtol = 0.0;
   int maxit = 0, chunk = 20, max_outer = 60;
   int form = MF_CG_SPLIT_DUAL; // MF_CG_SPLIT_DUAL, MF_CG_ASSEMBLED or MF_CG_SPLIT_DUAL_FUSED
   int vt = 8;                  // element type of the CG vectors (8, 4 or ELEM_DD), set at start
   int precond = MF_PRECOND_NONE;
+  // mixed: continue the inner CG across defect-correction steps (reliable updates: the FP32
+  // residual replaced by the FP64 one, the search direction kept) instead of restarting it;
+  // the inner vectors then stay scaled by 1/||b|| for the whole solve
+  bool reliable = true;
   HostMirror* hm = nullptr;
   int phase = 0, total_it = 0, outer = 0;
   double bn = 0.0, rel = 0.0;

@@ -12,7 +12,7 @@ from tests._gpu import DevOp, oracle_op, rel_max
 pytestmark = pytest.mark.gpu
 
 
-def solve(d, b, rtol, maxit, mixed, hist_cap=0, cg_form=0):
+def solve(d, b, rtol, maxit, mixed, hist_cap=0, cg_form=0, mixed_restart=0):
     x = torch.zeros(d.n_native, dtype=d.dtype, device="cuda")
     ws = torch.empty(mf.mf_cg_workspace_bytes(d.op, mixed), dtype=torch.uint8, device="cuda")
     hist = np.zeros(max(hist_cap, 1))
@@ -20,7 +20,7 @@ def solve(d, b, rtol, maxit, mixed, hist_cap=0, cg_form=0):
         mf.mf_cg_record_history(hist.ctypes.data, hist_cap)
     try:
         st = mf.mf_cg_solve(d.op, b.data_ptr(), x.data_ptr(), rtol, maxit, mixed, ws.data_ptr(), ws.numel(),
-                            allow_not_converged=True, cg_form=cg_form)
+                            allow_not_converged=True, cg_form=cg_form, mixed_restart=mixed_restart)
     finally:
         mf.mf_cg_record_history(None, 0)
     return x, st, hist
@@ -61,16 +61,21 @@ def test_fp64_cg_converges_to_oracle_solution(oracle, geom, k):
     d.close()
 
 
-@pytest.mark.parametrize("geom,kind", [("curved", mf.MF_LAPLACE), ("shear", mf.MF_HELMHOLTZ)])
-def test_mixed_precision_defect_correction(oracle, geom, kind):
-    """FP32 inner CG inside FP64 defect correction reaches the FP64 tolerance 1e-10 (true
-    residual checked by the oracle) and matches the FP64 solve."""
+@pytest.mark.parametrize("geom,kind,cg_form,restart", [
+    ("curved", mf.MF_LAPLACE, 0, 0), ("shear", mf.MF_HELMHOLTZ, 0, 0), ("curved", mf.MF_LAPLACE, 0, 1),
+    ("shear", mf.MF_HELMHOLTZ, 0, 1), ("curved", mf.MF_LAPLACE, mf.MF_CG_ASSEMBLED, 0),
+    ("shear", mf.MF_LAPLACE, mf.MF_CG_SPLIT_DUAL_FUSED, 0)])
+def test_mixed_precision_defect_correction(oracle, geom, kind, cg_form, restart):
+    """FP32 inner CG inside FP64 defect correction -- continued with reliable updates
+    (restart = 0) or restarted at every defect-correction step -- reaches the FP64 tolerance
+    1e-10 (true residual checked by the oracle) and matches the FP64 solve, for every form of
+    the inner iteration."""
     N, k = 6, 3
     d = DevOp(N, N, N, k, geom, kind, 1.0, mf.MF_MIXED, 1)
     o = oracle_op(oracle, N, N, N, k, geom, 1.0 if kind == mf.MF_HELMHOLTZ else 0.0, 1)
     bu = inputs.random_unique(N, N, N, k, 9)
     b = d.native_from_unique(bu)
-    x, st, _ = solve(d, b, 1e-10, 20000, 1)
+    x, st, _ = solve(d, b, 1e-10, 20000, 1, cg_form=cg_form, mixed_restart=restart)
     assert st["code"] == mf.MF_OK, st
     assert st["outer_iterations"] >= 2
     xg = d.unique_from_native(x)
@@ -80,6 +85,29 @@ def test_mixed_precision_defect_correction(oracle, geom, kind):
     x64, st64, _ = solve(d, b, 1e-10, 20000, 0)
     assert st64["code"] == mf.MF_OK
     assert rel_max(xg, d.unique_from_native(x64)) <= 1e-7
+    d.close()
+
+
+@pytest.mark.parametrize("geom,k", [("curved", 4), ("cart", 2)])
+def test_reliable_updates_keep_the_krylov_space(oracle, geom, k):
+    """With reliable updates the inner CG continues across defect-correction steps: on a
+    problem that needs several outer steps it takes fewer inner iterations in total than the
+    restarted inner CG, and both reach 1e-10 with the true residual checked by the oracle."""
+    N = 10
+    d = DevOp(N, N, N, k, geom, mf.MF_LAPLACE, 1.0, mf.MF_MIXED, 1)
+    o = oracle_op(oracle, N, N, N, k, geom, 0.0, 1)
+    bu = inputs.random_unique(N, N, N, k, 4)
+    b = d.native_from_unique(bu)
+    bm = np.where(o.boundary_mask(), 0.0, bu)
+    its = {}
+    for restart in (0, 1):
+        x, st, _ = solve(d, b, 1e-10, 20000, 1, mixed_restart=restart)
+        assert st["code"] == mf.MF_OK, st
+        res = np.linalg.norm(bm - o.apply(d.unique_from_native(x))) / np.linalg.norm(bm)
+        assert res <= 2e-10, (restart, res)
+        its[restart] = (st["iterations"], st["outer_iterations"])
+    assert its[1][1] >= 3, its
+    assert its[0][0] < its[1][0], its
     d.close()
 
 
@@ -213,13 +241,14 @@ def test_diagonal_matches_assembled_matrix(oracle, dims, k, geom, kind, bc):
 def test_jacobi_pcg_converges_with_fewer_iterations(oracle, geom, k, prec, mixed):
     """Jacobi-preconditioned CG (split-dual) reaches 1e-10 (true residual checked by the oracle)
     in fewer iterations than plain CG, on meshes where the diagonal varies (stretched cells,
-    curved map, high degree)."""
+    curved map, high degree).  The mixed solve compares like with like: the preconditioned
+    inner CG is restarted at every defect-correction step, so the plain one is too."""
     N = 6
     d = DevOp(N, N + 1, N - 1, k, geom, mf.MF_LAPLACE, 1.0, prec, 1)
     o = oracle_op(oracle, N, N + 1, N - 1, k, geom, 0.0, 1)
     bu = inputs.random_unique(N, N + 1, N - 1, k, 17)
     b = d.native_from_unique(bu)
-    x0, st0, _ = solve(d, b, 1e-10, 20000, mixed)
+    x0, st0, _ = solve(d, b, 1e-10, 20000, mixed, mixed_restart=mixed)
     x1 = torch.zeros(d.n_native, dtype=d.dtype, device="cuda")
     ws = torch.empty(mf.mf_cg_workspace_bytes(d.op, mixed), dtype=torch.uint8, device="cuda")
     st1 = mf.mf_cg_solve(d.op, b.data_ptr(), x1.data_ptr(), 1e-10, 20000, mixed, ws.data_ptr(), ws.numel(),

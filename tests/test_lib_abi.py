@@ -167,3 +167,22 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(mf, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         mf.lib()
+
+
+def test_mixed_restart_option_validation(L):
+    """The mixed solver's restart switch and the server's copy of it accept 0 or 1 only; the
+    checks run before any device call."""
+    mesh = mf.mf_mesh_create(4, 4, 4)
+    op = mf.mf_operator_create(mesh, 2)
+    for bad in (-1, 2):
+        with pytest.raises(mf.MfError) as e:
+            mf.mf_cg_solve(op, 256, 512, 1e-8, 10, 1, 256, 1 << 20, mixed_restart=bad)
+        assert e.value.code == mf.MF_ERR_ARG and "bad options" in str(e.value)
+        with pytest.raises(mf.MfError) as e:
+            mf.mf_server_create(256, 1 << 20, mixed_restart=bad)
+        assert e.value.code == mf.MF_ERR_ARG and "mixed_restart" in str(e.value)
+    with pytest.raises(mf.MfError) as e:
+        mf.mf_server_create(256, 1 << 20, inner_rtol=1.5)
+    assert e.value.code == mf.MF_ERR_ARG
+    mf.mf_operator_destroy(op)
+    mf.mf_mesh_destroy(mesh)
