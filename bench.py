@@ -296,7 +296,8 @@ def profile_apply(args):
         x = random_native(mf, torch, op, info, N, k, 1, dt, s)
         y = torch.empty_like(x)
     tensor = mf.mf_operator_get_variant(op) == mf.MF_VARIANT_TENSOR
-    for v in ([args.variant] if args.variant >= 0 else [0, 1, 2] + ([mf.MF_VARIANT_TENSOR] if tensor else [])):
+    small = [mf.MF_VARIANT_SMALL_CTA] if p == mf.MF_FP64 else []
+    for v in ([args.variant] if args.variant >= 0 else [0, 1, 2] + small + ([mf.MF_VARIANT_TENSOR] if tensor else [])):
         mf.mf_operator_set_variant(op, v)
         t = time_apply(mf, torch, op, x, y, stream, args.reps, 1)
         ta, td = time_kernels(mf, torch, op, x, y, stream, args.reps)
@@ -382,6 +383,70 @@ def dss_ablation(args):
         mf.mf_operator_destroy(op)
         mf.mf_mesh_destroy(mesh)
         del ws, x, y, sc
+        torch.cuda.empty_cache()
+
+
+def block_sweep(args):
+    """Sec. 6 block-size sweep: the degree-3 split apply (no duplicate summation) with B = 4, 8,
+    16, 32 cells per CTA, the resident threads per SM held at launch variant 0's, Laplace on
+    N^3 cells (128^3: 134 M cell-wise DoFs, the paper's size), Cartesian and curved, FP64
+    (double-float) and FP32; then the Cartesian Helmholtz FP64 apply of the ~50 M DoF degree
+    sweep at k = 1..8.  Beside it: launch variants 0-2 and the operator's default (the
+    tensor-core apply for Cartesian FP64 at k = 2, 3)."""
+    import torch
+
+    import paper_2609_04534_gb300 as mf
+
+    stream = torch.cuda.Stream()
+    s = stream.cuda_stream
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    N, k = args.block_n, 3
+    pk = peaks()["hbm_gbs"]
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        stream.synchronize()
+        ev[0].record(stream)
+        for _ in range(args.reps):
+            fn()
+        ev[1].record(stream)
+        ev[1].synchronize()
+        return ev[0].elapsed_time(ev[1]) / 1e3 / args.reps
+
+    # degree 3 on N^3 (every path and precision), then the Cartesian Helmholtz FP64 apply of
+    # the ~50 M DoF degree sweep at every degree
+    cases = [(N, 3, geom, prec, mf.MF_LAPLACE) for geom, prec in
+             (("cart", "fp64"), ("curved", "fp64"), ("cart", "fp32"), ("curved", "fp32"))]
+    if not args.no_sweep:
+        cases += [(nn, kk, "cart", "fp64", mf.MF_HELMHOLTZ) for kk, nn in SWEEP_N.items()]
+    for N, k, geom, prec, kind in cases:
+        g = mf.MF_CURVED_SIN if geom == "curved" else mf.MF_AFFINE
+        p = {"fp64": mf.MF_FP64, "fp32": mf.MF_FP32}[prec]
+        dt = torch.float64 if p == mf.MF_FP64 else torch.float32
+        mesh, op, info, ws = make_op(mf, torch, N, k, g, kind, p, 0, s)
+        with torch.cuda.stream(stream):
+            x = random_native(mf, torch, op, info, N, k, 1, dt, s)
+            y = torch.empty_like(x)
+        ab = info["algorithmic_bytes_per_apply"]
+        out = {"case": f"Q{k} {'Helmholtz' if kind == mf.MF_HELMHOLTZ else 'Laplace'} {geom} {N}^3 {prec}",
+               "n_cellwise": info["n_cellwise"], "algorithmic_bytes": ab}
+
+        def rec(t):
+            return {"ms": round(t * 1e3, 4), "gdofs": round(info["n_cellwise"] / t / 1e9, 3),
+                    "hbm_frac": round(ab / t / 1e9 / pk, 4)}
+        default = mf.mf_operator_get_variant(op)
+        for b in (4, 8, 16, 32):
+            if 32 <= (k + 1) ** 2 * b <= 1024:
+                out[f"B{b}"] = rec(timed(lambda: mf.mf_apply_split_block(op, b, x.data_ptr(), y.data_ptr(), s)))
+        for v in sorted({0, 1, 2, default} | ({mf.MF_VARIANT_SMALL_CTA} if p == mf.MF_FP64 else set())):
+            mf.mf_operator_set_variant(op, v)
+            out[f"variant{v}"] = rec(timed(lambda: mf.mf_apply_split(op, x.data_ptr(), y.data_ptr(), s)))
+        out["default_variant"] = default
+        print(json.dumps(out), flush=True)
+        mf.mf_operator_destroy(op)
+        mf.mf_mesh_destroy(mesh)
+        del ws, x, y
         torch.cuda.empty_cache()
 
 
@@ -548,6 +613,9 @@ def main():
                     help="only run --reps CG iterations of one case (for ncu), e.g. 48,4,curved,fp64")
     ap.add_argument("--dss-ablation", action="store_true",
                     help="only time the sweep vs atomic duplicate summation and the apply's launch variants")
+    ap.add_argument("--block-sweep", action="store_true",
+                    help="Sec. 6 block-size sweep of the degree-3 apply (B = 4..32 cells per CTA)")
+    ap.add_argument("--block-n", type=int, default=128, help="cells per axis of the --block-sweep mesh")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--variant", type=int, default=-1, help="--profile-apply: launch variant (-1: all)")
     ap.add_argument("--serve", type=int, default=0, metavar="NREQ",
@@ -570,6 +638,9 @@ def main():
         return
     if args.dss_ablation:
         dss_ablation(args)
+        return
+    if args.block_sweep:
+        block_sweep(args)
         return
     if args.solve:
         solve_run(args)

@@ -111,13 +111,16 @@ mf_status mf_operator_setup(mf_operator* op, void* workspace_dev, size_t bytes, 
  * threads per CTA, registers capped for two CTAs per SM; variant 1: half the cells per CTA,
  * capped for three; variant 2: half the cells per CTA, no register cap; variant 3, for
  * MF_FP64 operators on an axis-aligned affine mesh of degree 1..3 only: the tensor-core
- * apply, see MF_VARIANT_TENSOR) with `reps` applies of x_dev into y_dev (both native vectors
+ * apply, see MF_VARIANT_TENSOR; variant 4, for MF_FP64 (double-float) operators only: half
+ * the cells per CTA with variant 0's resident threads per SM, see MF_VARIANT_SMALL_CTA) with
+ * `reps` applies of x_dev into y_dev (both native vectors
  * of this operator; y is overwritten) and keeps the fastest.  The choice is cached per
- * (device, degree, path, kind, precision) for the life of the process, so later operators of
+ * (device, degree, path, kind, precision, size class = floor(log2(cells))) for the life of
+ * the process, so later operators of
  * the same class reuse it without timing, and persisted across processes in a JSON file keyed
  * by the GPU's name (MF_AUTOTUNE_CACHE, else $XDG_CACHE_HOME/libmf/autotune.json or
  * $HOME/.cache/libmf/autotune.json; MF_AUTOTUNE_CACHE=off disables the file): a stored choice
- * is used without timing.  Synchronises `stream` when it times.  Variants 0-2 run the same
+ * is used without timing.  Synchronises `stream` when it times.  Variants 0-2 and 4 run the same
  * per-thread arithmetic and give bitwise equal results; variant 3 rounds differently (same
  * accuracy class), so its results agree with theirs within 1e-12 relative max-norm. */
 mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, int reps, void* stream);
@@ -133,9 +136,14 @@ mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, 
  * per value.  A non-finite input value makes its cell's outputs NaN.  Needs
  * mf_operator_setup (the digit table lives in the operator workspace, at most 48 KB). */
 #define MF_VARIANT_TENSOR 3
-/* Forces a launch variant (0, 1 or 2) for every precision view, or MF_VARIANT_TENSOR for
- * the FP64 view (MF_ERR_UNSUPPORTED for an operator it does not cover); MF_ERR_ARG for any
- * other value. */
+/* Half the cells per CTA of variant 0, with registers capped so that the resident threads
+ * per SM stay variant 0's: the block size alone changes (the B axis of the paper's
+ * block-size experiment, Sec. 6; see mf_apply_split_block).  Double-float view of MF_FP64
+ * operators; same per-thread arithmetic as variants 0-2 (bitwise equal results). */
+#define MF_VARIANT_SMALL_CTA 4
+/* Forces a launch variant (0, 1 or 2) for every precision view, or MF_VARIANT_TENSOR /
+ * MF_VARIANT_SMALL_CTA for the double-float view of an MF_FP64 operator (MF_ERR_UNSUPPORTED
+ * for an operator they do not cover); MF_ERR_ARG for any other value. */
 mf_status mf_operator_set_variant(mf_operator* op, int variant);
 /* Variant in use for the operator's main precision view (-1 for a NULL operator). */
 int mf_operator_get_variant(const mf_operator* op);
@@ -185,6 +193,19 @@ mf_status mf_make_consistent(const mf_operator* op, void* y_dev, void* stream);
  * precision as the operator's vectors; P y for Dirichlet. */
 size_t mf_dss_atomic_workspace_bytes(const mf_operator* op);
 mf_status mf_dss_atomic(const mf_operator* op, void* y_dev, void* scratch_dev, size_t scratch_bytes, void* stream);
+/* Block-size sweep (a measurement entry: the paper sweeps the cells per thread block B of
+ * its volume kernel, Sec. 6): mf_apply_split with cells_per_cta = B in {4, 8, 16, 32} cells
+ * per CTA -- divisors of the 32-cell layout tile -- instead of the launch variant's.
+ * Registers are capped so that every B keeps launch variant 0's resident threads per SM.
+ * Same result as mf_apply_split with launch variant 0 (the arithmetic of a cell does not
+ * depend on B), no duplicate summation.  Built for degree 3 on every path with MF_FP64
+ * (double-float) and MF_FP32 operators, and for the Cartesian path of MF_FP64 operators at
+ * every degree; n^2 B threads must lie in 32..1024.  x_dev, y_dev: device, n_native elements
+ * of the operator's vector precision, caller-owned, distinct.  Errors: MF_ERR_ARG (NULL
+ * operator or vectors, B not one of the four, operator not ready), MF_ERR_UNSUPPORTED (a
+ * combination not built; MF_FP64_DFMA and MF_MIXED, whose double vectors take the native
+ * FP64 apply), MF_ERR_CUDA. */
+mf_status mf_apply_split_block(const mf_operator* op, int cells_per_cta, const void* x_dev, void* y_dev, void* stream);
 /* Stream twin of the apply kernel (a measurement entry: the paper times kernels that keep a
  * kernel's memory accesses and drop its arithmetic, Sec. 6, as the ceiling of its access
  * pattern).  One launch with the apply's grid and cells per CTA (the operator's launch

@@ -24,6 +24,7 @@ MF_BC_NONE, MF_BC_DIRICHLET0 = 0, 1
 MF_CG_DEFAULT, MF_CG_SPLIT_DUAL, MF_CG_ASSEMBLED, MF_CG_SPLIT_DUAL_FUSED = 0, 1, 2, 3
 MF_PRECOND_NONE, MF_PRECOND_JACOBI, MF_PRECOND_CHEBYSHEV = 0, 1, 2
 MF_VARIANT_TENSOR = 3
+MF_VARIANT_SMALL_CTA = 4
 
 _STATUS = {0: "MF_OK", -1: "MF_ERR_ARG", -2: "MF_ERR_OOM", -3: "MF_ERR_CUDA", -4: "MF_ERR_NOT_CONVERGED",
            -5: "MF_ERR_BREAKDOWN", -6: "MF_ERR_TIMEOUT", -7: "MF_ERR_BUSY", -8: "MF_ERR_UNSUPPORTED",
@@ -105,6 +106,7 @@ def lib() -> C.CDLL:
                "mf_apply_split", "mf_apply_stream_twin"):
         getattr(L, nm).argtypes = [vp, vp, vp, vp]
     L.mf_dss.argtypes = [vp, vp, vp]
+    L.mf_apply_split_block.argtypes = [vp, i32, vp, vp, vp]
     L.mf_make_consistent.argtypes = [vp, vp, vp]
     L.mf_apply_host_workspace_bytes.argtypes = [vp]
     L.mf_apply_host_workspace_bytes.restype = sz
@@ -251,6 +253,11 @@ def mf_apply_split(op, x_ptr: int, y_ptr: int, stream: int = 0) -> None:
 def mf_apply_stream_twin(op, x_ptr: int, y_ptr: int, stream: int = 0) -> None:
     """The apply kernel's memory accesses without its arithmetic; y receives a copy of x."""
     _check(lib().mf_apply_stream_twin(op, x_ptr, y_ptr, stream or None))
+
+
+def mf_apply_split_block(op, cells_per_cta: int, x_ptr: int, y_ptr: int, stream: int = 0) -> None:
+    """mf_apply_split of a degree-3 operator with B = cells_per_cta cells per CTA (4, 8, 16, 32)."""
+    _check(lib().mf_apply_split_block(op, cells_per_cta, x_ptr, y_ptr, stream or None))
 
 
 def mf_dss(op, y_ptr: int, stream: int = 0) -> None:

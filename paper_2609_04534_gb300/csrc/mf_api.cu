@@ -292,6 +292,18 @@ mf_status mf_apply_split(const mf_operator* op, const void* x_dev, void* y_dev, 
   return launch_apply_split(op, view_of_elem(op, elem_of(op)), x_dev, y_dev, static_cast<cudaStream_t>(stream));
 }
 
+mf_status mf_apply_split_block(const mf_operator* op, int cells_per_cta, const void* x_dev, void* y_dev,
+                               void* stream) {
+  if (!op) return set_error(MF_ERR_ARG, "mf_apply_split_block: NULL operator");
+  if (cells_per_cta != 4 && cells_per_cta != 8 && cells_per_cta != 16 && cells_per_cta != 32)
+    return set_error(MF_ERR_ARG, "mf_apply_split_block: cells per CTA must be 4, 8, 16 or 32");
+  mf_status st = check_ready(op, "mf_apply_split_block");
+  if (st) return st;
+  if (!x_dev || !y_dev || x_dev == y_dev) return set_error(MF_ERR_ARG, "mf_apply_split_block: bad vectors");
+  MF_DISPATCH_N(op->n, apply_block_n, op, view_of_elem(op, elem_of(op)), cells_per_cta, x_dev, y_dev,
+                static_cast<cudaStream_t>(stream));
+}
+
 mf_status mf_dss(const mf_operator* op, void* y_dev, void* stream) {
   if (!op || !y_dev) return set_error(MF_ERR_ARG, "mf_dss: NULL argument");
   return launch_dss(op, elem_of(op), y_dev, static_cast<cudaStream_t>(stream));
@@ -369,7 +381,17 @@ mf_status mf_apply_host(const mf_operator* op, const void* x_host, void* y_host,
 }
 
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int, int, int>, int> g_tune_cache; // (device, n, path, kind, view) -> variant
+// (device, n, path, kind, view, size class) -> variant
+static std::map<std::tuple<int, int, int, int, int, int>, int> g_tune_cache;
+// Size class of an operator for the autotuner: floor(log2(cells)).  The best launch shape
+// depends on how many waves of CTAs the mesh makes, so a choice timed on a small mesh is not
+// reused for a large one.
+static int tune_size_class(const mf_operator* op) {
+  const long long cells = (long long)op->g.nx * op->g.ny * op->g.nz;
+  int c = 0;
+  while (c < 62 && (2LL << c) <= cells) ++c;
+  return c;
+}
 
 // The autotuner's choices persist across processes in a JSON object of "key": variant
 // entries, one per line, with key "<GPU name>|lib=2|n=<n>|path=<p>|kind=<k>|view=<v>".  The
@@ -404,7 +426,7 @@ static void tune_file_load(const std::string& path) {
     const char* colon = std::strchr(q1, ':');
     if (!colon) continue;
     int v = -1;
-    if (std::sscanf(colon + 1, " %d", &v) == 1 && v >= 0 && v <= MF_VARIANT_TENSOR)
+    if (std::sscanf(colon + 1, " %d", &v) == 1 && v >= 0 && v <= MF_VARIANT_SMALL_CTA)
       g_tune_file[std::string(q0 + 1, q1)] = v;
   }
   std::fclose(f);
@@ -439,7 +461,8 @@ static std::string tune_key(int dev, const mf_operator* op, int vk) {
   std::string name = "unknown";
   if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
   char buf[160];
-  std::snprintf(buf, sizeof(buf), "|lib=2|n=%d|path=%d|kind=%d|view=%d", op->n, op->path, op->kind, vk);
+  std::snprintf(buf, sizeof(buf), "|lib=3|n=%d|path=%d|kind=%d|view=%d|cells=2^%d", op->n, op->path, op->kind, vk,
+                tune_size_class(op));
   return name + buf;
 }
 
@@ -452,7 +475,7 @@ mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, 
   int dev = 0;
   if ((st = cuda_check(cudaGetDevice(&dev), "cudaGetDevice"))) return st;
   const int vk = view_of_elem(op, elem_of(op));
-  const auto key = std::make_tuple(dev, op->n, op->path, op->kind, vk);
+  const auto key = std::make_tuple(dev, op->n, op->path, op->kind, vk, tune_size_class(op));
   const std::string fkey = tune_key(dev, op, vk);
   const std::string fpath = tune_file_path();
   {
@@ -465,8 +488,10 @@ mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, 
     if (!g_tune_file_loaded) tune_file_load(fpath);
     auto ft = g_tune_file.find(fkey);
     // a stored choice is used if it is valid for this operator (the tensor-core variant only
-    // where it is built)
-    if (ft != g_tune_file.end() && (ft->second < MF_VARIANT_TENSOR || (vk == VK_DD && tc_eligible(op)))) {
+    // where it is built, the small-CTA one on the double-float view)
+    if (ft != g_tune_file.end() &&
+        (ft->second < MF_VARIANT_TENSOR || (ft->second == MF_VARIANT_TENSOR && vk == VK_DD && tc_eligible(op)) ||
+         (ft->second == MF_VARIANT_SMALL_CTA && vk == VK_DD))) {
       op->variant[vk] = ft->second;
       g_tune_cache[key] = ft->second;
       return MF_OK;
@@ -477,8 +502,14 @@ mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, 
   if ((st = cuda_check(cudaEventCreate(&e1), "event"))) { cudaEventDestroy(e0); return st; }
   float best = 1e30f;
   int best_v = 0;
-  const int nvar = (vk == VK_DD && tc_eligible(op)) ? 4 : 3; // variant 3: the tensor-core apply
-  for (int v = 0; v < nvar && st == MF_OK; ++v) {
+  // candidates: 0-2 everywhere, the small-CTA variant on the double-float view, the
+  // tensor-core apply where it is built
+  int cand[5], nvar = 0;
+  for (int v = 0; v < 3; ++v) cand[nvar++] = v;
+  if (vk == VK_DD) cand[nvar++] = MF_VARIANT_SMALL_CTA;
+  if (vk == VK_DD && tc_eligible(op)) cand[nvar++] = MF_VARIANT_TENSOR;
+  for (int ci = 0; ci < nvar && st == MF_OK; ++ci) {
+    const int v = cand[ci];
     op->variant[vk] = v;
     st = launch_apply_split(op, vk, x_dev, y_dev, s); // warm-up
     if (st) break;
@@ -503,7 +534,15 @@ mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, 
 }
 
 mf_status mf_operator_set_variant(mf_operator* op, int variant) {
-  if (!op || variant < 0 || variant > MF_VARIANT_TENSOR) return set_error(MF_ERR_ARG, "mf_operator_set_variant: bad argument");
+  if (!op || variant < 0 || variant > MF_VARIANT_SMALL_CTA)
+    return set_error(MF_ERR_ARG, "mf_operator_set_variant: bad argument");
+  if (variant == MF_VARIANT_SMALL_CTA) {
+    if (view_of_elem(op, elem_of(op)) != VK_DD)
+      return set_error(MF_ERR_UNSUPPORTED, "mf_operator_set_variant: the small-CTA variant covers the double-float "
+                                           "view of MF_FP64 operators");
+    op->variant[VK_DD] = MF_VARIANT_SMALL_CTA;
+    return MF_OK;
+  }
   if (variant == MF_VARIANT_TENSOR) {
     if (!tc_eligible(op))
       return set_error(MF_ERR_UNSUPPORTED, "mf_operator_set_variant: the tensor-core apply covers FP64 Cartesian "

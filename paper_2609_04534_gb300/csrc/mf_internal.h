@@ -223,6 +223,8 @@ mf_status launch_layout(const mf_operator* op, int elem, int mode, const void* i
 template <int N>
 mf_status apply_split_n(const mf_operator* op, int vk, const void* x, void* y, cudaStream_t s);
 template <int N>
+mf_status apply_block_n(const mf_operator* op, int vk, int cells, const void* x, void* y, cudaStream_t s);
+template <int N>
 mf_status apply_cg_n(const mf_operator* op, int vk, void* p, const void* r, void* y, CgState* st, double* partials,
                      int update_p, long long* nblocks, cudaStream_t s);
 template <int N>

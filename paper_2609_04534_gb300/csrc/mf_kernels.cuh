@@ -6,6 +6,7 @@
 // Included once per degree by mf_apply_k<k>.cu so the eight degrees compile in parallel.
 #pragma once
 #include <mutex>
+#include <type_traits>
 
 #include "mf_dd.cuh"
 #include "mf_internal.h"
@@ -19,7 +20,10 @@ namespace mf {
 // Launch configurations of the apply kernels, chosen per operator by the autotuner
 // (mf_operator_autotune): variant 0 = CB0 cells per CTA with registers capped for 2 resident
 // CTAs per SM; variant 1 = CB0/2 cells per CTA, capped for 3 resident CTAs per SM;
-// variant 2 = CB0/2 cells per CTA with no register cap (high degrees spill under a cap).
+// variant 2 = CB0/2 cells per CTA with no register cap (high degrees spill under a cap);
+// variant 4 (double-float compute only) = CB0/2 cells per CTA, capped so that the resident
+// threads per SM equal variant 0's: the smaller block alone (the block-size sweep of Sec. 6
+// measured it 14% faster for the Cartesian apply at k = 5).
 // (Staging the streamed geometry into shared memory with cp.async was measured and lost:
 // the 2-CTA configuration already hides its load latency.)
 constexpr int MF_NUM_VARIANTS = 3;
@@ -32,8 +36,9 @@ struct Cfg {
   static constexpr int CB0 = CELLS0 / CPL;
   static constexpr int CBH = (CB0 / 2) * CPL >= 4 ? CB0 / 2 : 4 / CPL;
   static constexpr int CB = V == 0 ? CB0 : CBH;
-  static constexpr int MINB = V == 0 ? 2 : (V == 1 ? 3 : 1);
+  static constexpr int MINB = V == 0 ? 2 : (V == 1 ? 3 : (V == 4 ? 2 * CB0 / CBH : 1));
   static constexpr int NT = N * N * CB;
+  static constexpr bool GENERAL = true; // kernels of the affine and curved paths built too
   static_assert(CB * CPL >= 4 && BL % (CB * CPL) == 0, "a CTA holds at least 4 cells of a tile (apply_max_blocks)");
 };
 
@@ -1022,7 +1027,7 @@ template <int N>
 mf_status stream_twin_n(const mf_operator* op, int vk, const void* x, void* y, const void* geom, int nc,
                         cudaStream_t s) {
   const int var = op->variant[vk == VK_DDS ? VK_DD : vk];
-  const bool half = var == 1 || var == 2;
+  const bool half = var == 1 || var == 2 || (var == MF_VARIANT_SMALL_CTA && vk != VK_F32);
   if (vk == VK_F32) {
     using C0 = Cfg<FP32C, N, 0>;
     using CH = Cfg<FP32C, N, 1>;
@@ -1362,10 +1367,27 @@ static int prefetch_distance_tiles(const void* kernel, int threads, size_t smem,
   return tiles;
 }
 
-template <typename S, typename T, int N, int V>
-static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, const void* geom, const CgFuse<S>& cg,
+// Block-size sweep of Sec. 6 (B cells per CTA; a measurement entry): the registers are capped
+// so that the resident threads per SM equal those of launch variant 0 (MINB * NT = 2 * NT of
+// variant 0), which separates the block size from the register budget.
+template <typename T, int N, int B, bool G>
+struct BCfg {
+  static constexpr int CPL = CellsPer<T>::value;
+  static constexpr int CB = B / CPL;
+  static constexpr int MINB = 2 * Cfg<T, N, 0>::CB / CB > 0 ? 2 * Cfg<T, N, 0>::CB / CB : 1;
+  static constexpr int NT = N * N * CB;
+  static constexpr bool GENERAL = G;
+  static_assert(B >= 4 && BL % B == 0 && CB * CPL == B && NT <= 1024 && NT >= 32, "B cells per CTA: 4, 8, 16 or 32");
+};
+// B cells per CTA: a CTA of n^2 * B threads, at most 1024 and at least one full warp (the
+// CTA reductions fold in warp 0)
+template <int N, int B>
+constexpr bool block_fits() { return N * N * B <= 1024 && N * N * B >= 32; }
+
+// C: the launch configuration (cells per CTA CB * CPL, MINB resident CTAs, NT threads)
+template <typename S, typename T, int N, typename C>
+static mf_status apply_split_c(const mf_operator* op, const void* x, void* y, const void* geom, const CgFuse<S>& cg,
                                long long* nblocks, cudaStream_t s) {
-  using C = Cfg<T, N, V>;
   ApplyArgs<S, T, N> a;
   fill_job<S, T>(op, a.j);
   fill_tab<typename CoefOf<T>::type, N>(op, a.tab);
@@ -1380,12 +1402,17 @@ static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, co
   if (nblocks) *nblocks = blocks;
   if (blocks <= 0) return MF_OK;
   void (*k)(ApplyArgs<S, T, N>) = nullptr;
-  if (op->path == PATH_CARTESIAN)
+  if (op->path == PATH_CARTESIAN) {
     k = helm ? apply_cartesian<S, T, N, C::CB, C::MINB, true> : apply_cartesian<S, T, N, C::CB, C::MINB, false>;
-  else if (op->path == PATH_AFFINE)
-    k = helm ? apply_general<S, T, N, C::CB, C::MINB, false, true> : apply_general<S, T, N, C::CB, C::MINB, false, false>;
-  else
-    k = helm ? apply_general<S, T, N, C::CB, C::MINB, true, true> : apply_general<S, T, N, C::CB, C::MINB, true, false>;
+  } else if constexpr (C::GENERAL) {
+    if (op->path == PATH_AFFINE)
+      k = helm ? apply_general<S, T, N, C::CB, C::MINB, false, true>
+               : apply_general<S, T, N, C::CB, C::MINB, false, false>;
+    else
+      k = helm ? apply_general<S, T, N, C::CB, C::MINB, true, true> : apply_general<S, T, N, C::CB, C::MINB, true, false>;
+  } else {
+    return set_error(MF_ERR_UNSUPPORTED, "block-size sweep: built for the Cartesian path at this degree");
+  }
   if (smem > 227 * 1024) return set_error(MF_ERR_UNSUPPORTED, "apply variant needs %zu bytes of shared memory", smem);
   // the kernels also hold static shared memory (the CG partial's park, NT doubles, and a few
   // bytes of the compiler's), and static + dynamic above 48 KB needs the opt-in
@@ -1398,12 +1425,51 @@ static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, co
   k<<<(unsigned)blocks, C::NT, smem, s>>>(a);
   return cuda_check(cudaGetLastError(), "apply launch");
 }
+template <typename S, typename T, int N, int V>
+static mf_status apply_split_v(const mf_operator* op, const void* x, void* y, const void* geom, const CgFuse<S>& cg,
+                               long long* nblocks, cudaStream_t s) {
+  return apply_split_c<S, T, N, Cfg<T, N, V>>(op, x, y, geom, cg, nblocks, s);
+}
+
+// Degree 3 (n = 4, the degree of the paper's block-size experiment): every path, the
+// double-float and FP32 views.  Other degrees: the Cartesian double-float apply.
+template <int N, int B>
+static mf_status apply_block_t(const mf_operator* op, int vk, const void* x, void* y, cudaStream_t s) {
+  if constexpr (!block_fits<N, B>()) {
+    return set_error(MF_ERR_UNSUPPORTED, "mf_apply_split_block: %d cells of degree %d do not make a CTA of 32..1024 threads",
+                     B, N - 1);
+  } else {
+    constexpr bool all = N == 4;
+    if (vk == VK_DD)
+      return apply_split_c<double, dd, N, BCfg<dd, N, B, all>>(op, x, y, op->v64.geom, CgFuse<double>{}, nullptr, s);
+    if constexpr (all) {
+      if (vk == VK_F32)
+        return apply_split_c<float, FP32C, N, BCfg<FP32C, N, B, true>>(op, x, y, op->v32.geom, CgFuse<float>{},
+                                                                       nullptr, s);
+    }
+    return set_error(MF_ERR_UNSUPPORTED, "mf_apply_split_block: MF_FP64 (double-float)%s operators only",
+                     all ? " or MF_FP32" : "");
+  }
+}
+template <int N>
+mf_status apply_block_n(const mf_operator* op, int vk, int cells, const void* x, void* y, cudaStream_t s) {
+  switch (cells) {
+    case 4: return apply_block_t<N, 4>(op, vk, x, y, s);
+    case 8: return apply_block_t<N, 8>(op, vk, x, y, s);
+    case 16: return apply_block_t<N, 16>(op, vk, x, y, s);
+    case 32: return apply_block_t<N, 32>(op, vk, x, y, s);
+    default: return set_error(MF_ERR_ARG, "mf_apply_split_block: cells per CTA must be 4, 8, 16 or 32");
+  }
+}
 
 template <typename S, typename T, int N>
 static mf_status apply_split_t(const mf_operator* op, int variant, const void* x, void* y, const void* geom,
                                const CgFuse<S>& cg, long long* nblocks, cudaStream_t s) {
   if (variant == 1) return apply_split_v<S, T, N, 1>(op, x, y, geom, cg, nblocks, s);
   if (variant == 2) return apply_split_v<S, T, N, 2>(op, x, y, geom, cg, nblocks, s);
+  if constexpr (std::is_same<T, dd>::value) {
+    if (variant == MF_VARIANT_SMALL_CTA) return apply_split_v<S, T, N, 4>(op, x, y, geom, cg, nblocks, s);
+  }
   return apply_split_v<S, T, N, 0>(op, x, y, geom, cg, nblocks, s);
 }
 
@@ -1500,6 +1566,9 @@ template <typename S, typename T, int N>
 static mf_status batch_fill_t(const BatchMember* m, int n, int vk, int variant, void* jobs_host, long long* block0_host) {
   if (variant == 1) return batch_fill_v<S, T, N, 1>(m, n, vk, jobs_host, block0_host);
   if (variant == 2) return batch_fill_v<S, T, N, 2>(m, n, vk, jobs_host, block0_host);
+  if constexpr (std::is_same<T, dd>::value) {
+    if (variant == MF_VARIANT_SMALL_CTA) return batch_fill_v<S, T, N, 4>(m, n, vk, jobs_host, block0_host);
+  }
   return batch_fill_v<S, T, N, 0>(m, n, vk, jobs_host, block0_host);
 }
 template <typename S, typename T, int N>
@@ -1507,6 +1576,10 @@ static mf_status batch_launch_t(const mf_operator* op0, int variant, const void*
                                 int njobs, long long blocks, cudaStream_t s) {
   if (variant == 1) return batch_launch_v<S, T, N, 1>(op0, jobs_dev, block0_dev, njobs, blocks, s);
   if (variant == 2) return batch_launch_v<S, T, N, 2>(op0, jobs_dev, block0_dev, njobs, blocks, s);
+  if constexpr (std::is_same<T, dd>::value) {
+    if (variant == MF_VARIANT_SMALL_CTA)
+      return batch_launch_v<S, T, N, 4>(op0, jobs_dev, block0_dev, njobs, blocks, s);
+  }
   return batch_launch_v<S, T, N, 0>(op0, jobs_dev, block0_dev, njobs, blocks, s);
 }
 
@@ -1602,6 +1675,7 @@ mf_status layout_n(const mf_operator* op, int elem, int mode, const void* in, vo
 #define MF_INSTANTIATE_DEGREE(NN)                                                                        \
   namespace mf {                                                                                        \
   template mf_status apply_split_n<NN>(const mf_operator*, int, const void*, void*, cudaStream_t);      \
+  template mf_status apply_block_n<NN>(const mf_operator*, int, int, const void*, void*, cudaStream_t);  \
   template mf_status apply_cg_n<NN>(const mf_operator*, int, void*, const void*, void*, CgState*, double*, \
                                     int, long long*, cudaStream_t);                                     \
   template mf_status dss_n<NN>(const mf_operator*, int, void*, cudaStream_t);                           \

@@ -4,6 +4,9 @@ import sys
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+# the tests time launch variants on small meshes: keep their choices out of the user's
+# persistent autotune file (the persistence test points a subprocess at a file of its own)
+os.environ["MF_AUTOTUNE_CACHE"] = "off"
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 

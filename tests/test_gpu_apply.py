@@ -284,11 +284,16 @@ def test_launch_variants_agree_bitwise_and_autotune(k, geom, prec):
     xn = d.native_from_unique(inputs.random_unique(5, 6, 3, k, 13))
     mf.mf_operator_set_variant(d.op, 0)
     y0 = d.apply(xn)
-    for v in (1, 2):
+    variants = (1, 2, mf.MF_VARIANT_SMALL_CTA) if prec == mf.MF_FP64 else (1, 2)
+    for v in variants:
         mf.mf_operator_set_variant(d.op, v)
         y1 = d.apply(xn)
         torch.cuda.synchronize()
         assert torch.equal(y0, y1), v
+    if prec != mf.MF_FP64:  # the small-CTA variant is built for the double-float view only
+        with pytest.raises(mf.MfError) as e:
+            mf.mf_operator_set_variant(d.op, mf.MF_VARIANT_SMALL_CTA)
+        assert e.value.code == mf.MF_ERR_UNSUPPORTED
     scratch = torch.empty_like(xn)
     v = mf.mf_operator_autotune(d.op, xn.data_ptr(), scratch.data_ptr(), 2)
     if v == mf.MF_VARIANT_TENSOR:  # the tensor-core apply rounds differently (same accuracy)
@@ -297,7 +302,7 @@ def test_launch_variants_agree_bitwise_and_autotune(k, geom, prec):
         torch.cuda.synchronize()
         assert float((y3 - y0).abs().max() / y0.abs().max()) <= 1e-12
     else:
-        assert v in (0, 1, 2)
+        assert v in variants or v == 0
         assert torch.equal(d.apply(xn), y0)
     d.close()
 
@@ -328,7 +333,7 @@ def test_atomic_dss_ablation_matches_sweep_dss(prec, dims, k, bc):
     d.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, mf.MF_VARIANT_SMALL_CTA])
 @pytest.mark.parametrize("geom,kind,prec,k,dims", [
     ("curved", mf.MF_LAPLACE, mf.MF_FP64, 4, (5, 6, 3)),
     ("curved", mf.MF_HELMHOLTZ, mf.MF_FP64, 1, (9, 5, 3)),
@@ -343,6 +348,8 @@ def test_atomic_dss_ablation_matches_sweep_dss(prec, dims, k, bc):
 def test_stream_twin_copies_x(geom, kind, prec, k, dims, variant):
     """The stream twin (the apply's accesses without its arithmetic) writes every native
     element, padding lanes included, as a bit-copy of x, for every view and launch variant."""
+    if variant == mf.MF_VARIANT_SMALL_CTA and prec != mf.MF_FP64:
+        pytest.skip("the small-CTA variant is built for the double-float view only")
     d = DevOp(*dims, k, geom, kind, 1.0, prec, 0)
     mf.mf_operator_set_variant(d.op, variant)
     g = torch.Generator(device="cuda").manual_seed(11)
@@ -387,3 +394,73 @@ def test_autotune_choice_persists_in_json_file(tmp_path):
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     assert int(r.stdout.strip().splitlines()[-1]) == planted
+
+
+@pytest.mark.parametrize("geom,prec,kind", [("cart", mf.MF_FP64, mf.MF_LAPLACE), ("curved", mf.MF_FP64, mf.MF_HELMHOLTZ),
+                                            ("shear", mf.MF_FP32, mf.MF_LAPLACE), ("cart", mf.MF_FP32, mf.MF_HELMHOLTZ),
+                                            ("curved", mf.MF_FP32, mf.MF_HELMHOLTZ)])
+def test_block_size_sweep_matches_split_apply(oracle, geom, prec, kind):
+    """The block-size sweep (B = 4, 8, 16, 32 cells per CTA, degree 3) computes each cell with
+    the arithmetic of launch variant 0: bitwise the same split result, on a ragged mesh whose
+    tiles are partly outside it; the FP64 result also matches the oracle's local apply."""
+    k, dims = 3, (9, 6, 5)
+    d = DevOp(*dims, k, geom, kind, 1.0, prec, 0)
+    xu = inputs.random_unique(*dims, k, 21)
+    xn = d.native_from_unique(xu)
+    mf.mf_operator_set_variant(d.op, 0)
+    y0 = d.apply(xn, split=True)
+    for b in (4, 8, 16, 32):
+        y = torch.full_like(y0, float("nan"))
+        mf.mf_apply_split_block(d.op, b, xn.data_ptr(), y.data_ptr())
+        torch.cuda.synchronize()
+        assert torch.equal(y, y0), b
+    if prec == mf.MF_FP64:
+        o = oracle_op(oracle, *dims, k, geom, 1.0 if kind == mf.MF_HELMHOLTZ else 0.0, 0)
+        ref = o.apply_cells(o.scatter(xu), np.arange(o.ncells)).ravel()
+        got = d.canonical_from_native(y0)
+        assert rel_max(got, ref) <= 1e-12
+    d.close()
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 5, 6, 7, 8])
+def test_block_size_sweep_cartesian_every_degree(oracle, k):
+    """The Cartesian double-float apply with B cells per CTA, at every degree and every B that
+    makes a CTA of 32..1024 threads: bitwise launch variant 0's split result."""
+    dims = (9, 6, 5)
+    d = DevOp(*dims, k, "cart", mf.MF_HELMHOLTZ, 1.0, mf.MF_FP64, 0)
+    xn = d.native_from_unique(inputs.random_unique(*dims, k, 22))
+    mf.mf_operator_set_variant(d.op, 0)
+    y0 = d.apply(xn, split=True)
+    n = k + 1
+    for b in (4, 8, 16, 32):
+        if not 32 <= n * n * b <= 1024:
+            continue
+        y = torch.full_like(y0, float("nan"))
+        mf.mf_apply_split_block(d.op, b, xn.data_ptr(), y.data_ptr())
+        torch.cuda.synchronize()
+        assert torch.equal(y, y0), b
+    d.close()
+
+
+def test_block_size_sweep_refusals():
+    """Combinations that are not built -- the curved path and FP32 away from degree 3, CTAs
+    outside 32..1024 threads, the native-FP64 (DFMA) view of MF_FP64_DFMA and MF_MIXED -- are
+    refused before any launch."""
+    for k, geom, prec, b in ((2, "curved", mf.MF_FP64, 8), (5, "cart", mf.MF_FP32, 8), (1, "cart", mf.MF_FP64, 4),
+                             (7, "cart", mf.MF_FP64, 32)):
+        d = DevOp(4, 4, 4, k, geom, mf.MF_LAPLACE, 1.0, prec, 0)
+        dt = torch.float32 if prec == mf.MF_FP32 else torch.float64
+        x = torch.zeros(d.n_native, dtype=dt, device="cuda")
+        y = torch.zeros_like(x)
+        with pytest.raises(mf.MfError) as e:
+            mf.mf_apply_split_block(d.op, b, x.data_ptr(), y.data_ptr())
+        assert e.value.code == mf.MF_ERR_UNSUPPORTED, (k, geom, prec, b)
+        d.close()
+    for prec in (mf.MF_FP64_DFMA, mf.MF_MIXED):
+        d = DevOp(4, 4, 4, 3, "cart", mf.MF_LAPLACE, 1.0, prec, 0)
+        x = torch.zeros(d.n_native, dtype=torch.float64, device="cuda")
+        y = torch.zeros_like(x)
+        with pytest.raises(mf.MfError) as e:
+            mf.mf_apply_split_block(d.op, 8, x.data_ptr(), y.data_ptr())
+        assert e.value.code == mf.MF_ERR_UNSUPPORTED
+        d.close()

@@ -186,3 +186,19 @@ def test_mixed_restart_option_validation(L):
     assert e.value.code == mf.MF_ERR_ARG
     mf.mf_operator_destroy(op)
     mf.mf_mesh_destroy(mesh)
+
+
+def test_block_sweep_argument_validation(L):
+    """mf_apply_split_block checks B before the operator's state (not set up: MF_ERR_ARG)."""
+    mesh = mf.mf_mesh_create(4, 4, 4)
+    for k, b, code in ((3, 5, mf.MF_ERR_ARG), (3, 64, mf.MF_ERR_ARG), (2, 8, mf.MF_ERR_ARG),
+                       (3, 8, mf.MF_ERR_ARG)):
+        op = mf.mf_operator_create(mesh, k)
+        with pytest.raises(mf.MfError) as e:
+            mf.mf_apply_split_block(op, b, 256, 512)
+        assert e.value.code == code, (k, b)
+        mf.mf_operator_destroy(op)
+    with pytest.raises(mf.MfError) as e:
+        mf.mf_apply_split_block(None, 8, 256, 512)
+    assert e.value.code == mf.MF_ERR_ARG
+    mf.mf_mesh_destroy(mesh)
