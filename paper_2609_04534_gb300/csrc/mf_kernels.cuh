@@ -171,21 +171,25 @@ struct Fold {
 // fastest; a pair value holds cells lane0 + 2c and lane0 + 2c + 1), zeroing padding cells and,
 // for Dirichlet, the constrained nodes (the P of P A P).  In a CG step with update_p the loaded
 // vector is the new direction p = r + beta p, written back.
+// Thread (l0, c) = (threadIdx.x / CB, threadIdx.x % CB) loads local dofs l0 + m n^2 of value c
+// (m < n): its cell is the same in every trip, so its coordinates are found once.
 template <typename S, typename T, int N, int CB, int NT>
 __device__ __forceinline__ void load_tile(const ApplyJob<S, T>& a, long long t, int lane0, T* buf) {
   constexpr int N2 = N * N, N3 = N2 * N, CPL = CellsPer<T>::value;
+  static_assert(NT == N2 * CB, "one thread per pencil position and value");
   const long long base = t * (long long)N3 * BL + lane0;
   const bool fuse = a.cg.st != nullptr && a.cg.update_p;
   const S beta = fuse ? scalar_from_double<S>(a.cg.st->beta) : S(0);
   S* __restrict__ pg = a.cg.p;
   const S* __restrict__ rg = a.cg.r;
+  const int c = threadIdx.x % CB, l0 = threadIdx.x / CB;
+  int cx, cy, cz;
+  cell_of(a.g, t, lane0 + c * CPL, cx, cy, cz); // for a pair: the second cell is at cx + 1
 #pragma unroll
-  for (int idx = threadIdx.x; idx < N3 * CB; idx += NT) {
-    const int l = idx / CB, c = idx - l * CB;
+  for (int m = 0; m < N; ++m) {
+    const int l = l0 + m * N2, idx = l * CB + c;
     const long long e = base + (long long)l * BL + c * CPL;
     if constexpr (CPL == 1) {
-      int cx, cy, cz;
-      cell_of(a.g, t, lane0 + c, cx, cy, cz);
       T v = T(0);
       if (cx < a.g.nx && cy < a.g.ny && cz < a.g.nz) {
         S xv;
@@ -205,8 +209,6 @@ __device__ __forceinline__ void load_tile(const ApplyJob<S, T>& a, long long t, 
       }
       buf[idx] = v;
     } else { // a pair of cells (FP32): 8-byte accesses
-      int cx, cy, cz;
-      cell_of(a.g, t, lane0 + 2 * c, cx, cy, cz); // the second cell is at cx + 1
       const bool yz = cy < a.g.ny && cz < a.g.nz;
       const bool v0 = yz && cx < a.g.nx, v1 = yz && cx + 1 < a.g.nx;
       float2 xv;
