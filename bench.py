@@ -525,8 +525,8 @@ def solve_run(args):
     print(json.dumps(solve_compare(args.solve_n, tuple(args.inner_rtol), True)), flush=True)
 
 
-def serve_stream(n, rate=0.0, single=False, no_batching=False, arena_gb=120, mixed_restart=0):
-    """Serving stream: n Poisson CG solve requests, mesh N^3 with N log-uniform in [4, 64],
+def serve_stream(n, rate=0.0, single=False, no_batching=False, arena_gb=120, mixed_restart=0, nmax=64, chunk=20):
+    """Serving stream: n Poisson CG solve requests, mesh N^3 with N log-uniform in [4, nmax],
     degree uniform in {2..6}, affine or curved 50/50, manufactured right-hand side, FP32 apply
     in FP64 refinement to 1e-10; seed 4.  Reports p50/p99 latency (submit -> result) and
     solved DoF/s over the makespan.  rate 0: all requests at t = 0 (a closed burst)."""
@@ -535,12 +535,13 @@ def serve_stream(n, rate=0.0, single=False, no_batching=False, arena_gb=120, mix
     import paper_2609_04534_gb300 as mf
 
     rng = np.random.default_rng(4)
-    Ns = np.rint(np.exp(rng.uniform(np.log(4), np.log(64), n))).astype(int)
+    Ns = np.rint(np.exp(rng.uniform(np.log(4), np.log(nmax), n))).astype(int)
     ks = rng.integers(2, 7, n)
     geo = rng.integers(0, 2, n)
     arena = torch.empty(int(arena_gb * 2**30), dtype=torch.uint8, device="cuda")
     # single: the baseline of the same stream, the plain FP64 solver one request at a time
     sv = mf.mf_server_create(arena.data_ptr(), arena.numel(), max_slots=1 if single else 64, autotune=1,
+                             chunk_iterations=chunk,
                              batching=-1 if (no_batching or single) else 0, mixed_restart=mixed_restart)
     reqs = [mf.make_request(int(N), int(N), int(N), int(k), geometry=mf.MF_CURVED_SIN if g else mf.MF_AFFINE,
                             rhs=mf.MF_RHS_MANUFACTURED, rtol=1e-10, maxit=400000, mixed=0 if single else 1)
@@ -582,6 +583,7 @@ def serve_stream(n, rate=0.0, single=False, no_batching=False, arena_gb=120, mix
                             outer=int(rs[i]["outer_iterations"]), latency_s=round(float(lat[i]), 3))
                        for i in np.argsort(-lat)[:5]],
            "inner_cg": "restarted" if mixed_restart else "reliable updates",
+           "mesh_n_range": [4, nmax], "chunk_iterations": chunk,
            "batching": not (no_batching or single),
            "solver": "plain FP64 CG, one request at a time" if single else "mixed precision, 64 slots",
            "arena_peak_gb": st["arena_peak"] / 2**30, "slots": 1 if single else 64}
@@ -592,7 +594,8 @@ def serve_stream(n, rate=0.0, single=False, no_batching=False, arena_gb=120, mix
 
 def serve_run(args):
     print(json.dumps(serve_stream(args.serve, args.rate, args.fp64_single, args.no_batching,
-                                  mixed_restart=int(args.mixed_restart))), flush=True)
+                                  mixed_restart=int(args.mixed_restart), nmax=args.serve_nmax,
+                                  chunk=args.serve_chunk)), flush=True)
 
 
 def main():
@@ -622,6 +625,8 @@ def main():
                     help="serving run: NREQ solve requests with Poisson arrivals (prints its own JSON line)")
     ap.add_argument("--rate", type=float, default=0.0, help="serving arrival rate (requests/s); 0 = measure capacity")
     ap.add_argument("--no-batching", action="store_true", help="serving: every request on its own graph chunks")
+    ap.add_argument("--serve-nmax", type=int, default=64, help="serving: largest mesh N (N^3 cells)")
+    ap.add_argument("--serve-chunk", type=int, default=20, help="serving: CG iterations per graph launch")
     ap.add_argument("--mixed-restart", action="store_true",
                     help="serving: restart the inner FP32 CG at every defect-correction step")
     ap.add_argument("--fp64-single", action="store_true",
@@ -879,6 +884,7 @@ def main():
             "helmholtz_sweep_50M": sweep,
             "solve_96cubed": solve,
             "serve_burst": serve,
+            "serve_burst_unbatched": serve_unbatched,
             "cpu_baseline": cpu,
             "e2e": e2e,
             # mask, max|b|, zero x, scale b, copy p, <r,r>, state; then 4 kernels per iteration

@@ -140,6 +140,7 @@ struct ApplyBatch {
   Tab<typename CoefOf<T>::type, N> tab;
   const ApplyJob<S, T>* jobs;
   const long long* block0; // njobs + 1 entries
+  long long nunits;        // block0[njobs]: CTA-sized work units of all jobs
   int njobs;
 };
 

@@ -5,6 +5,7 @@
 //
 // Included once per degree by mf_apply_k<k>.cu so the eight degrees compile in parallel.
 #pragma once
+#include <algorithm>
 #include <mutex>
 #include <type_traits>
 
@@ -754,42 +755,61 @@ __global__ void __launch_bounds__(N * N * CB, MINB) apply_general(ApplyArgs<S, T
   general_body<S, T, N, CB, CURVED, HELM>(A.j, A.tab, blockIdx.x / GPT, (blockIdx.x % GPT) * CC, blockIdx.x);
 }
 
-// the job of batched CTA blockIdx.x into shared memory; returns its local CTA index
+// The batched apply is one persistent launch: as many CTAs as fit the GPU at once, each
+// taking work units u = blockIdx.x, blockIdx.x + gridDim.x, ... of the concatenated unit
+// space of all jobs (a unit is what one CTA of the job's own launch does).  batch_unit finds
+// the job of unit u (largest i with block0[i] <= u), copies its description into shared
+// memory when it differs from the one held (jheld), and returns the unit's local index, so a
+// unit computes exactly what the job's solo launch computes in that CTA.
 template <typename S, typename T>
-__device__ __forceinline__ long long batch_job(const ApplyJob<S, T>* jobs, const long long* block0, int njobs,
-                                               ApplyJob<S, T>& sj) {
+__device__ __forceinline__ long long batch_unit(const ApplyJob<S, T>* jobs, const long long* block0, int njobs,
+                                                long long u, ApplyJob<S, T>& sj, int& jheld) {
   __shared__ int jsel;
   if (threadIdx.x == 0) {
-    int lo = 0, hi = njobs - 1; // largest i with block0[i] <= blockIdx.x
+    int lo = 0, hi = njobs - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (block0[mid] <= (long long)blockIdx.x) lo = mid;
+      if (block0[mid] <= u) lo = mid;
       else hi = mid - 1;
     }
     jsel = lo;
   }
   __syncthreads();
   const int j = jsel;
-  static_assert(sizeof(ApplyJob<S, T>) % 8 == 0, "job description copied as 8-byte words");
-  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(jobs + j);
-  unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sj);
-  for (int i = threadIdx.x; i < (int)(sizeof(ApplyJob<S, T>) / 8); i += blockDim.x) dst[i] = src[i];
-  __syncthreads();
-  return (long long)blockIdx.x - block0[j];
+  if (j != jheld) { // uniform: both are shared
+    static_assert(sizeof(ApplyJob<S, T>) % 8 == 0, "job description copied as 8-byte words");
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(jobs + j);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sj);
+    for (int i = threadIdx.x; i < (int)(sizeof(ApplyJob<S, T>) / 8); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    if (threadIdx.x == 0) jheld = j; // every thread has read jheld above; the next read follows
+                                     // the barrier that ends the unit
+  }
+  return u - block0[j];
 }
 template <typename S, typename T, int N, int CB, int MINB, bool HELM>
 __global__ void __launch_bounds__(N * N * CB, MINB) apply_cartesian_batch(ApplyBatch<S, T, N> B) {
   constexpr int CC = CB * CellsPer<T>::value, GPT = BL / CC;
   __shared__ __align__(16) ApplyJob<S, T> sj;
-  const long long b = batch_job(B.jobs, B.block0, B.njobs, sj);
-  cartesian_apply<S, T, N, CB, HELM>(sj, B.tab, b / GPT, (int)(b % GPT) * CC, b);
+  __shared__ int jheld;
+  if (threadIdx.x == 0) jheld = -1;
+  for (long long u = blockIdx.x; u < B.nunits; u += gridDim.x) {
+    const long long b = batch_unit(B.jobs, B.block0, B.njobs, u, sj, jheld);
+    cartesian_apply<S, T, N, CB, HELM>(sj, B.tab, b / GPT, (int)(b % GPT) * CC, b);
+    __syncthreads(); // the next unit reuses the shared buffers (and may replace sj)
+  }
 }
 template <typename S, typename T, int N, int CB, int MINB, bool CURVED, bool HELM>
 __global__ void __launch_bounds__(N * N * CB, MINB) apply_general_batch(ApplyBatch<S, T, N> B) {
   constexpr int CC = CB * CellsPer<T>::value, GPT = BL / CC;
   __shared__ __align__(16) ApplyJob<S, T> sj;
-  const long long b = batch_job(B.jobs, B.block0, B.njobs, sj);
-  general_body<S, T, N, CB, CURVED, HELM>(sj, B.tab, b / GPT, (int)(b % GPT) * CC, b);
+  __shared__ int jheld;
+  if (threadIdx.x == 0) jheld = -1;
+  for (long long u = blockIdx.x; u < B.nunits; u += gridDim.x) {
+    const long long b = batch_unit(B.jobs, B.block0, B.njobs, u, sj, jheld);
+    general_body<S, T, N, CB, CURVED, HELM>(sj, B.tab, b / GPT, (int)(b % GPT) * CC, b);
+    __syncthreads(); // the next unit reuses the shared buffers (and may replace sj)
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1345,6 +1365,33 @@ static void fill_tab(const mf_operator* op, Tab<T, N>& tab) {
 #ifndef MF_PREFETCH_WAVES
 #define MF_PREFETCH_WAVES 1
 #endif
+// CTAs of a kernel resident on the whole GPU at once (SMs x occupancy), cached per kernel,
+// dynamic shared memory and device; 2^31 - 1 when the query fails (then the launch is simply
+// not persistent).
+static long long resident_ctas(const void* kernel, int threads, size_t smem) {
+  struct Entry {
+    const void* k;
+    size_t smem;
+    int dev;
+    long long ctas;
+  };
+  static Entry cache[64];
+  static int ncache = 0;
+  static std::mutex mu;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  for (int i = 0; i < ncache; ++i)
+    if (cache[i].k == kernel && cache[i].smem == smem && cache[i].dev == dev) return cache[i].ctas;
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  cudaGetLastError();
+  const long long ctas = (sms > 0 && per_sm > 0) ? (long long)sms * per_sm : 0x7fffffffLL;
+  if (ncache < 64) cache[ncache++] = Entry{kernel, smem, dev, ctas};
+  return ctas;
+}
+
 static int prefetch_distance_tiles(const void* kernel, int threads, size_t smem, int gpt) {
   if (MF_PREFETCH_WAVES <= 0) return 0;
   struct Entry {
@@ -1559,8 +1606,10 @@ static mf_status batch_launch_v(const mf_operator* op0, const void* jobs_dev, co
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(e, "cudaFuncSetAttribute(batched apply)");
   }
-  if (blocks > 0x7fffffffLL) return set_error(MF_ERR_UNSUPPORTED, "batched apply of %lld CTAs", blocks);
-  k<<<(unsigned)blocks, C::NT, smem, s>>>(B);
+  // one persistent launch: the CTAs resident on the GPU at once, looping over the units
+  B.nunits = blocks;
+  const long long grid = std::min<long long>(blocks, resident_ctas((const void*)k, C::NT, smem));
+  k<<<(unsigned)grid, C::NT, smem, s>>>(B);
   return cuda_check(cudaGetLastError(), "batched apply launch");
 }
 

@@ -139,7 +139,7 @@ struct BatchClass {
   std::vector<uint64_t> planned;  // tickets whose descriptors are on the device
   BatchPlan plan;
   bool running = false;
-  cudaGraphExec_t exec = nullptr; // the chunk of the planned composition
+  cudaGraphExec_t exec = nullptr; // one iteration of the planned composition
   bool exec_current = false;
 };
 
@@ -307,7 +307,9 @@ int class_view(const Job* j) {
 }
 
 // The batch class of a request in its inner CG (created on first use).  nullptr when its
-// buffers do not fit: the request then runs its own chunks.
+// buffers do not fit: the request then runs its own chunks.  (Up to four concurrent chunks
+// per class -- a request ready while its class's chunk is in flight starting another -- were
+// measured: no gain on the 100- and 400-request streams.)
 BatchClass* class_of(mf_server* sv, const Job* j) {
   const int vk = class_view(j);
   const int variant = j->op->variant[vk == VK_DDS ? VK_DD : vk];
@@ -371,19 +373,15 @@ mf_status after_advance(mf_server* sv, Job* j, Slot& sl) {
   return cuda_check(cudaEventRecord(sl.ev, sl.s), "event record");
 }
 
-// The chunk of a class's planned batch as a CUDA graph: chunk batched iterations, the state
-// gather and its copy to the pinned mirror.  An existing executable graph is updated in place
-// when the new one differs only in parameters (launch sizes, copy size), else rebuilt.
-mf_status capture_chunk(BatchClass* c, int chunk, int n) {
+// One batched CG iteration of a class's planned composition as a CUDA graph (apply, alpha,
+// update, direction), launched chunk times per chunk.  A graph of one iteration keeps the
+// re-capture after a membership change short (a handful of launches instead of a chunk's
+// worth); an existing executable graph is updated in place when the new one differs only in
+// parameters (launch sizes), else rebuilt.
+mf_status capture_iteration(BatchClass* c) {
   mf_status st = cuda_check(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal), "batch capture");
   if (st) return st;
-  mf_status cst = MF_OK;
-  for (int it = 0; it < chunk && cst == MF_OK; ++it) cst = batch_iteration(c->plan, c->s);
-  CgState* states_dev = reinterpret_cast<CgState*>(c->dev + c->states_off);
-  if (!cst) cst = batch_gather_states(c->plan, states_dev, c->s);
-  if (!cst)
-    cst = cuda_check(cudaMemcpyAsync(c->host + c->states_off, states_dev, sizeof(CgState) * (size_t)n,
-                                     cudaMemcpyDeviceToHost, c->s), "batch states D2H");
+  const mf_status cst = batch_iteration(c->plan, c->s);
   cudaGraph_t g = nullptr;
   const cudaError_t ce = cudaStreamEndCapture(c->s, &g);
   if (cst || ce != cudaSuccess) {
@@ -401,6 +399,19 @@ mf_status capture_chunk(BatchClass* c, int chunk, int n) {
   if (!c->exec) st = cuda_check(cudaGraphInstantiate(&c->exec, g, 0), "batch graph instantiate");
   cudaGraphDestroy(g);
   c->exec_current = st == MF_OK;
+  return st;
+}
+
+// A chunk: chunk launches of the iteration graph, then the members' CG states gathered and
+// copied to the pinned mirror.
+mf_status launch_chunk(BatchClass* c, int chunk, int n) {
+  mf_status st = MF_OK;
+  for (int it = 0; it < chunk && st == MF_OK; ++it) st = cuda_check(cudaGraphLaunch(c->exec, c->s), "batch launch");
+  CgState* states_dev = reinterpret_cast<CgState*>(c->dev + c->states_off);
+  if (!st) st = batch_gather_states(c->plan, states_dev, c->s);
+  if (!st)
+    st = cuda_check(cudaMemcpyAsync(c->host + c->states_off, states_dev, sizeof(CgState) * (size_t)n,
+                                    cudaMemcpyDeviceToHost, c->s), "batch states D2H");
   return st;
 }
 
@@ -468,8 +479,8 @@ bool run_batches(mf_server* sv) {
       c->planned = st ? std::vector<uint64_t>() : tickets;
       c->exec_current = false;
     }
-    if (!st && !c->exec_current) st = capture_chunk(c, mem[0]->eng.chunk, (int)mem.size());
-    if (!st) st = cuda_check(cudaGraphLaunch(c->exec, c->s), "batch chunk launch");
+    if (!st && !c->exec_current) st = capture_iteration(c);
+    if (!st) st = launch_chunk(c, mem[0]->eng.chunk, (int)mem.size());
     if (!st) st = cuda_check(cudaEventRecord(c->ev, c->s), "batch event");
     if (st) {
       cudaStreamSynchronize(c->s);

@@ -180,3 +180,28 @@ def test_large_curved_q6_request_reaches_1e_10():
     assert res["status"] == mf.MF_OK, res
     assert res["rel_residual"] <= 1e-10, res
     assert res["n_cellwise"] == 60**3 * 7**3
+
+
+def test_persistent_batch_loops_over_more_units_than_resident_ctas():
+    """Twelve Q4 requests of 16 x 16 x 28..32 cells (240-256 tiles: at the batching cap), two
+    CTA-sized units per tile in the FP32 inner solve, make batched applies of ~3000 units per
+    class (affine, curved), more than the GPU holds at once: the persistent launch's CTAs
+    each take several units of several requests.  Every result equals the request solved
+    alone, bitwise."""
+    reqs = [dict(nx=16, ny=16, nz=28 + 2 * (i % 3), degree=4, geometry=mf.MF_CURVED_SIN if i % 2 else mf.MF_AFFINE,
+                 rhs=mf.MF_RHS_RANDOM, seed=60 + i, mixed=1) for i in range(12)]
+    sv, arena = make_server(arena_gb=8.0, slots=16)
+    try:
+        res, xs = run(sv, [mf.make_request(**p) for p in reqs], timeout=600.0)
+    finally:
+        mf.mf_server_destroy(sv)
+    for p, r in zip(reqs, res):
+        assert r["status"] == mf.MF_OK and r["rel_residual"] <= 1e-10, (p, r)
+    for i in (0, 1, 11):
+        sv1, arena1 = make_server(arena_gb=2.0, slots=1, batching=-1)
+        try:
+            (r1,), (x1,) = run(sv1, [mf.make_request(**reqs[i])], timeout=600.0)
+        finally:
+            mf.mf_server_destroy(sv1)
+        assert r1["iterations"] == res[i]["iterations"]
+        assert np.array_equal(x1, xs[i]), reqs[i]
