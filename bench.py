@@ -525,7 +525,7 @@ def solve_run(args):
     print(json.dumps(solve_compare(args.solve_n, tuple(args.inner_rtol), True)), flush=True)
 
 
-def serve_stream(n, rate=0.0, single=False, no_batching=False, arena_gb=120, mixed_restart=0, nmax=64, chunk=20):
+def serve_stream(n, rate=0.0, single=False, no_batching=False, arena_gb=120, mixed_restart=0, nmax=64, chunk=0):
     """Serving stream: n Poisson CG solve requests, mesh N^3 with N log-uniform in [4, nmax],
     degree uniform in {2..6}, affine or curved 50/50, manufactured right-hand side, FP32 apply
     in FP64 refinement to 1e-10; seed 4.  Reports p50/p99 latency (submit -> result) and
@@ -583,7 +583,7 @@ def serve_stream(n, rate=0.0, single=False, no_batching=False, arena_gb=120, mix
                             outer=int(rs[i]["outer_iterations"]), latency_s=round(float(lat[i]), 3))
                        for i in np.argsort(-lat)[:5]],
            "inner_cg": "restarted" if mixed_restart else "reliable updates",
-           "mesh_n_range": [4, nmax], "chunk_iterations": chunk,
+           "mesh_n_range": [4, nmax], "chunk_iterations": chunk or 10,
            "batching": not (no_batching or single),
            "solver": "plain FP64 CG, one request at a time" if single else "mixed precision, 64 slots",
            "arena_peak_gb": st["arena_peak"] / 2**30, "slots": 1 if single else 64}
@@ -626,7 +626,7 @@ def main():
     ap.add_argument("--rate", type=float, default=0.0, help="serving arrival rate (requests/s); 0 = measure capacity")
     ap.add_argument("--no-batching", action="store_true", help="serving: every request on its own graph chunks")
     ap.add_argument("--serve-nmax", type=int, default=64, help="serving: largest mesh N (N^3 cells)")
-    ap.add_argument("--serve-chunk", type=int, default=20, help="serving: CG iterations per graph launch")
+    ap.add_argument("--serve-chunk", type=int, default=0, help="serving: CG iterations per graph launch (0: 10)")
     ap.add_argument("--mixed-restart", action="store_true",
                     help="serving: restart the inner FP32 CG at every defect-correction step")
     ap.add_argument("--fp64-single", action="store_true",

@@ -388,7 +388,7 @@ enum { MF_RHS_MANUFACTURED = 0, MF_RHS_RANDOM = 1 };
 typedef struct {
   int32_t max_slots;        /* concurrent requests (default 32, at most 256) */
   int32_t queue_capacity;   /* pending requests before MF_ERR_BUSY (default 100000) */
-  int32_t chunk_iterations; /* CG iterations per graph launch (default 20) */
+  int32_t chunk_iterations; /* CG iterations per graph launch (default 10) */
   int32_t autotune;         /* 1: autotune the apply of each new operator class */
   double inner_rtol;        /* mixed: inner FP32 CG tolerance (default 0.1, reliable updates) */
   int32_t batching;         /* 0 / 1: continuous batches of CG iterations (default); -1: off */

@@ -370,7 +370,7 @@ def mf_cg_record_history(hist_ptr: int | None, cap: int) -> None:
 
 # ---------------------------------------------------------------- serving
 def mf_server_create(arena_ptr: int, arena_bytes: int, max_slots: int = 32, queue_capacity: int = 0,
-                     chunk_iterations: int = 20, autotune: int = 0, inner_rtol: float = 0.0, batching: int = 0,
+                     chunk_iterations: int = 0, autotune: int = 0, inner_rtol: float = 0.0, batching: int = 0,
                      mixed_restart: int = 0):
     cfg = mf_server_config(max_slots, queue_capacity, chunk_iterations, autotune, inner_rtol, batching, mixed_restart)
     h = C.c_void_p()
