@@ -724,15 +724,17 @@ def main():
     # algorithmic bytes of one apply (x 8 + y 8 + 6 metric words x 8 = 64 B per cell-wise DoF
     # for the curved FP64 Laplace operator) over its CUDA-event time, against the measured HBM
     # copy bandwidth.  traffic: DRAM bytes of this kernel from one ncu capture of the same kernel
-    # on the curved Q4 48^3 case, 79.0 B per cell-wise DoF, scaled to the bench's DoFs.
-    traffic = 79.02 * ncw
+    # on the curved Q4 48^3 case, 78.4 B per cell-wise DoF (the 14.4 above 64: its next-wave
+    # L2 prefetch), scaled to the bench's DoFs.
+    traffic = 1084.3e6 / 13824000 * ncw
     roof = {"bound": "hbm", "achieved": alg_bytes / t_fused / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": alg_bytes / t_fused / 1e9 / pk["hbm_gbs"], "traffic": traffic,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy kernel), of measured" if pk["source"] == "measured"
             else "fallback 6800 GB/s",
             "algorithmic_bytes_per_dof": alg_bytes / ncw,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of apply_general<dd,dd,5,16,2,1,0> "
-                              "on Q4 curved 48^3 (13.82 M DoFs): 1092.3 MB, scaled by DoFs",
+                              "on Q4 curved 48^3 (13.82 M DoFs): 1084.3 MB, scaled by DoFs; 874.6 MB with the "
+                              "L2 prefetch off",
             "kernel": "apply_general<dd,dd,5,curved,laplace> as the split-dual CG apply "
                       "(A_K p and <p, A_K p> at the quadrature points)",
             "kernel_ms": round(t_fused * 1e3, 4),
