@@ -846,7 +846,7 @@ def main():
             solve = {"error": str(exc)[:200]}
     # config 5 (shortened): a burst of requests of the serving stream through the batched
     # mixed-precision server
-    serve = None
+    serve = serve_unbatched = None
     if rank == 0 and args.serve_burst > 0:
         try:
             with Clocks(local) as vclk:
@@ -856,6 +856,16 @@ def main():
             serve["clocks"] = vclk.summary()
         except Exception as exc:
             serve = {"error": str(exc)[:200]}
+        # the same burst with every request on its own graph chunks (batching off)
+        try:
+            with Clocks(local) as uclk:
+                uclk.mark_start()
+                serve_unbatched = serve_stream(args.serve_burst, 0.0, False, True, arena_gb=60)
+                uclk.mark_end()
+            serve_unbatched["clocks"] = uclk.summary()
+            serve_unbatched.pop("slowest", None)
+        except Exception as exc:
+            serve_unbatched = {"error": str(exc)[:200]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
