@@ -296,7 +296,7 @@ def profile_apply(args):
         x = random_native(mf, torch, op, info, N, k, 1, dt, s)
         y = torch.empty_like(x)
     tensor = mf.mf_operator_get_variant(op) == mf.MF_VARIANT_TENSOR
-    small = [mf.MF_VARIANT_SMALL_CTA] if p == mf.MF_FP64 else []
+    small = [mf.MF_VARIANT_SMALL_CTA, mf.MF_VARIANT_OCCUPANCY] if p == mf.MF_FP64 else []
     for v in ([args.variant] if args.variant >= 0 else [0, 1, 2] + small + ([mf.MF_VARIANT_TENSOR] if tensor else [])):
         mf.mf_operator_set_variant(op, v)
         t = time_apply(mf, torch, op, x, y, stream, args.reps, 1)
@@ -439,7 +439,8 @@ def block_sweep(args):
         for b in (4, 8, 16, 32):
             if 32 <= (k + 1) ** 2 * b <= 1024:
                 out[f"B{b}"] = rec(timed(lambda: mf.mf_apply_split_block(op, b, x.data_ptr(), y.data_ptr(), s)))
-        for v in sorted({0, 1, 2, default} | ({mf.MF_VARIANT_SMALL_CTA} if p == mf.MF_FP64 else set())):
+        dd_only = {mf.MF_VARIANT_SMALL_CTA, mf.MF_VARIANT_OCCUPANCY} if p == mf.MF_FP64 else set()
+        for v in sorted({0, 1, 2, default} | dd_only):
             mf.mf_operator_set_variant(op, v)
             out[f"variant{v}"] = rec(timed(lambda: mf.mf_apply_split(op, x.data_ptr(), y.data_ptr(), s)))
         out["default_variant"] = default

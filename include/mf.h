@@ -111,16 +111,16 @@ mf_status mf_operator_setup(mf_operator* op, void* workspace_dev, size_t bytes, 
  * threads per CTA, registers capped for two CTAs per SM; variant 1: half the cells per CTA,
  * capped for three; variant 2: half the cells per CTA, no register cap; variant 3, for
  * MF_FP64 operators on an axis-aligned affine mesh of degree 1..3 only: the tensor-core
- * apply, see MF_VARIANT_TENSOR; variant 4, for MF_FP64 (double-float) operators only: half
- * the cells per CTA with variant 0's resident threads per SM, see MF_VARIANT_SMALL_CTA) with
- * `reps` applies of x_dev into y_dev (both native vectors
+ * apply, see MF_VARIANT_TENSOR; variants 4 and 5, for MF_FP64 (double-float) operators
+ * only: see MF_VARIANT_SMALL_CTA and MF_VARIANT_OCCUPANCY) with `reps` applies of x_dev into
+ * y_dev (both native vectors
  * of this operator; y is overwritten) and keeps the fastest.  The choice is cached per
  * (device, degree, path, kind, precision, size class = floor(log2(cells))) for the life of
  * the process, so later operators of
  * the same class reuse it without timing, and persisted across processes in a JSON file keyed
  * by the GPU's name (MF_AUTOTUNE_CACHE, else $XDG_CACHE_HOME/libmf/autotune.json or
  * $HOME/.cache/libmf/autotune.json; MF_AUTOTUNE_CACHE=off disables the file): a stored choice
- * is used without timing.  Synchronises `stream` when it times.  Variants 0-2 and 4 run the same
+ * is used without timing.  Synchronises `stream` when it times.  Variants 0-2, 4 and 5 run the same
  * per-thread arithmetic and give bitwise equal results; variant 3 rounds differently (same
  * accuracy class), so its results agree with theirs within 1e-12 relative max-norm. */
 mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, int reps, void* stream);
@@ -136,14 +136,18 @@ mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, 
  * per value.  A non-finite input value makes its cell's outputs NaN.  Needs
  * mf_operator_setup (the digit table lives in the operator workspace, at most 48 KB). */
 #define MF_VARIANT_TENSOR 3
-/* Half the cells per CTA of variant 0, with registers capped so that the resident threads
- * per SM stay variant 0's: the block size alone changes (the B axis of the paper's
- * block-size experiment, Sec. 6; see mf_apply_split_block).  Double-float view of MF_FP64
- * operators; same per-thread arithmetic as variants 0-2 (bitwise equal results). */
+/* Half the cells per CTA of variant 0 (the B axis of the paper's block-size experiment,
+ * Sec. 6; see mf_apply_split_block), with registers capped for 1.5x variant 0's resident
+ * threads per SM.  Double-float view of MF_FP64 operators; same per-thread arithmetic as
+ * variants 0-2 (bitwise equal results). */
 #define MF_VARIANT_SMALL_CTA 4
+/* Variant 0's cells per CTA with registers capped for three resident CTAs per SM instead of
+ * two.  Double-float view of MF_FP64 operators; bitwise equal results. */
+#define MF_VARIANT_OCCUPANCY 5
 /* Forces a launch variant (0, 1 or 2) for every precision view, or MF_VARIANT_TENSOR /
- * MF_VARIANT_SMALL_CTA for the double-float view of an MF_FP64 operator (MF_ERR_UNSUPPORTED
- * for an operator they do not cover); MF_ERR_ARG for any other value. */
+ * MF_VARIANT_SMALL_CTA / MF_VARIANT_OCCUPANCY for the double-float view of an MF_FP64
+ * operator (MF_ERR_UNSUPPORTED for an operator they do not cover); MF_ERR_ARG for any other
+ * value. */
 mf_status mf_operator_set_variant(mf_operator* op, int variant);
 /* Variant in use for the operator's main precision view (-1 for a NULL operator). */
 int mf_operator_get_variant(const mf_operator* op);

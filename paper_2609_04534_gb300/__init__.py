@@ -25,6 +25,7 @@ MF_CG_DEFAULT, MF_CG_SPLIT_DUAL, MF_CG_ASSEMBLED, MF_CG_SPLIT_DUAL_FUSED = 0, 1,
 MF_PRECOND_NONE, MF_PRECOND_JACOBI, MF_PRECOND_CHEBYSHEV = 0, 1, 2
 MF_VARIANT_TENSOR = 3
 MF_VARIANT_SMALL_CTA = 4
+MF_VARIANT_OCCUPANCY = 5
 
 _STATUS = {0: "MF_OK", -1: "MF_ERR_ARG", -2: "MF_ERR_OOM", -3: "MF_ERR_CUDA", -4: "MF_ERR_NOT_CONVERGED",
            -5: "MF_ERR_BREAKDOWN", -6: "MF_ERR_TIMEOUT", -7: "MF_ERR_BUSY", -8: "MF_ERR_UNSUPPORTED",

@@ -19,7 +19,7 @@ INC = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INC, "-I", CSRC]
-# extra nvcc flags for tuning sweeps, e.g. MF_NVCC_FLAGS="-DMF_APPLY_MIN_BLOCKS=2"
+# extra nvcc flags for tuning sweeps, e.g. MF_NVCC_FLAGS="-DMF_PREFETCH_WAVES=0"
 EXTRA = os.environ.get("MF_NVCC_FLAGS", "").split()
 
 

@@ -426,7 +426,7 @@ static void tune_file_load(const std::string& path) {
     const char* colon = std::strchr(q1, ':');
     if (!colon) continue;
     int v = -1;
-    if (std::sscanf(colon + 1, " %d", &v) == 1 && v >= 0 && v <= MF_VARIANT_SMALL_CTA)
+    if (std::sscanf(colon + 1, " %d", &v) == 1 && v >= 0 && v <= MF_VARIANT_OCCUPANCY)
       g_tune_file[std::string(q0 + 1, q1)] = v;
   }
   std::fclose(f);
@@ -461,7 +461,7 @@ static std::string tune_key(int dev, const mf_operator* op, int vk) {
   std::string name = "unknown";
   if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
   char buf[160];
-  std::snprintf(buf, sizeof(buf), "|lib=3|n=%d|path=%d|kind=%d|view=%d|cells=2^%d", op->n, op->path, op->kind, vk,
+  std::snprintf(buf, sizeof(buf), "|lib=4|n=%d|path=%d|kind=%d|view=%d|cells=2^%d", op->n, op->path, op->kind, vk,
                 tune_size_class(op));
   return name + buf;
 }
@@ -491,7 +491,7 @@ mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, 
     // where it is built, the small-CTA one on the double-float view)
     if (ft != g_tune_file.end() &&
         (ft->second < MF_VARIANT_TENSOR || (ft->second == MF_VARIANT_TENSOR && vk == VK_DD && tc_eligible(op)) ||
-         (ft->second == MF_VARIANT_SMALL_CTA && vk == VK_DD))) {
+         ((ft->second == MF_VARIANT_SMALL_CTA || ft->second == MF_VARIANT_OCCUPANCY) && vk == VK_DD))) {
       op->variant[vk] = ft->second;
       g_tune_cache[key] = ft->second;
       return MF_OK;
@@ -502,11 +502,14 @@ mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, 
   if ((st = cuda_check(cudaEventCreate(&e1), "event"))) { cudaEventDestroy(e0); return st; }
   float best = 1e30f;
   int best_v = 0;
-  // candidates: 0-2 everywhere, the small-CTA variant on the double-float view, the
-  // tensor-core apply where it is built
-  int cand[5], nvar = 0;
+  // candidates: 0-2 everywhere, the small-CTA and occupancy variants on the double-float
+  // view, the tensor-core apply where it is built
+  int cand[6], nvar = 0;
   for (int v = 0; v < 3; ++v) cand[nvar++] = v;
-  if (vk == VK_DD) cand[nvar++] = MF_VARIANT_SMALL_CTA;
+  if (vk == VK_DD) {
+    cand[nvar++] = MF_VARIANT_SMALL_CTA;
+    cand[nvar++] = MF_VARIANT_OCCUPANCY;
+  }
   if (vk == VK_DD && tc_eligible(op)) cand[nvar++] = MF_VARIANT_TENSOR;
   for (int ci = 0; ci < nvar && st == MF_OK; ++ci) {
     const int v = cand[ci];
@@ -534,13 +537,13 @@ mf_status mf_operator_autotune(mf_operator* op, const void* x_dev, void* y_dev, 
 }
 
 mf_status mf_operator_set_variant(mf_operator* op, int variant) {
-  if (!op || variant < 0 || variant > MF_VARIANT_SMALL_CTA)
+  if (!op || variant < 0 || variant > MF_VARIANT_OCCUPANCY)
     return set_error(MF_ERR_ARG, "mf_operator_set_variant: bad argument");
-  if (variant == MF_VARIANT_SMALL_CTA) {
+  if (variant == MF_VARIANT_SMALL_CTA || variant == MF_VARIANT_OCCUPANCY) {
     if (view_of_elem(op, elem_of(op)) != VK_DD)
-      return set_error(MF_ERR_UNSUPPORTED, "mf_operator_set_variant: the small-CTA variant covers the double-float "
+      return set_error(MF_ERR_UNSUPPORTED, "mf_operator_set_variant: variants 4 and 5 cover the double-float "
                                            "view of MF_FP64 operators");
-    op->variant[VK_DD] = MF_VARIANT_SMALL_CTA;
+    op->variant[VK_DD] = variant;
     return MF_OK;
   }
   if (variant == MF_VARIANT_TENSOR) {

@@ -22,9 +22,11 @@ namespace mf {
 // (mf_operator_autotune): variant 0 = CB0 cells per CTA with registers capped for 2 resident
 // CTAs per SM; variant 1 = CB0/2 cells per CTA, capped for 3 resident CTAs per SM;
 // variant 2 = CB0/2 cells per CTA with no register cap (high degrees spill under a cap);
-// variant 4 (double-float compute only) = CB0/2 cells per CTA, capped so that the resident
-// threads per SM equal variant 0's: the smaller block alone (the block-size sweep of Sec. 6
-// measured it 14% faster for the Cartesian apply at k = 5).
+// variant 4 (double-float compute only) = CB0/2 cells per CTA, registers capped for 1.5x
+// variant 0's resident threads per SM; variant 5 (double-float only) = CB0 cells per CTA,
+// capped for three resident CTAs (also 1.5x).  The block-size sweep of Sec. 6 found the
+// double-float apply faster in smaller blocks, and a later sweep of the register budget
+// found it faster at higher occupancy: the Cartesian apply at k = 4..7 gains 5-17%.
 // (Staging the streamed geometry into shared memory with cp.async was measured and lost:
 // the 2-CTA configuration already hides its load latency.)
 constexpr int MF_NUM_VARIANTS = 3;
@@ -36,8 +38,8 @@ struct Cfg {
   static constexpr int CELLS0 = (N <= 4) ? 32 : (N <= 6) ? 16 : (N <= 8) ? 8 : (IsF32<T>::value ? 8 : 4);
   static constexpr int CB0 = CELLS0 / CPL;
   static constexpr int CBH = (CB0 / 2) * CPL >= 4 ? CB0 / 2 : 4 / CPL;
-  static constexpr int CB = V == 0 ? CB0 : CBH;
-  static constexpr int MINB = V == 0 ? 2 : (V == 1 ? 3 : (V == 4 ? 2 * CB0 / CBH : 1));
+  static constexpr int CB = (V == 0 || V == 5) ? CB0 : CBH;
+  static constexpr int MINB = V == 0 ? 2 : (V == 1 || V == 5) ? 3 : (V == 4 ? 3 * CB0 / CBH : 1);
   static constexpr int NT = N * N * CB;
   static constexpr bool GENERAL = true; // kernels of the affine and curved paths built too
   static_assert(CB * CPL >= 4 && BL % (CB * CPL) == 0, "a CTA holds at least 4 cells of a tile (apply_max_blocks)");
@@ -1590,6 +1592,7 @@ static mf_status apply_split_t(const mf_operator* op, int variant, const void* x
   if (variant == 2) return apply_split_v<S, T, N, 2>(op, x, y, geom, cg, nblocks, s);
   if constexpr (std::is_same<T, dd>::value) {
     if (variant == MF_VARIANT_SMALL_CTA) return apply_split_v<S, T, N, 4>(op, x, y, geom, cg, nblocks, s);
+    if (variant == MF_VARIANT_OCCUPANCY) return apply_split_v<S, T, N, 5>(op, x, y, geom, cg, nblocks, s);
   }
   return apply_split_v<S, T, N, 0>(op, x, y, geom, cg, nblocks, s);
 }
@@ -1691,6 +1694,7 @@ static mf_status batch_fill_t(const BatchMember* m, int n, int vk, int variant, 
   if (variant == 2) return batch_fill_v<S, T, N, 2>(m, n, vk, jobs_host, block0_host);
   if constexpr (std::is_same<T, dd>::value) {
     if (variant == MF_VARIANT_SMALL_CTA) return batch_fill_v<S, T, N, 4>(m, n, vk, jobs_host, block0_host);
+    if (variant == MF_VARIANT_OCCUPANCY) return batch_fill_v<S, T, N, 5>(m, n, vk, jobs_host, block0_host);
   }
   return batch_fill_v<S, T, N, 0>(m, n, vk, jobs_host, block0_host);
 }
@@ -1702,6 +1706,8 @@ static mf_status batch_launch_t(const mf_operator* op0, int variant, const void*
   if constexpr (std::is_same<T, dd>::value) {
     if (variant == MF_VARIANT_SMALL_CTA)
       return batch_launch_v<S, T, N, 4>(op0, jobs_dev, block0_dev, njobs, blocks, s);
+    if (variant == MF_VARIANT_OCCUPANCY)
+      return batch_launch_v<S, T, N, 5>(op0, jobs_dev, block0_dev, njobs, blocks, s);
   }
   return batch_launch_v<S, T, N, 0>(op0, jobs_dev, block0_dev, njobs, blocks, s);
 }

@@ -284,16 +284,17 @@ def test_launch_variants_agree_bitwise_and_autotune(k, geom, prec):
     xn = d.native_from_unique(inputs.random_unique(5, 6, 3, k, 13))
     mf.mf_operator_set_variant(d.op, 0)
     y0 = d.apply(xn)
-    variants = (1, 2, mf.MF_VARIANT_SMALL_CTA) if prec == mf.MF_FP64 else (1, 2)
+    variants = (1, 2, mf.MF_VARIANT_SMALL_CTA, mf.MF_VARIANT_OCCUPANCY) if prec == mf.MF_FP64 else (1, 2)
     for v in variants:
         mf.mf_operator_set_variant(d.op, v)
         y1 = d.apply(xn)
         torch.cuda.synchronize()
         assert torch.equal(y0, y1), v
-    if prec != mf.MF_FP64:  # the small-CTA variant is built for the double-float view only
-        with pytest.raises(mf.MfError) as e:
-            mf.mf_operator_set_variant(d.op, mf.MF_VARIANT_SMALL_CTA)
-        assert e.value.code == mf.MF_ERR_UNSUPPORTED
+    if prec != mf.MF_FP64:  # variants 4 and 5 are built for the double-float view only
+        for v in (mf.MF_VARIANT_SMALL_CTA, mf.MF_VARIANT_OCCUPANCY):
+            with pytest.raises(mf.MfError) as e:
+                mf.mf_operator_set_variant(d.op, v)
+            assert e.value.code == mf.MF_ERR_UNSUPPORTED
     scratch = torch.empty_like(xn)
     v = mf.mf_operator_autotune(d.op, xn.data_ptr(), scratch.data_ptr(), 2)
     if v == mf.MF_VARIANT_TENSOR:  # the tensor-core apply rounds differently (same accuracy)
@@ -333,7 +334,7 @@ def test_atomic_dss_ablation_matches_sweep_dss(prec, dims, k, bc):
     d.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1, mf.MF_VARIANT_SMALL_CTA])
+@pytest.mark.parametrize("variant", [0, 1, mf.MF_VARIANT_SMALL_CTA, mf.MF_VARIANT_OCCUPANCY])
 @pytest.mark.parametrize("geom,kind,prec,k,dims", [
     ("curved", mf.MF_LAPLACE, mf.MF_FP64, 4, (5, 6, 3)),
     ("curved", mf.MF_HELMHOLTZ, mf.MF_FP64, 1, (9, 5, 3)),
@@ -348,8 +349,8 @@ def test_atomic_dss_ablation_matches_sweep_dss(prec, dims, k, bc):
 def test_stream_twin_copies_x(geom, kind, prec, k, dims, variant):
     """The stream twin (the apply's accesses without its arithmetic) writes every native
     element, padding lanes included, as a bit-copy of x, for every view and launch variant."""
-    if variant == mf.MF_VARIANT_SMALL_CTA and prec != mf.MF_FP64:
-        pytest.skip("the small-CTA variant is built for the double-float view only")
+    if variant in (mf.MF_VARIANT_SMALL_CTA, mf.MF_VARIANT_OCCUPANCY) and prec != mf.MF_FP64:
+        pytest.skip("variants 4 and 5 are built for the double-float view only")
     d = DevOp(*dims, k, geom, kind, 1.0, prec, 0)
     mf.mf_operator_set_variant(d.op, variant)
     g = torch.Generator(device="cuda").manual_seed(11)
