@@ -1801,6 +1801,8 @@ mf_status layout_n(const mf_operator* op, int elem, int mode, const void* in, vo
 
 } // namespace mf
 
+// Two translation units per degree, compiled in parallel: the single-operator kernels, and
+// the batched kernels of the serving loop.
 #define MF_INSTANTIATE_DEGREE(NN)                                                                        \
   namespace mf {                                                                                        \
   template mf_status apply_split_n<NN>(const mf_operator*, int, const void*, void*, cudaStream_t);      \
@@ -1813,9 +1815,12 @@ mf_status layout_n(const mf_operator* op, int elem, int mode, const void* in, vo
   template mf_status stream_twin_n<NN>(const mf_operator*, int, const void*, void*, const void*, int,    \
                                        cudaStream_t);                                                   \
   template mf_status diagonal_n<NN>(const mf_operator*, float*, float*, cudaStream_t);                   \
+  template mf_status geometry_n<NN>(const mf_operator*, int, void*, cudaStream_t);                      \
+  template mf_status layout_n<NN>(const mf_operator*, int, int, const void*, void*, cudaStream_t);      \
+  }
+#define MF_INSTANTIATE_DEGREE_BATCH(NN)                                                                  \
+  namespace mf {                                                                                        \
   template mf_status apply_batch_fill_n<NN>(const BatchMember*, int, int, void*, long long*);            \
   template mf_status apply_batch_launch_n<NN>(const mf_operator*, int, const void*, const long long*, int,  \
                                               long long, cudaStream_t);                                 \
-  template mf_status geometry_n<NN>(const mf_operator*, int, void*, cudaStream_t);                      \
-  template mf_status layout_n<NN>(const mf_operator*, int, int, const void*, void*, cudaStream_t);      \
   }
