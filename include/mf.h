@@ -378,7 +378,10 @@ mf_status mf_cg_record_history(double* hist_host, int cap);
  * iterations run in a continuous batch: every active request of the same degree, path,
  * operator kind, vector precision and launch variant takes part in one batched launch per
  * kernel of the (split-dual) CG iteration -- apply, alpha, update, direction -- in chunks of
- * chunk_iterations, and requests join and leave the batch between chunks.  Each request's
+ * chunk_iterations, and requests join and leave the batch between chunks.  The batched apply
+ * is one persistent launch: the CTAs that fit the GPU at once loop over the CTA-sized work
+ * units of all members.  Requests whose own apply takes more than 1024 CTAs run their own
+ * graph chunks (they fill the GPU alone).  Each request's
  * arithmetic (its CTAs, reductions and their order) is exactly that of its own solo launch,
  * so its result does not depend on what else is in the batch.  batching = -1 runs every
  * request as separate graph chunks on its own stream instead.  A native scheduler thread
