@@ -1442,7 +1442,7 @@ static void fill_tab(const mf_operator* op, Tab<T, N>& tab) {
 // CTAs of a kernel resident on the whole GPU at once (SMs x occupancy), cached per kernel,
 // dynamic shared memory and device; 2^31 - 1 when the query fails (then the launch is simply
 // not persistent).
-static long long resident_ctas(const void* kernel, int threads, size_t smem) {
+[[maybe_unused]] static long long resident_ctas(const void* kernel, int threads, size_t smem) {
   struct Entry {
     const void* k;
     size_t smem;
@@ -1466,7 +1466,7 @@ static long long resident_ctas(const void* kernel, int threads, size_t smem) {
   return ctas;
 }
 
-static int prefetch_distance_tiles(const void* kernel, int threads, size_t smem, int gpt) {
+[[maybe_unused]] static int prefetch_distance_tiles(const void* kernel, int threads, size_t smem, int gpt) {
   if (MF_PREFETCH_WAVES <= 0) return 0;
   struct Entry {
     const void* k;
